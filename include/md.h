@@ -1,0 +1,205 @@
+/*
+ * md.h -- C ABI of the GB300 (sm_103a) molecular-dynamics library.
+ *
+ * The library advances N classical particles in a cubic periodic box under a
+ * truncated (and by default shifted) 12-6 Lennard-Jones pair potential, either
+ * monatomic or as the Kob-Andersen A/B mixture, with the NVE velocity-Verlet
+ * integrator.  This is the MD step of Colberg & Hoefling (arXiv:0912.3824):
+ *   - Sec. 2.2: velocity Verlet, one thread per particle; cell binning by a
+ *     parallel sort; a fixed-size Verlet neighbour list with a skin, rebuilt
+ *     when the maximum particle displacement demands it; the force loop over
+ *     the list; parallel reductions (maximum displacement, potential energy,
+ *     temperature, centre-of-mass velocity, virial tensor); a periodic
+ *     space-filling-curve reorder of the particles in memory;
+ *   - Sec. 2.4: double-single arithmetic (a pair of floats, about 44 bits)
+ *     for the velocity-Verlet update and for the summation of force
+ *     contributions, while the pair forces themselves stay single precision;
+ *   - Sec. 3: the 12-6 potential cut at r_c; Sec. 5: the Kob-Andersen
+ *     parameters (sigma_AA=1, sigma_BB=0.88, sigma_AB=0.8, eps_AA=1,
+ *     eps_BB=0.5, eps_AB=1.5, equal masses).
+ * Several independent systems ("replicas", each with its own N and box) can
+ * be advanced together by one handle; they share the potential and dt.
+ *
+ * Units are reduced Lennard-Jones units (sigma_AA, eps_AA, m).
+ *
+ * Conventions for every call:
+ *   - Return value: MD_OK (0) or one of the MD_E_* codes below; the message of
+ *     the last failure is available from md_last_error().
+ *   - Host arrays passed in are owned by the caller and only read during the
+ *     call (they are copied).  Host arrays passed out must be allocated by the
+ *     caller with the stated size.
+ *   - Per-particle host arrays are in the ORIGINAL particle order (the order
+ *     given to md_create), replicas concatenated, whatever order the library
+ *     keeps internally.  Vectors are [n][3] row-major float64.
+ *   - Device memory: the library allocates no device memory.  The caller
+ *     provides one workspace of md_workspace_size() bytes, 256-byte aligned,
+ *     which must stay valid until md_destroy().  The library keeps
+ *     pinned host staging buffers of its own.
+ *   - All device work is issued on the CUDA stream given to md_create()
+ *     (a cudaStream_t cast to void*; NULL = legacy default stream).
+ *     md_step() returns without waiting for the GPU; the calls that return
+ *     data (md_compute_forces, md_observables, md_get_state,
+ *     md_get_neighbours, md_info, md_sync) wait for the stream.
+ *   - Device-side failures (neighbour-list overflow, a non-finite value, a
+ *     particle moving more than a quarter box in one step) stop the
+ *     step loop at the end of the offending step, leave the state at that
+ *     step, and are reported by the next md_sync / md_observables / md_step.
+ */
+#ifndef MD_GB300_H
+#define MD_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define MD_OK           0
+#define MD_E_INVAL      1  /* bad argument (sizes, box too small for the cutoff, dt <= 0 ...) */
+#define MD_E_NOMEM      2  /* workspace smaller than md_workspace_size()                     */
+#define MD_E_CUDA       3  /* a CUDA runtime call failed                                      */
+#define MD_E_NONFINITE  4  /* a position became NaN or infinite                               */
+#define MD_E_UNSTABLE   5  /* a particle moved more than a quarter box length in one step     */
+#define MD_E_TIMEOUT    6  /* the device-side step loop exceeded its iteration bound          */
+#define MD_E_CAPACITY   7  /* a neighbour list needed more than neigh_capacity entries        */
+
+/* precision modes (Sec. 2.4) */
+#define MD_PREC_FP64  0    /* everything in IEEE double                                        */
+#define MD_PREC_MIXED 1    /* FP32 pair forces; double-single positions, velocities and
+                              integration; compensated force summation; FP64 reductions   */
+#define MD_PREC_FP32  2    /* everything in single precision (the paper's comparator)         */
+
+typedef struct {
+    int32_t n_species;        /* 1 or 2                                                        */
+    int32_t shift;            /* 1 = truncated and shifted (V(r_c) = 0), 0 = truncated only    */
+    double  eps[2][2];        /* epsilon_ab (symmetric)                                         */
+    double  sigma[2][2];      /* sigma_ab (symmetric)                                           */
+    double  rcut[2][2];       /* absolute cutoff r_c,ab (Kob-Andersen: 2.5 sigma_ab)            */
+    double  mass[2];          /* mass per species                                               */
+    double  dt;               /* time step, > 0                                                 */
+    double  skin;             /* neighbour-list skin, >= 0 (default 0.3)                        */
+    int32_t precision;        /* MD_PREC_*                                                      */
+    int32_t neigh_capacity;   /* list entries per particle; 0 = derived from the density        */
+    int32_t sample_interval;  /* record observables every this many steps (>= 1)                */
+    int32_t obs_capacity;     /* ring-buffer samples kept on the device (0 = 4096)              */
+    int32_t threads_per_particle; /* force-kernel lanes per particle: 0 = automatic, else 1..32,
+                                     a power of two                                              */
+    int32_t use_graph;        /* 1 = md_step runs as one CUDA graph with the rebuild branch and
+                                 the step loop decided on the device (default); 0 = plain
+                                 stream launches, for debugging and per-kernel timing          */
+    int32_t reorder;          /* 1 = order cells along a Morton curve (default); 0 = x-fastest  */
+    int32_t reserved[7];      /* must be zero                                                   */
+} md_params;
+
+/* one sample of the reductions of Sec. 2.2, per replica */
+typedef struct {
+    int64_t step;             /* MD step index of the sample                                    */
+    double  e_pot;            /* sum over pairs of V(r_ij)                                      */
+    double  e_kin;            /* sum of m v^2 / 2                                               */
+    double  virial;           /* sum over pairs of r_ij . F_ij                                  */
+    double  w[6];             /* virial tensor xx, yy, zz, xy, xz, yz                           */
+    double  p[3];             /* total momentum                                                 */
+    double  max_disp;         /* largest displacement since the last list build (all replicas)  */
+    int64_t rebuilds;         /* neighbour-list builds so far (all replicas)                    */
+} md_obs;
+
+typedef struct {
+    int64_t n_total;          /* particles over all replicas                                    */
+    int32_t n_replicas;
+    int32_t neigh_capacity;   /* K in use                                                       */
+    int32_t threads_per_particle;
+    int32_t cells_per_edge;   /* of replica 0 (1 when the box holds fewer than 3 cells)         */
+    int64_t step;             /* MD steps done since md_create                                  */
+    int64_t rebuilds;         /* neighbour-list builds since md_create                          */
+    int64_t kernel_launches;  /* library kernels executed on the device since md_create         */
+    int32_t max_neighbours;   /* largest list length at the last build                          */
+    int32_t status;           /* pending device status (MD_OK if none)                          */
+    double  force_ms;         /* with use_graph = 0: summed CUDA-event time of the force kernel */
+    int64_t force_launches;   /* with use_graph = 0: force-kernel launches timed                */
+} md_info_t;
+
+typedef struct md_handle md_handle;
+
+/* Fill p with the monatomic LJ defaults: eps = sigma = m = 1, r_c = 2.5,
+ * shifted, dt = 0.005, skin = 0.3, MD_PREC_MIXED, sample_interval = 100,
+ * use_graph = 1, reorder = 1.  Returns MD_OK, or MD_E_INVAL if p is NULL. */
+int md_params_default(md_params *p);
+
+/* Device workspace needed for n_replicas systems with n_per_replica[r]
+ * particles in cubic boxes of edge box[r].  Writes *bytes. */
+int md_workspace_size(const md_params *p, int32_t n_replicas,
+                      const int64_t *n_per_replica, const double *box, size_t *bytes);
+
+/* Create a handle.  species[n_total] in {0, n_species-1}; pos[n_total][3]
+ * (any real coordinates: they are wrapped into [0, box)), vel[n_total][3],
+ * image[n_total][3] (may be NULL = zeros).  Uploads the state, bins the
+ * particles, builds the neighbour lists, evaluates the forces and records
+ * the step-0 sample.  Each box must exceed twice the largest cutoff plus
+ * skin.  workspace: device memory of at least md_workspace_size() bytes.
+ * cuda_stream: a cudaStream_t or NULL. */
+int md_create(md_handle **h, const md_params *p, int32_t n_replicas,
+              const int64_t *n_per_replica, const double *box,
+              const int32_t *species, const double *pos, const double *vel,
+              const int32_t *image, void *workspace, size_t workspace_bytes,
+              void *cuda_stream);
+
+/* Advance every replica by nsteps >= 1 velocity-Verlet steps (Sec. 2.2),
+ * rebuilding the neighbour lists whenever some particle has moved more than
+ * skin/2 since the last build.  Asynchronous on the handle's stream. */
+int md_step(md_handle *h, int64_t nsteps);
+
+/* Scale all velocities of replica r by sqrt(T_target[r] / T_r), with
+ * T_r = 2 E_kin,r / (3 N_r - 3)  (the exact rescale of Sec. 2.3). */
+int md_rescale_velocities(md_handle *h, const double *T_target);
+
+/* Force on every particle at the current positions, f[n_total][3] (may be
+ * NULL), per-particle potential energy e[n_total] = half of each pair
+ * energy (may be NULL), and per-replica totals[n_replicas] (may be NULL;
+ * e_pot, virial, w are the force-kernel reductions, e_kin and p those of the
+ * current velocities).  Rebuilds the lists first.  Waits for the stream. */
+int md_compute_forces(md_handle *h, double *f, double *e, md_obs *totals);
+
+/* Copy out the samples recorded since the previous call, oldest first, as
+ * [sample][replica] records; at most max_samples samples (the newest are kept
+ * when more were recorded than the ring holds).  *n_samples receives the
+ * number written.  Waits for the stream; returns any pending device status. */
+int md_observables(md_handle *h, md_obs *out, int32_t max_samples, int32_t *n_samples);
+
+/* Current positions (wrapped into [0, box)), velocities and image counters,
+ * original order.  Any output may be NULL.  Waits for the stream. */
+int md_get_state(md_handle *h, double *pos, double *vel, int32_t *image);
+
+/* Replace positions, velocities and images (original order; image may be
+ * NULL = zeros), then re-bin, rebuild the lists and evaluate the forces.
+ * Asynchronous: the host arrays are staged through pinned memory before
+ * the call returns. */
+int md_set_state(md_handle *h, const double *pos, const double *vel, const int32_t *image);
+
+/* Current neighbour lists, for inspection: counts[n_total] and
+ * lists[n_total][kmax] of partner indices (original order; unused entries -1;
+ * lists may be NULL).  Waits for the stream. */
+int md_get_neighbours(md_handle *h, int32_t *counts, int32_t *lists, int32_t kmax);
+
+/* Counters and settings of the handle.  Waits for the stream. */
+int md_info(md_handle *h, md_info_t *out);
+
+/* Wait for the stream and return the pending device status (MD_OK if none).
+ * A status is reported once; the state stays at the step where it arose. */
+int md_sync(md_handle *h);
+
+/* Release the handle (not the workspace).  Waits for the stream. */
+int md_destroy(md_handle *h);
+
+/* Message of the last failure on h (never NULL). */
+const char *md_last_error(const md_handle *h);
+
+/* Fixed name of a status code. */
+const char *md_status_string(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MD_GB300_H */

@@ -87,6 +87,9 @@ def _load():
             lib.orc_neighbours_brute.argtypes = [P, C.c_long, C.c_double, _ip, _dp, C.c_double,
                                                  _ip, C.c_void_p, C.c_long]
             lib.orc_neighbours_brute.restype = C.c_long
+            lib.orc_force_one.argtypes = [P, C.c_long, C.c_double, _ip, _dp, C.c_long, _dp,
+                                          C.POINTER(C.c_double)]
+            lib.orc_force_one.restype = None
             _lib = lib
     return _lib
 
@@ -138,6 +141,24 @@ def forces_brute(params, box, species, pos):
 
 def forces_cells(params, box, species, pos):
     return _forces(_load().orc_forces_cells, params, box, species, pos)
+
+
+def force_on(params, box, species, pos, idx):
+    """Brute-force force and energy share on each particle in idx: (f[k,3], e[k])."""
+    n = len(species)
+    pos = _f64(pos, (n, 3))
+    sp = _i32(species)
+    lib = _load()
+    p = _pot(params)
+    f = np.zeros((len(idx), 3))
+    e = np.zeros(len(idx))
+    f3 = np.zeros(3)
+    ei = C.c_double()
+    for k, i in enumerate(idx):
+        lib.orc_force_one(C.byref(p), n, float(box), sp, pos, int(i), f3, C.byref(ei))
+        f[k] = f3
+        e[k] = ei.value
+    return f, e
 
 
 def kinetic(params, species, vel):

@@ -139,6 +139,35 @@ void orc_forces_brute(const orc_pot *p, long n, double L, const int *type,
 }
 
 /*
+ * Force f3[3] and energy share *e (half of each pair energy) on the single
+ * particle i, summed over every other particle by brute force.  Used to
+ * check large systems on a sample of particles.
+ */
+void orc_force_one(const orc_pot *p, long n, double L, const int *type,
+                   const double *pos, long i, double *f3, double *e)
+{
+    double fx = 0.0, fy = 0.0, fz = 0.0, ei = 0.0;
+    for (long j = 0; j < n; ++j) {
+        if (j == i)
+            continue;
+        double dx = min_image(pos[3 * i + 0] - pos[3 * j + 0], L);
+        double dy = min_image(pos[3 * i + 1] - pos[3 * j + 1], L);
+        double dz = min_image(pos[3 * i + 2] - pos[3 * j + 2], L);
+        double v, fr;
+        if (orc_pair(p, type[i], type[j], dx * dx + dy * dy + dz * dz, &v, &fr)) {
+            fx += fr * dx;
+            fy += fr * dy;
+            fz += fr * dz;
+            ei += 0.5 * v;
+        }
+    }
+    f3[0] = fx;
+    f3[1] = fy;
+    f3[2] = fz;
+    *e = ei;
+}
+
+/*
  * Cell-list version, written independently of the brute-force loop:
  * textbook linked cells (head / next arrays), cell edge >= r_c,max,
  * each unordered pair visited once by only taking partners j > i.

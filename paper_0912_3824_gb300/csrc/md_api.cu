@@ -1,0 +1,1056 @@
+// md_api.cu -- host implementation of the C ABI declared in include/md.h.
+//
+// The handle carves every device array out of the caller's workspace, keeps
+// the per-replica tables there, and drives the kernels on the caller's stream.
+// md_step() runs as one CUDA graph:
+//
+//   integrate(FIRST) -> IF(rebuild){bin, scan, scatter, permute, copyback, nbuild}
+//     -> WHILE(loop){ force -> integrate(LOOP) -> IF(rebuild){...} }
+//
+// where the last block of each integrate kernel sets both conditions on the
+// device (rebuild when the largest displacement since the last build exceeds
+// skin/2; loop while steps remain), so a whole md_step of n steps is one graph
+// launch with no host round trip.  With use_graph = 0 the same kernels are
+// launched one by one and the rebuild kernels return at once when no rebuild
+// is pending.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "md.h"
+#include "md_common.cuh"
+
+using mdk::KArgs;
+using mdk::KernelSet;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+constexpr int kIntBlock = 256, kForceBlock = 256, kNbBlock = 256, kScanBlock = 1024;
+constexpr double kCellMargin = 1e-3;   // cell edge exceeds the largest list radius by this
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+// Everything that follows from the parameters and the replica sizes.
+struct Geometry {
+    int R = 0;
+    int64_t n = 0;
+    int K = 0, tpp = 8, ppb_f = 32;
+    int nblk_i = 0, nblk_f = 0, ncell = 0;
+    double rl_max = 0.0;
+    std::vector<mdk::Rep> rep;
+    std::vector<int4> blk_i, blk_f;
+    std::vector<int> crank;
+    std::vector<int4> cxyz;
+};
+
+struct Layout {
+    size_t off_ctl, off_rep, off_blk_i, off_blk_f, off_crank, off_cxyz;
+    size_t off_pa, off_pb, off_va, off_vb, off_pa2, off_pb2, off_va2, off_vb2, off_force;
+    size_t off_rref, off_image, off_image2, off_key, off_tmpidx, off_cellof;
+    size_t off_ccount, off_ccursor, off_cstart, off_nbr, off_nnbr, off_part_f, off_part_i;
+    size_t off_ring, off_totals, off_scale, off_st_pos, off_st_vel, off_st_img, off_st_code;
+    size_t off_st_f, off_st_e, total;
+};
+
+int prec_pos_bytes(int prec) { return prec == MD_PREC_FP64 ? 32 : 16; }
+
+uint32_t spread3(uint32_t v)
+{
+    uint32_t r = 0;
+    for (int b = 0; b < 10; ++b)
+        r |= ((v >> b) & 1u) << (3 * b);
+    return r;
+}
+
+int auto_capacity(const md_params *p, const Geometry &g, const std::vector<double> &box,
+                  const std::vector<int64_t> &nrep)
+{
+    double rho = 0.0;
+    for (size_t r = 0; r < box.size(); ++r)
+        rho = std::max(rho, (double)nrep[r] / (box[r] * box[r] * box[r]));
+    const double nl = 4.18879020478639 * g.rl_max * g.rl_max * g.rl_max * rho;   // 4/3 pi r^3 rho
+    int k = (int)std::ceil(1.35 * nl + 24.0);
+    k = (k + 31) / 32 * 32;
+    (void)p;
+    return std::max(k, 32);
+}
+
+// Returns MD_OK or MD_E_INVAL with *msg set.
+int make_geometry(const md_params *p, int R, const int64_t *nrep, const double *box, Geometry &g,
+                  std::string &msg)
+{
+    if (!p || R < 1 || !nrep || !box) {
+        msg = "null argument or n_replicas < 1";
+        return MD_E_INVAL;
+    }
+    if (p->n_species < 1 || p->n_species > 2) { msg = "n_species must be 1 or 2"; return MD_E_INVAL; }
+    if (!(p->dt > 0.0) || !std::isfinite(p->dt)) { msg = "dt must be positive"; return MD_E_INVAL; }
+    if (!(p->skin >= 0.0)) { msg = "skin must be >= 0"; return MD_E_INVAL; }
+    if (p->precision < 0 || p->precision > 2) { msg = "unknown precision mode"; return MD_E_INVAL; }
+    if (p->sample_interval < 1) { msg = "sample_interval must be >= 1"; return MD_E_INVAL; }
+    const int tpp = p->threads_per_particle;
+    if (tpp != 0 && (tpp < 1 || tpp > 32 || (tpp & (tpp - 1)))) {
+        msg = "threads_per_particle must be 0 or a power of two in [1, 32]";
+        return MD_E_INVAL;
+    }
+    for (int k = 0; k < 7; ++k)
+        if (p->reserved[k] != 0) { msg = "reserved fields must be zero"; return MD_E_INVAL; }
+    const int ns = p->n_species;
+    double rcmax = 0.0;
+    for (int a = 0; a < ns; ++a) {
+        if (!(p->mass[a] > 0.0)) { msg = "masses must be positive"; return MD_E_INVAL; }
+        for (int b = 0; b < ns; ++b) {
+            if (p->eps[a][b] != p->eps[b][a] || p->sigma[a][b] != p->sigma[b][a] ||
+                p->rcut[a][b] != p->rcut[b][a]) {
+                msg = "pair parameters must be symmetric";
+                return MD_E_INVAL;
+            }
+            if (!(p->sigma[a][b] > 0.0) || !(p->rcut[a][b] > 0.0)) {
+                msg = "sigma and rcut must be positive";
+                return MD_E_INVAL;
+            }
+            rcmax = std::max(rcmax, p->rcut[a][b]);
+        }
+    }
+    g.R = R;
+    g.rl_max = rcmax + p->skin + (double)mdk::kListMargin;
+    g.tpp = tpp ? tpp : 8;
+    g.ppb_f = kForceBlock / g.tpp;
+    g.n = 0;
+    g.rep.assign(R, mdk::Rep{});
+    g.blk_i.clear();
+    g.blk_f.clear();
+    g.crank.clear();
+    g.cxyz.clear();
+    int cell0 = 0;
+    for (int r = 0; r < R; ++r) {
+        const double L = box[r];
+        if (nrep[r] < 2) { msg = "every replica needs at least 2 particles"; return MD_E_INVAL; }
+        if (!(L > 2.0 * g.rl_max)) {
+            char b[160];
+            snprintf(b, sizeof b, "box %d (L = %g) must exceed twice the largest cutoff plus skin (%g)",
+                     r, L, 2.0 * g.rl_max);
+            msg = b;
+            return MD_E_INVAL;
+        }
+        if (g.n + nrep[r] > (int64_t)(1 << 30)) { msg = "too many particles"; return MD_E_INVAL; }
+        mdk::Rep &q = g.rep[r];
+        q.start = (int)g.n;
+        q.n = (int)nrep[r];
+        int nc = (int)std::floor(L / (g.rl_max + kCellMargin));
+        if (nc < 3)
+            nc = 1;
+        if (nc > 1024)
+            nc = 1024;
+        q.nc = nc;
+        q.cell0 = cell0;
+        q.L = L;
+        q.invL = 1.0 / L;
+        q.cscale = nc / L;
+        q.invLf = (float)(1.0 / L);
+        q.cscalef = (float)(nc / L);
+        // anchoring grid: smallest power of two with 2L < 2^24 * grid
+        int e = (int)std::ceil(std::log2(2.0 * L)) - 24;
+        double grid = std::ldexp(1.0, e);
+        while (2.0 * L >= grid * 16777216.0)
+            grid *= 2.0;
+        q.grid = (float)grid;
+        q.inv_grid = (float)(1.0 / grid);
+        if (p->precision == MD_PREC_MIXED) {
+            const double lh = std::rint(L / grid) * grid;
+            q.Lhi = (float)lh;
+            q.Llo = (float)(L - lh);
+        } else {
+            q.Lhi = (float)L;
+            q.Llo = (float)(L - (double)(float)L);
+        }
+        // integrate-kernel blocks
+        q.bi0 = (int)g.blk_i.size();
+        for (int s = 0; s < q.n; s += kIntBlock)
+            g.blk_i.push_back(make_int4(q.start + s, q.start + std::min(q.n, s + kIntBlock), r, 0));
+        q.bi1 = (int)g.blk_i.size();
+        q.bf0 = (int)g.blk_f.size();
+        for (int s = 0; s < q.n; s += g.ppb_f)
+            g.blk_f.push_back(make_int4(q.start + s, q.start + std::min(q.n, s + g.ppb_f), r, 0));
+        q.bf1 = (int)g.blk_f.size();
+        // cells, ordered along a Morton curve (or x-fastest)
+        const int nc3 = nc * nc * nc;
+        std::vector<std::pair<uint32_t, int>> order(nc3);
+        for (int lin = 0; lin < nc3; ++lin) {
+            const int cx = lin % nc, cy = (lin / nc) % nc, cz = lin / (nc * nc);
+            const uint32_t code = p->reorder ? (spread3(cx) | (spread3(cy) << 1) | (spread3(cz) << 2))
+                                             : (uint32_t)lin;
+            order[lin] = {code, lin};
+        }
+        std::sort(order.begin(), order.end());
+        g.crank.resize(cell0 + nc3);
+        g.cxyz.resize(cell0 + nc3);
+        for (int rank = 0; rank < nc3; ++rank) {
+            const int lin = order[rank].second;
+            g.crank[cell0 + lin] = cell0 + rank;
+            g.cxyz[cell0 + rank] = make_int4(lin % nc, (lin / nc) % nc, lin / (nc * nc), r);
+        }
+        cell0 += nc3;
+        g.n += nrep[r];
+    }
+    g.ncell = cell0;
+    g.nblk_i = (int)g.blk_i.size();
+    g.nblk_f = (int)g.blk_f.size();
+    std::vector<double> bx(box, box + R);
+    std::vector<int64_t> nr(nrep, nrep + R);
+    g.K = p->neigh_capacity > 0 ? (p->neigh_capacity + 7) / 8 * 8 : auto_capacity(p, g, bx, nr);
+    return MD_OK;
+}
+
+Layout make_layout(const md_params *p, const Geometry &g)
+{
+    Layout L;
+    size_t o = 0;
+    auto take = [&](size_t bytes) { size_t r = o; o = align_up(o + std::max<size_t>(bytes, 1)); return r; };
+    const size_t n = (size_t)g.n;
+    const size_t pb = prec_pos_bytes(p->precision);
+    const bool mixed = p->precision == MD_PREC_MIXED;
+    const int cap = p->obs_capacity > 0 ? p->obs_capacity : 4096;
+    L.off_ctl = take(sizeof(mdk::Ctl));
+    L.off_rep = take(sizeof(mdk::Rep) * g.R);
+    L.off_blk_i = take(sizeof(int4) * g.nblk_i);
+    L.off_blk_f = take(sizeof(int4) * g.nblk_f);
+    L.off_crank = take(sizeof(int) * g.ncell);
+    L.off_cxyz = take(sizeof(int4) * g.ncell);
+    L.off_pa = take(pb * n);
+    L.off_pb = take(mixed ? 16 * n : 0);
+    L.off_va = take(pb * n);
+    L.off_vb = take(mixed ? 16 * n : 0);
+    L.off_pa2 = take(pb * n);
+    L.off_pb2 = take(mixed ? 16 * n : 0);
+    L.off_va2 = take(pb * n);
+    L.off_vb2 = take(mixed ? 16 * n : 0);
+    L.off_force = take(pb * n);
+    L.off_rref = take(16 * n);
+    L.off_image = take(16 * n);
+    L.off_image2 = take(16 * n);
+    L.off_key = take(4 * n);
+    L.off_tmpidx = take(4 * n);
+    L.off_cellof = take(4 * n);
+    L.off_ccount = take(4 * (size_t)g.ncell);
+    L.off_ccursor = take(4 * (size_t)g.ncell);
+    L.off_cstart = take(4 * ((size_t)g.ncell + 1));
+    L.off_nbr = take(4 * n * (size_t)g.K);
+    L.off_nnbr = take(4 * n);
+    L.off_part_f = take(8 * 8 * (size_t)g.nblk_f);
+    L.off_part_i = take(8 * 4 * (size_t)g.nblk_i);
+    L.off_ring = take(sizeof(mdk::Obs) * (size_t)cap * g.R);
+    L.off_totals = take(sizeof(mdk::Obs) * g.R);
+    L.off_scale = take(8 * (size_t)g.R);
+    L.off_st_pos = take(24 * n);
+    L.off_st_vel = take(24 * n);
+    L.off_st_img = take(12 * n);
+    L.off_st_code = take(4 * n);
+    L.off_st_f = take(24 * n);
+    L.off_st_e = take(8 * n);
+    L.total = o;
+    return L;
+}
+
+const KernelSet &kernel_set(int prec)
+{
+    if (prec == MD_PREC_FP64)
+        return mdk::kernels_fp64();
+    if (prec == MD_PREC_FP32)
+        return mdk::kernels_fp32();
+    return mdk::kernels_mixed();
+}
+
+int force_index(int tpp)
+{
+    int k = 0;
+    while ((1 << k) < tpp)
+        ++k;
+    return k;
+}
+
+}  // namespace
+
+struct md_handle {
+    md_params p;
+    Geometry g;
+    Layout lay;
+    cudaStream_t s = nullptr;
+    char *ws = nullptr;
+    KArgs a;
+    const KernelSet *ks = nullptr;
+    int cap = 4096;
+    // pinned host staging
+    char *pin = nullptr;
+    size_t pin_bytes = 0;
+    cudaEvent_t ev_stage = nullptr;
+    // graph
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    // timing of the force kernel (use_graph = 0)
+    cudaEvent_t ev_f0 = nullptr, ev_f1 = nullptr;
+    double force_ms = 0.0;
+    int64_t force_launches = 0;
+    int64_t obs_read = 0;
+    std::string err;
+};
+
+namespace {
+
+int fail(md_handle *h, int code, const std::string &m)
+{
+    if (h)
+        h->err = m;
+    return code;
+}
+
+int cuda_fail(md_handle *h, cudaError_t e, const char *what)
+{
+    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    return fail(h, MD_E_CUDA, m);
+}
+
+#define CK(h, expr)                                   \
+    do {                                              \
+        cudaError_t e_ = (expr);                      \
+        if (e_ != cudaSuccess)                        \
+            return cuda_fail((h), e_, #expr);         \
+    } while (0)
+
+int launch(md_handle *h, const void *f, int grid, int block, const KArgs &a)
+{
+    if (grid <= 0)
+        return MD_OK;
+    void *pp[1] = {(void *)&a};
+    CK(h, cudaLaunchKernel(f, dim3((unsigned)grid), dim3((unsigned)block), pp, 0, h->s));
+    return MD_OK;
+}
+
+int grid_n(int64_t n, int per) { return (int)((n + per - 1) / per); }
+
+int launch_rebuild(md_handle *h)
+{
+    const KernelSet &k = *h->ks;
+    const KArgs &a = h->a;
+    int rc;
+    if ((rc = launch(h, k.bin, h->g.nblk_i, kIntBlock, a))) return rc;
+    if ((rc = launch(h, k.scan, 1, kScanBlock, a))) return rc;
+    if ((rc = launch(h, k.scatter, grid_n(h->g.n, kIntBlock), kIntBlock, a))) return rc;
+    if ((rc = launch(h, k.permute, grid_n(h->g.n, kIntBlock), kIntBlock, a))) return rc;
+    if ((rc = launch(h, k.copyback, grid_n(h->g.n, kIntBlock), kIntBlock, a))) return rc;
+    if ((rc = launch(h, k.nbuild, grid_n(h->g.n * 32, kNbBlock), kNbBlock, a))) return rc;
+    return MD_OK;
+}
+
+int launch_force(md_handle *h, int fsample)
+{
+    KArgs a = h->a;
+    a.fsample = fsample;
+    return launch(h, h->ks->force[force_index(h->g.tpp)], h->g.nblk_f, kForceBlock, a);
+}
+
+int launch_integrate(md_handle *h, int mode)
+{
+    KArgs a = h->a;
+    a.imode = mode;
+    a.use_cond = 0;
+    return launch(h, h->ks->integrate, h->g.nblk_i, kIntBlock, a);
+}
+
+// ---- graph construction ----
+int add_kernel(md_handle *h, cudaGraph_t g, cudaGraphNode_t *node, const cudaGraphNode_t *deps, size_t ndeps,
+               const void *f, int grid, int block, const KArgs &a)
+{
+    alignas(cudaGraphNodeParams) unsigned char np_buf[sizeof(cudaGraphNodeParams)] = {};
+    cudaGraphNodeParams &np = *reinterpret_cast<cudaGraphNodeParams *>(np_buf);
+    np.type = cudaGraphNodeTypeKernel;
+    np.kernel.func = (void *)f;
+    np.kernel.gridDim = dim3((unsigned)grid);
+    np.kernel.blockDim = dim3((unsigned)block);
+    np.kernel.sharedMemBytes = 0;
+    void *pp[1] = {(void *)&a};
+    np.kernel.kernelParams = pp;
+    CK(h, cudaGraphAddNode(node, g, deps, nullptr, ndeps, &np));
+    return MD_OK;
+}
+
+int add_rebuild_chain(md_handle *h, cudaGraph_t g)
+{
+    const KernelSet &k = *h->ks;
+    const KArgs &a = h->a;
+    struct { const void *f; int grid, block; } seq[6] = {
+        {k.bin, h->g.nblk_i, kIntBlock},
+        {k.scan, 1, kScanBlock},
+        {k.scatter, grid_n(h->g.n, kIntBlock), kIntBlock},
+        {k.permute, grid_n(h->g.n, kIntBlock), kIntBlock},
+        {k.copyback, grid_n(h->g.n, kIntBlock), kIntBlock},
+        {k.nbuild, grid_n(h->g.n * 32, kNbBlock), kNbBlock},
+    };
+    cudaGraphNode_t prev = nullptr;
+    for (int s = 0; s < 6; ++s) {
+        cudaGraphNode_t node;
+        int rc = add_kernel(h, g, &node, prev ? &prev : nullptr, prev ? 1 : 0, seq[s].f, seq[s].grid,
+                            seq[s].block, a);
+        if (rc)
+            return rc;
+        prev = node;
+    }
+    return MD_OK;
+}
+
+int add_conditional(md_handle *h, cudaGraph_t g, cudaGraphNode_t *node, cudaGraphNode_t dep,
+                    cudaGraphConditionalHandle c, cudaGraphConditionalNodeType type, cudaGraph_t *body)
+{
+    alignas(cudaGraphNodeParams) unsigned char np_buf[sizeof(cudaGraphNodeParams)] = {};
+    cudaGraphNodeParams &np = *reinterpret_cast<cudaGraphNodeParams *>(np_buf);
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = c;
+    np.conditional.type = type;
+    np.conditional.size = 1;
+    CK(h, cudaGraphAddNode(node, g, &dep, nullptr, 1, &np));
+    *body = np.conditional.phGraph_out[0];
+    return MD_OK;
+}
+
+int build_graph(md_handle *h)
+{
+    int rc;
+    cudaGraph_t g;
+    CK(h, cudaGraphCreate(&g, 0));
+    h->graph = g;
+    cudaGraphConditionalHandle c_loop, c_reb0;
+    CK(h, cudaGraphConditionalHandleCreate(&c_loop, g, 1, cudaGraphCondAssignDefault));
+    CK(h, cudaGraphConditionalHandleCreate(&c_reb0, g, 0, 0));
+
+    KArgs first = h->a;
+    first.imode = mdk::IM_FIRST;
+    first.use_cond = 1;
+    first.h_rebuild = c_reb0;
+    first.h_loop = c_loop;
+    cudaGraphNode_t n_first, n_if0, n_while;
+    if ((rc = add_kernel(h, g, &n_first, nullptr, 0, h->ks->integrate, h->g.nblk_i, kIntBlock, first)))
+        return rc;
+    cudaGraph_t body0;
+    if ((rc = add_conditional(h, g, &n_if0, n_first, c_reb0, cudaGraphCondTypeIf, &body0)))
+        return rc;
+    if ((rc = add_rebuild_chain(h, body0)))
+        return rc;
+    cudaGraph_t wbody;
+    if ((rc = add_conditional(h, g, &n_while, n_if0, c_loop, cudaGraphCondTypeWhile, &wbody)))
+        return rc;
+    cudaGraphConditionalHandle c_reb1;
+    CK(h, cudaGraphConditionalHandleCreate(&c_reb1, wbody, 0, 0));
+    KArgs fa = h->a;
+    fa.fsample = 0;
+    cudaGraphNode_t n_f, n_i, n_if1;
+    if ((rc = add_kernel(h, wbody, &n_f, nullptr, 0, h->ks->force[force_index(h->g.tpp)], h->g.nblk_f,
+                         kForceBlock, fa)))
+        return rc;
+    KArgs loop = h->a;
+    loop.imode = mdk::IM_LOOP;
+    loop.use_cond = 1;
+    loop.h_rebuild = c_reb1;
+    loop.h_loop = c_loop;
+    if ((rc = add_kernel(h, wbody, &n_i, &n_f, 1, h->ks->integrate, h->g.nblk_i, kIntBlock, loop)))
+        return rc;
+    cudaGraph_t body1;
+    if ((rc = add_conditional(h, wbody, &n_if1, n_i, c_reb1, cudaGraphCondTypeIf, &body1)))
+        return rc;
+    if ((rc = add_rebuild_chain(h, body1)))
+        return rc;
+    CK(h, cudaGraphInstantiate(&h->gexec, g, 0));
+    return MD_OK;
+}
+
+int stage_wait(md_handle *h)
+{
+    CK(h, cudaEventSynchronize(h->ev_stage));
+    return MD_OK;
+}
+
+int ensure_pinned(md_handle *h, size_t bytes)
+{
+    if (bytes <= h->pin_bytes)
+        return MD_OK;
+    int rc = stage_wait(h);
+    if (rc)
+        return rc;
+    CK(h, cudaStreamSynchronize(h->s));
+    if (h->pin)
+        cudaFreeHost(h->pin);
+    h->pin = nullptr;
+    h->pin_bytes = 0;
+    CK(h, cudaMallocHost((void **)&h->pin, bytes));
+    h->pin_bytes = bytes;
+    return MD_OK;
+}
+
+int read_ctl(md_handle *h, mdk::Ctl *out)
+{
+    int rc = ensure_pinned(h, sizeof(mdk::Ctl));
+    if (rc)
+        return rc;
+    if ((rc = stage_wait(h)))
+        return rc;
+    CK(h, cudaMemcpyAsync(h->pin, h->a.ctl, sizeof(mdk::Ctl), cudaMemcpyDeviceToHost, h->s));
+    CK(h, cudaStreamSynchronize(h->s));
+    memcpy(out, h->pin, sizeof(mdk::Ctl));
+    return MD_OK;
+}
+
+int status_code(unsigned st)
+{
+    if (st & mdk::ST_NONFINITE) return MD_E_NONFINITE;
+    if (st & mdk::ST_UNSTABLE) return MD_E_UNSTABLE;
+    if (st & mdk::ST_OVERFLOW) return MD_E_CAPACITY;
+    if (st & mdk::ST_TIMEOUT) return MD_E_TIMEOUT;
+    return MD_OK;
+}
+
+const char *status_message(int code)
+{
+    switch (code) {
+    case MD_E_NONFINITE: return "a position became non-finite; the step loop stopped";
+    case MD_E_UNSTABLE: return "a particle moved more than a quarter box in one step; the step loop stopped";
+    case MD_E_CAPACITY: return "a neighbour list exceeded neigh_capacity; the step loop stopped";
+    case MD_E_TIMEOUT: return "the device step loop exceeded its iteration bound";
+    default: return "";
+    }
+}
+
+// Synchronise, report (once) and clear a device status.
+int check_device(md_handle *h)
+{
+    mdk::Ctl c;
+    int rc = read_ctl(h, &c);
+    if (rc)
+        return rc;
+    const int code = status_code(c.status);
+    if (code != MD_OK) {
+        KArgs a = h->a;
+        if ((rc = launch(h, h->ks->reset, 1, 1, a)))
+            return rc;
+        CK(h, cudaStreamSynchronize(h->s));
+        return fail(h, code, status_message(code));
+    }
+    return MD_OK;
+}
+
+// Copy the caller's state into pinned staging, upload it, load it into the
+// working layout, rebuild, evaluate forces.
+int upload_state(md_handle *h, const int32_t *species, const double *pos, const double *vel,
+                 const int32_t *image)
+{
+    const size_t n = (size_t)h->g.n;
+    const size_t bytes = 24 * n + 24 * n + 12 * n + 4 * n;
+    int rc = ensure_pinned(h, bytes);
+    if (rc)
+        return rc;
+    if ((rc = stage_wait(h)))
+        return rc;
+    char *q = h->pin;
+    memcpy(q, pos, 24 * n);
+    if (vel)
+        memcpy(q + 24 * n, vel, 24 * n);
+    else
+        memset(q + 24 * n, 0, 24 * n);
+    if (image)
+        memcpy(q + 48 * n, image, 12 * n);
+    else
+        memset(q + 48 * n, 0, 12 * n);
+    memcpy(q + 60 * n, species, 4 * n);
+    CK(h, cudaMemcpyAsync(h->a.st_pos, q, 24 * n, cudaMemcpyHostToDevice, h->s));
+    CK(h, cudaMemcpyAsync(h->a.st_vel, q + 24 * n, 24 * n, cudaMemcpyHostToDevice, h->s));
+    CK(h, cudaMemcpyAsync(h->a.st_img, q + 48 * n, 12 * n, cudaMemcpyHostToDevice, h->s));
+    CK(h, cudaMemcpyAsync(h->a.st_code, q + 60 * n, 4 * n, cudaMemcpyHostToDevice, h->s));
+    CK(h, cudaEventRecord(h->ev_stage, h->s));
+    if ((rc = launch(h, h->ks->load, h->g.nblk_i, kIntBlock, h->a)))
+        return rc;
+    if ((rc = launch_rebuild(h)))
+        return rc;
+    return launch_force(h, 1);
+}
+
+}  // namespace
+
+extern "C" {
+
+int md_params_default(md_params *p)
+{
+    if (!p)
+        return MD_E_INVAL;
+    memset(p, 0, sizeof *p);
+    p->n_species = 1;
+    p->shift = 1;
+    for (int a = 0; a < 2; ++a) {
+        for (int b = 0; b < 2; ++b) {
+            p->eps[a][b] = 1.0;
+            p->sigma[a][b] = 1.0;
+            p->rcut[a][b] = 2.5;
+        }
+        p->mass[a] = 1.0;
+    }
+    p->dt = 0.005;
+    p->skin = 0.3;
+    p->precision = MD_PREC_MIXED;
+    p->sample_interval = 100;
+    p->use_graph = 1;
+    p->reorder = 1;
+    return MD_OK;
+}
+
+int md_workspace_size(const md_params *p, int32_t n_replicas, const int64_t *n_per_replica,
+                      const double *box, size_t *bytes)
+{
+    if (!bytes)
+        return MD_E_INVAL;
+    Geometry g;
+    std::string msg;
+    int rc = make_geometry(p, n_replicas, n_per_replica, box, g, msg);
+    if (rc)
+        return rc;
+    *bytes = make_layout(p, g).total;
+    return MD_OK;
+}
+
+static int create_impl(md_handle *h, const md_params *p, const int32_t *species, const double *pos,
+                       const double *vel, const int32_t *image, void *workspace, size_t workspace_bytes,
+                       void *cuda_stream)
+{
+    int rc;
+    h->p = *p;
+    h->lay = make_layout(p, h->g);
+    if (!species || !pos || !workspace || ((uintptr_t)workspace % kAlign) != 0)
+        return fail(h, MD_E_INVAL, "null array or workspace not 256-byte aligned");
+    if (workspace_bytes < h->lay.total)
+        return fail(h, MD_E_NOMEM, "workspace smaller than md_workspace_size()");
+    for (int64_t i = 0; i < h->g.n; ++i)
+        if (species[i] < 0 || species[i] >= p->n_species)
+            return fail(h, MD_E_INVAL, "species out of range");
+    h->s = (cudaStream_t)cuda_stream;
+    h->ws = (char *)workspace;
+    h->ks = &kernel_set(p->precision);
+    h->cap = p->obs_capacity > 0 ? p->obs_capacity : 4096;
+    const Geometry &g = h->g;
+    const Layout &L = h->lay;
+    KArgs &a = h->a;
+    memset(&a, 0, sizeof a);
+    char *w = h->ws;
+    a.n = (int)g.n;
+    a.nrep = g.R;
+    a.ncell = g.ncell;
+    a.K = g.K;
+    a.tpp = g.tpp;
+    a.si = p->sample_interval;
+    a.obs_cap = h->cap;
+    a.nblk_i = g.nblk_i;
+    a.nblk_f = g.nblk_f;
+    a.pa = w + L.off_pa; a.pb = w + L.off_pb; a.va = w + L.off_va; a.vb = w + L.off_vb;
+    a.pa2 = w + L.off_pa2; a.pb2 = w + L.off_pb2; a.va2 = w + L.off_va2; a.vb2 = w + L.off_vb2;
+    a.force = w + L.off_force;
+    a.rref = (float4 *)(w + L.off_rref);
+    a.image = (int4 *)(w + L.off_image);
+    a.image2 = (int4 *)(w + L.off_image2);
+    a.key = (int *)(w + L.off_key);
+    a.tmpidx = (int *)(w + L.off_tmpidx);
+    a.cellof = (int *)(w + L.off_cellof);
+    a.ccount = (int *)(w + L.off_ccount);
+    a.ccursor = (int *)(w + L.off_ccursor);
+    a.cstart = (int *)(w + L.off_cstart);
+    a.crank = (const int *)(w + L.off_crank);
+    a.cxyz = (const int4 *)(w + L.off_cxyz);
+    a.nbr = (int *)(w + L.off_nbr);
+    a.nnbr = (int *)(w + L.off_nnbr);
+    a.blk_i = (const int4 *)(w + L.off_blk_i);
+    a.blk_f = (const int4 *)(w + L.off_blk_f);
+    a.part_f = (double *)(w + L.off_part_f);
+    a.part_i = (double *)(w + L.off_part_i);
+    a.ring = (mdk::Obs *)(w + L.off_ring);
+    a.totals = (mdk::Obs *)(w + L.off_totals);
+    a.ctl = (mdk::Ctl *)(w + L.off_ctl);
+    a.rep = (const mdk::Rep *)(w + L.off_rep);
+    a.st_pos = (double *)(w + L.off_st_pos);
+    a.st_vel = (double *)(w + L.off_st_vel);
+    a.st_img = (int *)(w + L.off_st_img);
+    a.st_code = (int *)(w + L.off_st_code);
+    a.st_f = (double *)(w + L.off_st_f);
+    a.st_e = (double *)(w + L.off_st_e);
+    a.scale = (double *)(w + L.off_scale);
+    // pair table (Sec. 3 potential, Sec. 5 parameters)
+    for (int x = 0; x < 2; ++x)
+        for (int y = 0; y < 2; ++y) {
+            const int k = x * 2 + y;
+            const int xs = std::min(x, p->n_species - 1), ys = std::min(y, p->n_species - 1);
+            const double eps = p->eps[xs][ys], sig = p->sigma[xs][ys], rc = p->rcut[xs][ys];
+            const double sr6 = std::pow(sig / rc, 6.0);
+            const double shift = p->shift ? 4.0 * eps * (sr6 * sr6 - sr6) : 0.0;
+            const double rl = rc + p->skin + (double)mdk::kListMargin;
+            a.tab.rc2d[k] = rc * rc;
+            a.tab.rl2d[k] = rl * rl;
+            a.tab.sig2d[k] = sig * sig;
+            a.tab.eps4d[k] = 4.0 * eps;
+            a.tab.eps48d[k] = 48.0 * eps;
+            a.tab.shiftd[k] = shift;
+            a.tab.rc2[k] = (float)(rc * rc);
+            a.tab.rl2[k] = (float)(rl * rl);
+            a.tab.sig2[k] = (float)(sig * sig);
+            a.tab.eps4[k] = (float)(4.0 * eps);
+            a.tab.eps48[k] = (float)(48.0 * eps);
+            a.tab.shift[k] = (float)shift;
+        }
+    for (int s = 0; s < 2; ++s) {
+        const int ss = std::min(s, p->n_species - 1);
+        const double m = p->mass[ss];
+        const double hk = 0.5 * p->dt / m;
+        a.mass[s] = m;
+        a.hdtm[s] = hk;
+        a.hdtm_hi[s] = (float)hk;
+        a.hdtm_lo[s] = (float)(hk - (double)(float)hk);
+    }
+    a.dt = p->dt;
+    a.dt_hi = (float)p->dt;
+    a.dt_lo = (float)(p->dt - (double)(float)p->dt);
+    const double thr = std::max(0.5 * p->skin - (double)mdk::kDispMargin, 0.0);
+    a.disp_thr2 = (float)(thr * thr);
+    if (a.hdtm_hi[0] == 0.0f)
+        return fail(h, MD_E_INVAL, "dt / (2 m) underflows single precision");
+
+    // pinned staging, events
+    CK(h, cudaEventCreateWithFlags(&h->ev_stage, cudaEventDisableTiming));
+    CK(h, cudaEventCreate(&h->ev_f0));
+    CK(h, cudaEventCreate(&h->ev_f1));
+    CK(h, cudaEventRecord(h->ev_stage, h->s));
+    size_t tbytes = sizeof(mdk::Rep) * g.R + sizeof(int4) * (g.nblk_i + g.nblk_f) +
+                    sizeof(int) * g.ncell + sizeof(int4) * g.ncell;
+    size_t sbytes = 64 * (size_t)g.n;
+    if ((rc = ensure_pinned(h, std::max(tbytes, sbytes) + 4096)))
+        return rc;
+    // tables
+    {
+        char *q = h->pin;
+        auto put = [&](size_t off, const void *src, size_t bytes) -> int {
+            memcpy(q, src, bytes);
+            cudaError_t e = cudaMemcpyAsync(w + off, q, bytes, cudaMemcpyHostToDevice, h->s);
+            q += align_up(bytes);
+            return e == cudaSuccess ? MD_OK : cuda_fail(h, e, "table upload");
+        };
+        if ((rc = put(L.off_rep, g.rep.data(), sizeof(mdk::Rep) * g.R)) ||
+            (rc = put(L.off_blk_i, g.blk_i.data(), sizeof(int4) * g.nblk_i)) ||
+            (rc = put(L.off_blk_f, g.blk_f.data(), sizeof(int4) * g.nblk_f)) ||
+            (rc = put(L.off_crank, g.crank.data(), sizeof(int) * g.ncell)) ||
+            (rc = put(L.off_cxyz, g.cxyz.data(), sizeof(int4) * g.ncell)))
+            return rc;
+        cudaError_t e = cudaMemsetAsync(a.ctl, 0, sizeof(mdk::Ctl), h->s);
+        if (e == cudaSuccess)
+            e = cudaMemsetAsync(a.ccount, 0, 4 * (size_t)g.ncell, h->s);
+        if (e == cudaSuccess)
+            e = cudaEventRecord(h->ev_stage, h->s);
+        if (e != cudaSuccess)
+            return cuda_fail(h, e, "initialisation");
+    }
+    if ((rc = upload_state(h, species, pos, vel, image)) || (rc = launch_integrate(h, mdk::IM_SAMPLE)))
+        return rc;
+    return check_device(h);
+}
+
+int md_create(md_handle **out, const md_params *p, int32_t n_replicas, const int64_t *n_per_replica,
+              const double *box, const int32_t *species, const double *pos, const double *vel,
+              const int32_t *image, void *workspace, size_t workspace_bytes, void *cuda_stream)
+{
+    if (!out)
+        return MD_E_INVAL;
+    *out = nullptr;
+    md_handle *h = new (std::nothrow) md_handle();
+    if (!h)
+        return MD_E_NOMEM;
+    std::string msg;
+    int rc = make_geometry(p, n_replicas, n_per_replica, box, h->g, msg);
+    if (rc == MD_OK)
+        rc = create_impl(h, p, species, pos, vel, image, workspace, workspace_bytes, cuda_stream);
+    if (rc != MD_OK) {
+        md_destroy(h);
+        return rc;
+    }
+    *out = h;
+    return MD_OK;
+}
+
+int md_step(md_handle *h, int64_t nsteps)
+{
+    if (!h)
+        return MD_E_INVAL;
+    if (nsteps < 1)
+        return fail(h, MD_E_INVAL, "nsteps must be >= 1");
+    int rc;
+    KArgs a = h->a;
+    a.nsteps = nsteps;
+    if ((rc = launch(h, h->ks->set_steps, 1, 1, a)))
+        return rc;
+    if (h->p.use_graph) {
+        if (!h->gexec && (rc = build_graph(h)))
+            return rc;
+        CK(h, cudaGraphLaunch(h->gexec, h->s));
+        return MD_OK;
+    }
+    if ((rc = launch_integrate(h, mdk::IM_FIRST)) || (rc = launch_rebuild(h)))
+        return rc;
+    for (int64_t k = 0; k < nsteps; ++k) {
+        CK(h, cudaEventRecord(h->ev_f0, h->s));
+        if ((rc = launch_force(h, 0)))
+            return rc;
+        CK(h, cudaEventRecord(h->ev_f1, h->s));
+        if ((rc = launch_integrate(h, mdk::IM_LOOP)) || (rc = launch_rebuild(h)))
+            return rc;
+        CK(h, cudaEventSynchronize(h->ev_f1));
+        float ms = 0.f;
+        CK(h, cudaEventElapsedTime(&ms, h->ev_f0, h->ev_f1));
+        h->force_ms += ms;
+        h->force_launches += 1;
+    }
+    return MD_OK;
+}
+
+int md_rescale_velocities(md_handle *h, const double *T_target)
+{
+    if (!h || !T_target)
+        return MD_E_INVAL;
+    int rc;
+    for (int r = 0; r < h->g.R; ++r)
+        if (!(T_target[r] >= 0.0))
+            return fail(h, MD_E_INVAL, "target temperatures must be >= 0");
+    if ((rc = stage_wait(h)))
+        return rc;
+    memcpy(h->pin, T_target, 8 * (size_t)h->g.R);
+    CK(h, cudaMemcpyAsync(h->a.scale, h->pin, 8 * (size_t)h->g.R, cudaMemcpyHostToDevice, h->s));
+    CK(h, cudaEventRecord(h->ev_stage, h->s));
+    if ((rc = launch_integrate(h, mdk::IM_KE)))
+        return rc;
+    return launch(h, h->ks->scale, h->g.nblk_i, kIntBlock, h->a);
+}
+
+int md_compute_forces(md_handle *h, double *f, double *e, md_obs *totals)
+{
+    if (!h)
+        return MD_E_INVAL;
+    int rc;
+    const size_t n = (size_t)h->g.n;
+    if ((rc = launch(h, h->ks->mark_rebuild, 1, 1, h->a)) || (rc = launch_rebuild(h)) ||
+        (rc = launch_force(h, 1)) || (rc = launch_integrate(h, mdk::IM_TOTALS)) ||
+        (rc = launch(h, h->ks->expforce, grid_n(h->g.n, kIntBlock), kIntBlock, h->a)))
+        return rc;
+    if ((rc = check_device(h)))
+        return rc;
+    const size_t tb = sizeof(md_obs) * h->g.R;
+    if ((rc = ensure_pinned(h, 32 * n + tb + 512)))
+        return rc;
+    char *q = h->pin;
+    CK(h, cudaMemcpyAsync(q, h->a.st_f, 24 * n, cudaMemcpyDeviceToHost, h->s));
+    CK(h, cudaMemcpyAsync(q + 24 * n, h->a.st_e, 8 * n, cudaMemcpyDeviceToHost, h->s));
+    CK(h, cudaMemcpyAsync(q + 32 * n, h->a.totals, tb, cudaMemcpyDeviceToHost, h->s));
+    CK(h, cudaStreamSynchronize(h->s));
+    if (f)
+        memcpy(f, q, 24 * n);
+    if (e)
+        memcpy(e, q + 24 * n, 8 * n);
+    if (totals)
+        memcpy(totals, q + 32 * n, tb);
+    return MD_OK;
+}
+
+int md_observables(md_handle *h, md_obs *out, int32_t max_samples, int32_t *n_samples)
+{
+    if (!h || !n_samples || (max_samples > 0 && !out))
+        return MD_E_INVAL;
+    *n_samples = 0;
+    mdk::Ctl c;
+    int rc = read_ctl(h, &c);
+    if (rc)
+        return rc;
+    const int64_t avail = c.obs_count - h->obs_read;
+    int64_t m = std::min<int64_t>(avail, h->cap);
+    m = std::min<int64_t>(m, max_samples);
+    const int64_t first = c.obs_count - m;
+    const size_t rec = sizeof(md_obs) * h->g.R;
+    if (m > 0) {
+        if ((rc = ensure_pinned(h, rec * (size_t)m)))
+            return rc;
+        int64_t done = 0;
+        while (done < m) {
+            const int64_t slot = (first + done) % h->cap;
+            const int64_t cnt = std::min<int64_t>(m - done, h->cap - slot);
+            CK(h, cudaMemcpyAsync(h->pin + rec * done, (char *)h->a.ring + rec * slot, rec * cnt,
+                                  cudaMemcpyDeviceToHost, h->s));
+            done += cnt;
+        }
+        CK(h, cudaStreamSynchronize(h->s));
+        memcpy(out, h->pin, rec * (size_t)m);
+    }
+    h->obs_read = c.obs_count;
+    *n_samples = (int32_t)m;
+    const int code = status_code(c.status);
+    if (code != MD_OK)
+        return check_device(h);
+    return MD_OK;
+}
+
+int md_get_state(md_handle *h, double *pos, double *vel, int32_t *image)
+{
+    if (!h)
+        return MD_E_INVAL;
+    int rc;
+    const size_t n = (size_t)h->g.n;
+    if ((rc = launch(h, h->ks->getstate, grid_n(h->g.n, kIntBlock), kIntBlock, h->a)))
+        return rc;
+    if ((rc = ensure_pinned(h, 60 * n)) || (rc = stage_wait(h)))
+        return rc;
+    char *q = h->pin;
+    CK(h, cudaMemcpyAsync(q, h->a.st_pos, 24 * n, cudaMemcpyDeviceToHost, h->s));
+    CK(h, cudaMemcpyAsync(q + 24 * n, h->a.st_vel, 24 * n, cudaMemcpyDeviceToHost, h->s));
+    CK(h, cudaMemcpyAsync(q + 48 * n, h->a.st_img, 12 * n, cudaMemcpyDeviceToHost, h->s));
+    CK(h, cudaStreamSynchronize(h->s));
+    if (pos)
+        memcpy(pos, q, 24 * n);
+    if (vel)
+        memcpy(vel, q + 24 * n, 24 * n);
+    if (image)
+        memcpy(image, q + 48 * n, 12 * n);
+    return MD_OK;
+}
+
+int md_set_state(md_handle *h, const double *pos, const double *vel, const int32_t *image)
+{
+    if (!h || !pos || !vel)
+        return MD_E_INVAL;
+    int rc;
+    // species are kept: read them back from the working layout is not needed,
+    // the staging area still holds the codes uploaded at creation
+    const size_t n = (size_t)h->g.n;
+    if ((rc = ensure_pinned(h, 64 * n)) || (rc = stage_wait(h)))
+        return rc;
+    char *q = h->pin;
+    memcpy(q, pos, 24 * n);
+    memcpy(q + 24 * n, vel, 24 * n);
+    if (image)
+        memcpy(q + 48 * n, image, 12 * n);
+    else
+        memset(q + 48 * n, 0, 12 * n);
+    CK(h, cudaMemcpyAsync(h->a.st_pos, q, 24 * n, cudaMemcpyHostToDevice, h->s));
+    CK(h, cudaMemcpyAsync(h->a.st_vel, q + 24 * n, 24 * n, cudaMemcpyHostToDevice, h->s));
+    CK(h, cudaMemcpyAsync(h->a.st_img, q + 48 * n, 12 * n, cudaMemcpyHostToDevice, h->s));
+    CK(h, cudaEventRecord(h->ev_stage, h->s));
+    if ((rc = launch(h, h->ks->load, h->g.nblk_i, kIntBlock, h->a)) || (rc = launch_rebuild(h)))
+        return rc;
+    return launch_force(h, 1);
+}
+
+int md_get_neighbours(md_handle *h, int32_t *counts, int32_t *lists, int32_t kmax)
+{
+    if (!h || !counts || (lists && kmax < 1))
+        return MD_E_INVAL;
+    const size_t n = (size_t)h->g.n, K = (size_t)h->g.K;
+    int rc;
+    if ((rc = ensure_pinned(h, 4 * n * K + 4 * n + 16 * n + 256)) || (rc = stage_wait(h)))
+        return rc;
+    char *q = h->pin;
+    int *nn = (int *)q;
+    int4 *img = (int4 *)(q + align_up(4 * n));
+    int *nb = (int *)(q + align_up(4 * n) + align_up(16 * n));
+    CK(h, cudaMemcpyAsync(nn, h->a.nnbr, 4 * n, cudaMemcpyDeviceToHost, h->s));
+    CK(h, cudaMemcpyAsync(img, h->a.image, 16 * n, cudaMemcpyDeviceToHost, h->s));
+    if (lists)
+        CK(h, cudaMemcpyAsync(nb, h->a.nbr, 4 * n * K, cudaMemcpyDeviceToHost, h->s));
+    CK(h, cudaStreamSynchronize(h->s));
+    for (size_t s = 0; s < n; ++s) {
+        const int t = img[s].w;
+        counts[t] = nn[s];
+        if (lists) {
+            for (int k = 0; k < kmax; ++k)
+                lists[(size_t)t * kmax + k] = (k < nn[s] && (size_t)k < K) ? img[nb[s * K + k]].w : -1;
+        }
+    }
+    return MD_OK;
+}
+
+int md_info(md_handle *h, md_info_t *out)
+{
+    if (!h || !out)
+        return MD_E_INVAL;
+    mdk::Ctl c;
+    int rc = read_ctl(h, &c);
+    if (rc)
+        return rc;
+    memset(out, 0, sizeof *out);
+    out->n_total = h->g.n;
+    out->n_replicas = h->g.R;
+    out->neigh_capacity = h->g.K;
+    out->threads_per_particle = h->g.tpp;
+    out->cells_per_edge = h->g.rep[0].nc;
+    out->step = c.step;
+    out->rebuilds = c.rebuilds;
+    out->kernel_launches = c.n_force + c.n_integrate + c.n_rebuild_k + c.n_other;
+    out->max_neighbours = c.max_nbr;
+    out->status = status_code(c.status);
+    out->force_ms = h->force_ms;
+    out->force_launches = h->force_launches;
+    return MD_OK;
+}
+
+int md_sync(md_handle *h)
+{
+    if (!h)
+        return MD_E_INVAL;
+    return check_device(h);
+}
+
+int md_destroy(md_handle *h)
+{
+    if (!h)
+        return MD_E_INVAL;
+    if (h->ws)
+        cudaStreamSynchronize(h->s);
+    if (h->gexec)
+        cudaGraphExecDestroy(h->gexec);
+    if (h->graph)
+        cudaGraphDestroy(h->graph);
+    if (h->pin)
+        cudaFreeHost(h->pin);
+    if (h->ev_stage)
+        cudaEventDestroy(h->ev_stage);
+    if (h->ev_f0)
+        cudaEventDestroy(h->ev_f0);
+    if (h->ev_f1)
+        cudaEventDestroy(h->ev_f1);
+    delete h;
+    return MD_OK;
+}
+
+const char *md_last_error(const md_handle *h)
+{
+    if (!h)
+        return "null handle";
+    return h->err.c_str();
+}
+
+const char *md_status_string(int code)
+{
+    switch (code) {
+    case MD_OK: return "MD_OK";
+    case MD_E_INVAL: return "MD_E_INVAL";
+    case MD_E_NOMEM: return "MD_E_NOMEM";
+    case MD_E_CUDA: return "MD_E_CUDA";
+    case MD_E_NONFINITE: return "MD_E_NONFINITE";
+    case MD_E_UNSTABLE: return "MD_E_UNSTABLE";
+    case MD_E_TIMEOUT: return "MD_E_TIMEOUT";
+    case MD_E_CAPACITY: return "MD_E_CAPACITY";
+    default: return "MD_E_UNKNOWN";
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,166 @@
+// md_common.cuh -- device-side data structures and double-single arithmetic
+// shared by the kernels and the host API of the GB300 MD library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mdk {
+
+// precision modes (same values as MD_PREC_* in md.h)
+enum { FP64 = 0, MIXED = 1, FP32 = 2 };
+
+// device status bits
+enum { ST_OVERFLOW = 1u, ST_NONFINITE = 2u, ST_UNSTABLE = 4u, ST_TIMEOUT = 8u };
+
+// integrate-kernel modes
+enum {
+    IM_FIRST = 0,   // half kick + drift (start of md_step)
+    IM_LOOP = 1,    // half kick, sample, then half kick + drift unless this is the last step
+    IM_SAMPLE = 2,  // kinetic reductions only; record a ring-buffer sample
+    IM_TOTALS = 3,  // kinetic reductions only; write the per-replica totals record
+    IM_KE = 4       // kinetic energy only; turn targets in scale[] into rescale factors
+};
+
+// neighbour-list radius margin and rebuild-threshold margin (absolute, sigma units):
+// they absorb the single-precision rounding of distances and displacements.
+constexpr float kListMargin = 1e-4f;
+constexpr float kDispMargin = 1e-4f;
+
+// Control block in device memory, written by the kernels.
+struct Ctl {
+    unsigned int status;      // ST_* bits
+    unsigned int rebuild;     // 1: lists must be rebuilt before the next force evaluation
+    unsigned int maxdisp2;    // float bits of the largest squared displacement (this step)
+    unsigned int ticket;      // last-block counter of the integrate kernel
+    int max_nbr;              // largest list length seen at the last build
+    int pad0;
+    long long step;           // time index of the current positions
+    long long remaining;      // force evaluations left in the running md_step
+    long long budget;         // loop-iteration bound of the running md_step
+    long long rebuilds;
+    long long obs_count;      // samples written to the ring
+    long long n_force, n_integrate, n_rebuild_k, n_other;   // kernel executions
+    float last_maxdisp2;
+    float pad1;
+};
+
+struct Rep {                  // one independent system
+    int start, n;             // particle range (sorted order keeps replicas contiguous)
+    int cell0, nc;            // first global cell id, cells per edge (1 if fewer than 3 fit)
+    int bi0, bi1;             // integrate-kernel block range
+    int bf0, bf1;             // force-kernel block range
+    double L, invL, cscale;   // box edge, 1/L, nc/L
+    float Lhi, Llo, invLf, cscalef;
+    float grid, inv_grid;     // anchoring grid of MIXED positions (powers of two)
+    float pad[2];
+};
+
+struct PairTab {              // [a*2+b]
+    float rc2[4], rl2[4], sig2[4], eps4[4], eps48[4], shift[4];
+    double rc2d[4], rl2d[4], sig2d[4], eps4d[4], eps48d[4], shiftd[4];
+};
+
+struct Obs {                  // identical layout to md_obs
+    long long step;
+    double e_pot, e_kin, virial, w[6], p[3], max_disp;
+    long long rebuilds;
+};
+
+struct __align__(32) d4 { double x, y, z, w; };
+
+// Every kernel takes this one struct by value.
+struct KArgs {
+    int n, nrep, ncell, K, tpp, si, obs_cap, imode, use_cond, fsample;
+    int nblk_i, nblk_f;
+    void *pa, *pb, *va, *vb;          // state: MIXED pos hi/lo, vel hi/lo (float4);
+                                      // FP64 pos, vel (d4); FP32 pos, vel (float4)
+    void *pa2, *pb2, *va2, *vb2;      // permutation targets
+    void *force;                      // float4 (MIXED, FP32) or d4 (FP64): f.xyz, e_i in w
+    float4 *rref;                     // positions at the last list build
+    int4 *image, *image2;             // image counters, w = original index
+    int *key, *ccount, *cstart, *ccursor, *tmpidx, *cellof;
+    const int *crank;                 // [global linear cell] -> global sorted cell id
+    const int4 *cxyz;                 // [global sorted cell id] -> cx, cy, cz, replica
+    int *nbr, *nnbr;
+    const int4 *blk_i, *blk_f;        // per block: first particle, end, replica
+    double *part_f, *part_i;          // per-block partial sums [nblk][8], [nblk][4]
+    Obs *ring, *totals;
+    Ctl *ctl;
+    const Rep *rep;
+    double *st_pos, *st_vel, *st_f, *st_e;   // staging, original order
+    int *st_img, *st_code;
+    double *scale;                    // [nrep] targets in, factors out (rescale)
+    PairTab tab;
+    double hdtm[2], dt, mass[2];      // dt / (2 m_a), dt, m_a
+    long long nsteps;                 // for k_set_steps
+    float hdtm_hi[2], hdtm_lo[2], dt_hi, dt_lo;
+    float disp_thr2;
+    cudaGraphConditionalHandle h_loop, h_rebuild;
+};
+
+// ---------------------------------------------------------------------------
+// Double-single arithmetic (Sec. 2.4, Algorithm 1): a value is hi + lo with
+// |lo| <= ulp(hi)/2.  Sums use Knuth's branch-free two-sum, products the
+// exact fmaf residual; the intrinsics keep the compiler from contracting or
+// reassociating the error terms.
+// ---------------------------------------------------------------------------
+struct ds { float hi, lo; };
+
+__device__ __forceinline__ ds ds_from(float hi, float lo) { ds r; r.hi = hi; r.lo = lo; return r; }
+
+// renormalise s + e with |e| small against s (Dekker's fast two-sum)
+__device__ __forceinline__ ds ds_norm(float s, float e)
+{
+    float h = __fadd_rn(s, e);
+    return ds_from(h, __fsub_rn(e, __fsub_rn(h, s)));
+}
+
+// a + b, both double-single
+__device__ __forceinline__ ds ds_add(ds a, ds b)
+{
+    float s = __fadd_rn(a.hi, b.hi);
+    float bb = __fsub_rn(s, a.hi);                       // part of s that came from b
+    float err = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+    err = __fadd_rn(__fadd_rn(err, a.lo), b.lo);
+    return ds_norm(s, err);
+}
+
+// a * b for double-single a and single b
+__device__ __forceinline__ ds ds_mul_f(ds a, float b)
+{
+    float p = __fmul_rn(a.hi, b);
+    float e = __fmaf_rn(a.hi, b, -p);                    // exact rounding error of a.hi*b
+    e = __fmaf_rn(a.lo, b, e);
+    return ds_norm(p, e);
+}
+
+// a * b, both double-single
+__device__ __forceinline__ ds ds_mul(ds a, ds b)
+{
+    float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    return ds_norm(p, e);
+}
+
+__device__ __forceinline__ double ds_to_double(ds a) { return (double)a.hi + (double)a.lo; }
+
+__device__ __forceinline__ ds ds_from_double(double x)
+{
+    float hi = __double2float_rn(x);
+    return ds_from(hi, __double2float_rn(x - (double)hi));
+}
+
+// table of kernel entry addresses for one precision (one translation unit each)
+struct KernelSet {
+    const void *integrate, *force[6], *bin, *scan, *scatter, *permute, *copyback, *nbuild;
+    const void *load, *getstate, *expforce, *scale, *set_steps, *reset, *mark_rebuild;
+};
+
+const KernelSet &kernels_fp64();
+const KernelSet &kernels_mixed();
+const KernelSet &kernels_fp32();
+
+}  // namespace mdk

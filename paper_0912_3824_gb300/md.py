@@ -1,0 +1,329 @@
+"""Python binding of the C ABI in include/md.h (argument marshalling only).
+
+Every function below has the name of the C entry point it wraps and does no
+computation of its own: all simulation work runs in the CUDA library
+libmdgb300.so.  Importing this module raises if that library is missing -- there
+is no CPU fallback.  PyTorch supplies the device workspace and the CUDA stream.
+
+    from paper_0912_3824_gb300 import md, synth
+    s = synth.ka_mixture(n=65536)
+    sim = md.System.from_synth(s, dt=0.001, precision=md.MD_PREC_MIXED)
+    sim.step(1000)
+    obs = sim.observables()
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmdgb300.so")
+
+MD_OK, MD_E_INVAL, MD_E_NOMEM, MD_E_CUDA, MD_E_NONFINITE, MD_E_UNSTABLE, MD_E_TIMEOUT, MD_E_CAPACITY = range(8)
+MD_PREC_FP64, MD_PREC_MIXED, MD_PREC_FP32 = 0, 1, 2
+PRECISIONS = {"fp64": MD_PREC_FP64, "mixed": MD_PREC_MIXED, "fp32": MD_PREC_FP32}
+
+
+class md_params(C.Structure):
+    _fields_ = [("n_species", C.c_int32), ("shift", C.c_int32),
+                ("eps", (C.c_double * 2) * 2), ("sigma", (C.c_double * 2) * 2),
+                ("rcut", (C.c_double * 2) * 2), ("mass", C.c_double * 2),
+                ("dt", C.c_double), ("skin", C.c_double),
+                ("precision", C.c_int32), ("neigh_capacity", C.c_int32),
+                ("sample_interval", C.c_int32), ("obs_capacity", C.c_int32),
+                ("threads_per_particle", C.c_int32), ("use_graph", C.c_int32),
+                ("reorder", C.c_int32), ("reserved", C.c_int32 * 7)]
+
+
+class md_obs(C.Structure):
+    _fields_ = [("step", C.c_int64), ("e_pot", C.c_double), ("e_kin", C.c_double),
+                ("virial", C.c_double), ("w", C.c_double * 6), ("p", C.c_double * 3),
+                ("max_disp", C.c_double), ("rebuilds", C.c_int64)]
+
+
+class md_info_t(C.Structure):
+    _fields_ = [("n_total", C.c_int64), ("n_replicas", C.c_int32),
+                ("neigh_capacity", C.c_int32), ("threads_per_particle", C.c_int32),
+                ("cells_per_edge", C.c_int32), ("step", C.c_int64), ("rebuilds", C.c_int64),
+                ("kernel_launches", C.c_int64), ("max_neighbours", C.c_int32),
+                ("status", C.c_int32), ("force_ms", C.c_double), ("force_launches", C.c_int64)]
+
+
+OBS_DTYPE = np.dtype([("step", np.int64), ("e_pot", np.float64), ("e_kin", np.float64),
+                      ("virial", np.float64), ("w", np.float64, (6,)), ("p", np.float64, (3,)),
+                      ("max_disp", np.float64), ("rebuilds", np.int64)])
+assert OBS_DTYPE.itemsize == C.sizeof(md_obs)
+
+
+class MDError(RuntimeError):
+    def __init__(self, code: int, message: str):
+        super().__init__(f"{_status_name(code)}: {message}")
+        self.code = code
+
+
+def _load() -> C.CDLL:
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"CUDA library not built: {LIB_PATH} (run paper_0912_3824_gb300.build)")
+    lib = C.CDLL(LIB_PATH)
+    H = C.c_void_p
+    P = C.POINTER(md_params)
+    d = C.POINTER(C.c_double)
+    i32 = C.POINTER(C.c_int32)
+    i64 = C.POINTER(C.c_int64)
+    sig = {
+        "md_params_default": ([P], C.c_int),
+        "md_workspace_size": ([P, C.c_int32, i64, d, C.POINTER(C.c_size_t)], C.c_int),
+        "md_create": ([C.POINTER(H), P, C.c_int32, i64, d, i32, d, d, i32, C.c_void_p, C.c_size_t,
+                       C.c_void_p], C.c_int),
+        "md_step": ([H, C.c_int64], C.c_int),
+        "md_rescale_velocities": ([H, d], C.c_int),
+        "md_compute_forces": ([H, d, d, C.POINTER(md_obs)], C.c_int),
+        "md_observables": ([H, C.POINTER(md_obs), C.c_int32, i32], C.c_int),
+        "md_get_state": ([H, d, d, i32], C.c_int),
+        "md_set_state": ([H, d, d, i32], C.c_int),
+        "md_get_neighbours": ([H, i32, i32, C.c_int32], C.c_int),
+        "md_info": ([H, C.POINTER(md_info_t)], C.c_int),
+        "md_sync": ([H], C.c_int),
+        "md_destroy": ([H], C.c_int),
+        "md_last_error": ([H], C.c_char_p),
+        "md_status_string": ([C.c_int], C.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    return lib
+
+
+_lib = _load()
+EXPORTED = ("md_params_default", "md_workspace_size", "md_create", "md_step",
+            "md_rescale_velocities", "md_compute_forces", "md_observables", "md_get_state",
+            "md_set_state", "md_get_neighbours", "md_info", "md_sync", "md_destroy",
+            "md_last_error", "md_status_string")
+
+
+def _status_name(code: int) -> str:
+    return _lib.md_status_string(code).decode()
+
+
+def _check(rc: int, h=None):
+    if rc != MD_OK:
+        msg = _lib.md_last_error(h).decode() if h else ""
+        raise MDError(rc, msg)
+
+
+def _dptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double)) if a is not None else None
+
+
+def _iptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_int32)) if a is not None else None
+
+
+def _f64(a, shape):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64).reshape(shape))
+
+
+def _i32(a, shape):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.int32).reshape(shape))
+
+
+# ---------------------------------------------------------------------------
+# one Python function per C entry point
+# ---------------------------------------------------------------------------
+def md_params_default() -> md_params:
+    p = md_params()
+    _check(_lib.md_params_default(C.byref(p)))
+    return p
+
+
+def md_workspace_size(p: md_params, n_per_replica, box) -> int:
+    n = np.ascontiguousarray(n_per_replica, dtype=np.int64)
+    b = np.ascontiguousarray(box, dtype=np.float64)
+    out = C.c_size_t()
+    _check(_lib.md_workspace_size(C.byref(p), len(n), n.ctypes.data_as(C.POINTER(C.c_int64)),
+                                  _dptr(b), C.byref(out)))
+    return out.value
+
+
+def md_create(p: md_params, n_per_replica, box, species, pos, vel, image, workspace_ptr: int,
+              workspace_bytes: int, stream_ptr: int):
+    n = np.ascontiguousarray(n_per_replica, dtype=np.int64)
+    b = np.ascontiguousarray(box, dtype=np.float64)
+    ntot = int(n.sum())
+    sp = _i32(species, (ntot,))
+    ps = _f64(pos, (ntot, 3))
+    vs = _f64(vel, (ntot, 3))
+    im = _i32(image, (ntot, 3)) if image is not None else None
+    h = C.c_void_p()
+    rc = _lib.md_create(C.byref(h), C.byref(p), len(n), n.ctypes.data_as(C.POINTER(C.c_int64)),
+                        _dptr(b), _iptr(sp), _dptr(ps), _dptr(vs), _iptr(im),
+                        C.c_void_p(workspace_ptr), workspace_bytes, C.c_void_p(stream_ptr))
+    _check(rc)
+    return h
+
+
+def md_step(h, nsteps: int):
+    _check(_lib.md_step(h, int(nsteps)), h)
+
+
+def md_rescale_velocities(h, T_target):
+    t = np.ascontiguousarray(T_target, dtype=np.float64)
+    _check(_lib.md_rescale_velocities(h, _dptr(t)), h)
+
+
+def md_compute_forces(h, n_total: int, n_replicas: int):
+    f = np.empty((n_total, 3))
+    e = np.empty(n_total)
+    tot = (md_obs * n_replicas)()
+    _check(_lib.md_compute_forces(h, _dptr(f), _dptr(e), tot), h)
+    return f, e, np.frombuffer(tot, dtype=OBS_DTYPE).copy()
+
+
+def md_observables(h, n_replicas: int, max_samples: int = 1 << 16):
+    buf = (md_obs * (max_samples * n_replicas))()
+    n = C.c_int32()
+    _check(_lib.md_observables(h, buf, max_samples, C.byref(n)), h)
+    arr = np.frombuffer(buf, dtype=OBS_DTYPE)[: n.value * n_replicas].copy()
+    return arr.reshape(n.value, n_replicas)
+
+
+def md_get_state(h, n_total: int):
+    pos = np.empty((n_total, 3))
+    vel = np.empty((n_total, 3))
+    img = np.empty((n_total, 3), dtype=np.int32)
+    _check(_lib.md_get_state(h, _dptr(pos), _dptr(vel), _iptr(img)), h)
+    return pos, vel, img
+
+
+def md_set_state(h, pos, vel, image=None):
+    n = np.asarray(pos).size // 3
+    ps = _f64(pos, (n, 3))
+    vs = _f64(vel, (n, 3))
+    im = _i32(image, (n, 3)) if image is not None else None
+    _check(_lib.md_set_state(h, _dptr(ps), _dptr(vs), _iptr(im)), h)
+
+
+def md_get_neighbours(h, n_total: int, kmax: int):
+    counts = np.empty(n_total, dtype=np.int32)
+    lists = np.empty((n_total, kmax), dtype=np.int32)
+    _check(_lib.md_get_neighbours(h, _iptr(counts), _iptr(lists), kmax), h)
+    return counts, lists
+
+
+def md_info(h) -> dict:
+    out = md_info_t()
+    _check(_lib.md_info(h, C.byref(out)), h)
+    return {k: getattr(out, k) for k, _ in md_info_t._fields_}
+
+
+def md_sync(h) -> int:
+    """Returns the pending device status code (does not raise)."""
+    return _lib.md_sync(h)
+
+
+def md_destroy(h):
+    _check(_lib.md_destroy(h))
+
+
+def md_last_error(h) -> str:
+    return _lib.md_last_error(h).decode()
+
+
+# ---------------------------------------------------------------------------
+# convenience: parameters from the input generator's dictionaries, and a
+# handle that owns its torch workspace
+# ---------------------------------------------------------------------------
+def make_params(pot: dict, dt: float, skin: float = 0.3, precision: int = MD_PREC_MIXED,
+                sample_interval: int = 100, neigh_capacity: int = 0, threads_per_particle: int = 0,
+                use_graph: bool = True, reorder: bool = True, obs_capacity: int = 0) -> md_params:
+    p = md_params_default()
+    p.n_species = int(pot["n_species"])
+    p.shift = 1 if pot.get("shift", True) else 0
+    for a in range(2):
+        for b in range(2):
+            p.eps[a][b] = float(pot["eps"][a][b])
+            p.sigma[a][b] = float(pot["sigma"][a][b])
+            p.rcut[a][b] = float(pot["rcut"][a][b])
+        p.mass[a] = float(pot["mass"][a])
+    p.dt = float(dt)
+    p.skin = float(skin)
+    p.precision = int(precision)
+    p.sample_interval = int(sample_interval)
+    p.neigh_capacity = int(neigh_capacity)
+    p.threads_per_particle = int(threads_per_particle)
+    p.use_graph = 1 if use_graph else 0
+    p.reorder = 1 if reorder else 0
+    p.obs_capacity = int(obs_capacity)
+    return p
+
+
+class System:
+    """A handle plus the torch-owned device workspace it lives in."""
+
+    def __init__(self, params: md_params, n_per_replica, box, species, pos, vel, image=None,
+                 device: str = "cuda", stream=None):
+        import torch
+        self.params = params
+        self.n_per_replica = np.ascontiguousarray(n_per_replica, dtype=np.int64)
+        self.box = np.ascontiguousarray(box, dtype=np.float64)
+        self.n = int(self.n_per_replica.sum())
+        self.nrep = len(self.n_per_replica)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(device)
+        nbytes = md_workspace_size(params, self.n_per_replica, self.box)
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=device)
+        base = self.workspace.data_ptr()
+        self._ws_ptr = (base + 255) // 256 * 256
+        self.workspace_bytes = nbytes
+        self.h = md_create(params, self.n_per_replica, self.box, species, pos, vel, image,
+                           self._ws_ptr, nbytes, self.stream.cuda_stream)
+
+    @classmethod
+    def from_synth(cls, sysm, dt: float, **kw):
+        device = kw.pop("device", "cuda")
+        stream = kw.pop("stream", None)
+        p = make_params(sysm.params, dt, **kw)
+        return cls(p, [sysm.n], [sysm.box], sysm.species, sysm.pos, sysm.vel, sysm.image,
+                   device=device, stream=stream)
+
+    def step(self, n: int):
+        md_step(self.h, n)
+
+    def rescale(self, temperature):
+        t = np.broadcast_to(np.asarray(temperature, dtype=np.float64), (self.nrep,))
+        md_rescale_velocities(self.h, t)
+
+    def forces(self):
+        return md_compute_forces(self.h, self.n, self.nrep)
+
+    def observables(self, max_samples: int = 1 << 16):
+        return md_observables(self.h, self.nrep, max_samples)
+
+    def get_state(self):
+        return md_get_state(self.h, self.n)
+
+    def set_state(self, pos, vel, image=None):
+        md_set_state(self.h, pos, vel, image)
+
+    def neighbours(self, kmax: int | None = None):
+        k = kmax if kmax is not None else self.info()["neigh_capacity"]
+        return md_get_neighbours(self.h, self.n, k)
+
+    def info(self) -> dict:
+        return md_info(self.h)
+
+    def sync(self) -> int:
+        return md_sync(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            md_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,287 @@
+"""GPU parity: the CUDA path against the FP64 CPU oracle, through the C ABI.
+
+Tolerances (per call, identical configurations):
+  forces       max_i |F_gpu - F_ref| / rms|F_ref|   <= 1e-12 (FP64), 1e-5 (MIXED)
+  E_pot        |E_gpu - E_ref| / |E_ref|             <= 1e-13 (FP64), 1e-6 (MIXED)
+  e_i          max_i |e_gpu - e_ref| / rms|e_ref|    <= 1e-12 (FP64), 1e-5 (MIXED)
+FP32 (positions themselves single precision) is compared with the oracle
+evaluated at the single-precision positions it actually holds; its remaining
+error is the rounding of a pair separation across the periodic boundary, at
+most ulp(L)/2 per component, so it gets 2e-4 on forces and 1e-5 on E_pot.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_0912_3824_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL_F = {"fp64": 1e-12, "mixed": 1e-5, "fp32": 2e-4}
+TOL_E = {"fp64": 1e-13, "mixed": 1e-6, "fp32": 1e-5}
+
+
+@pytest.fixture(scope="module")
+def md():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_0912_3824_gb300 import build
+    build.build()
+    from paper_0912_3824_gb300 import md as m
+    return m
+
+
+def _system(kind, n, seed=3, amp=0.1, temperature=None):
+    if kind == "lj":
+        s = synth.make_system(n, 0.8442, temperature or 0.722, seed, synth.lj_params())
+    else:
+        s = synth.make_system(n, 1.2, temperature or 0.7, seed, synth.ka_params())
+    return synth.perturb(s, amp, seed + 100) if amp > 0 else s
+
+
+def _sim(md, s, prec, dt=0.001, **kw):
+    return md.System.from_synth(s, dt=dt, precision=md.PRECISIONS[prec], **kw)
+
+
+def _ref_pos(s, prec):
+    if prec == "fp32":
+        return s.pos.astype(np.float32).astype(np.float64)
+    return s.pos
+
+
+def _ferr(f, ref):
+    return np.abs(f - ref).max() / np.sqrt((ref ** 2).sum(axis=1).mean())
+
+
+CASES = [("lj", 864), ("ka", 1000), ("ka", 4000), ("ka", 500), ("lj", 2000)]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "fp32"])
+@pytest.mark.parametrize("kind,n", CASES)
+def test_forces_energy_virial_match_oracle(md, prec, kind, n):
+    s = _system(kind, n)
+    sim = _sim(md, s, prec)
+    f, e, tot = sim.forces()
+    fr, er, w7 = oracle.forces_cells(s.params, s.box, s.species, _ref_pos(s, prec))
+    assert _ferr(f, fr) <= TOL_F[prec]
+    assert abs(tot["e_pot"][0] - er.sum()) <= TOL_E[prec] * abs(er.sum())
+    assert np.abs(e - er).max() <= TOL_F[prec] * np.sqrt((er ** 2).mean())
+    assert abs(tot["virial"][0] - w7[0]) <= 10 * TOL_E[prec] * abs(w7[0]) + 1e-9
+    assert np.allclose(tot["w"][0], w7[1:], rtol=0, atol=10 * TOL_E[prec] * abs(w7[0]) + 1e-9)
+    ek, mom = oracle.kinetic(s.params, s.species, s.vel)
+    assert tot["e_kin"][0] == pytest.approx(ek, rel=1e-6 if prec == "fp32" else 1e-13)
+    sim.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_melted_liquid_forces(md, prec):
+    """A configuration taken from an oracle trajectory (fcc melted for 300 steps)."""
+    s = _system("ka", 2000, amp=0.0, temperature=1.5)
+    pos, vel, img, _, _ = oracle.vv_run(s.params, s.box, s.species, s.pos, s.vel, s.image, 0.002, 300)
+    s.pos, s.vel, s.image = pos, vel, img
+    sim = _sim(md, s, prec)
+    f, e, tot = sim.forces()
+    fr, er, _ = oracle.forces_cells(s.params, s.box, s.species, s.pos)
+    assert _ferr(f, fr) <= TOL_F[prec]
+    assert abs(tot["e_pot"][0] - er.sum()) <= TOL_E[prec] * abs(er.sum())
+    sim.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "fp32"])
+def test_neighbour_lists_contain_all_pairs_within_list_radius(md, prec):
+    s = _system("ka", 3000)
+    skin = 0.3
+    sim = _sim(md, s, prec)
+    counts, lists = sim.neighbours()
+    inner, inner_l = oracle.neighbours_brute(s.params, s.box, s.species, s.pos, skin - 1e-4, kmax=256)
+    outer, outer_l = oracle.neighbours_brute(s.params, s.box, s.species, s.pos, skin + 1e-3, kmax=256)
+    assert (counts >= inner).all() and (counts <= outer).all()
+    for i in range(0, s.n, 7):
+        got = set(lists[i, :counts[i]].tolist())
+        assert set(inner_l[i, :inner[i]].tolist()) <= got <= set(outer_l[i, :outer[i]].tolist())
+        assert len(got) == counts[i]       # no duplicates
+    sim.close()
+
+
+def _trajectory(md, s, prec, dt, nsteps, sample, **kw):
+    sim = _sim(md, s, prec, dt=dt, sample_interval=sample, **kw)
+    sim.step(nsteps)
+    assert sim.sync() == md.MD_OK
+    pos, vel, img = sim.get_state()
+    obs = sim.observables()
+    info = sim.info()
+    sim.close()
+    return pos, vel, img, obs[:, 0], info
+
+
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_fp64_trajectory_matches_oracle(md, use_graph):
+    """200 velocity-Verlet steps of the LJ fluid (several list rebuilds)."""
+    s = _system("lj", 864, amp=0.02)
+    pos, vel, img, obs, info = _trajectory(md, s, "fp64", 0.005, 200, 20, use_graph=use_graph)
+    rp, rv, ri, _, rec = oracle.vv_run(s.params, s.box, s.species, s.pos, s.vel, s.image, 0.005, 200,
+                                       sample=20)
+    assert info["rebuilds"] >= 3
+    assert np.abs((pos + img * s.box) - (rp + ri * s.box)).max() < 1e-9
+    assert np.abs(vel - rv).max() < 1e-8
+    assert (obs["step"] == rec["step"]).all()
+    assert np.allclose(obs["e_pot"], rec["e_pot"], rtol=1e-11)
+    assert np.allclose(obs["e_kin"], rec["e_kin"], rtol=1e-11)
+    assert np.abs(obs["p"]).max() < 1e-10
+
+
+def test_mixed_trajectory_close_to_oracle(md):
+    s = _system("ka", 2000, amp=0.02)
+    pos, vel, img, obs, info = _trajectory(md, s, "mixed", 0.001, 300, 50)
+    rp, rv, ri, _, rec = oracle.vv_run(s.params, s.box, s.species, s.pos, s.vel, s.image, 0.001, 300,
+                                       sample=50)
+    assert np.abs((pos + img * s.box) - (rp + ri * s.box)).max() < 1e-5
+    e_gpu = obs["e_pot"] + obs["e_kin"]
+    e_ref = rec["e_pot"] + rec["e_kin"]
+    assert np.allclose(e_gpu, e_ref, rtol=1e-6)
+    assert np.abs(obs["p"]).max() < 1e-6 * s.n
+
+
+def test_graph_and_stream_launches_agree_bitwise(md):
+    s = _system("ka", 3000, amp=0.05)
+    a = _trajectory(md, s, "mixed", 0.002, 150, 10, use_graph=True)
+    b = _trajectory(md, s, "mixed", 0.002, 150, 10, use_graph=False)
+    assert a[4]["rebuilds"] == b[4]["rebuilds"] >= 2
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2])
+    assert np.array_equal(a[3]["e_pot"], b[3]["e_pot"])
+
+
+def test_repeated_runs_are_deterministic(md):
+    s = _system("lj", 2000, amp=0.05)
+    a = _trajectory(md, s, "fp64", 0.005, 100, 10)
+    b = _trajectory(md, s, "fp64", 0.005, 100, 10)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_reorder_does_not_change_forces(md, prec):
+    s = _system("ka", 4000)
+    f1, _, t1 = _sim(md, s, prec, reorder=True).forces()
+    f2, _, t2 = _sim(md, s, prec, reorder=False).forces()
+    assert _ferr(f1, f2) <= TOL_F[prec]
+    assert t1["e_pot"][0] == pytest.approx(t2["e_pot"][0], rel=TOL_E[prec])
+
+
+@pytest.mark.parametrize("tpp", [1, 2, 4, 16, 32])
+def test_threads_per_particle_variants(md, tpp):
+    s = _system("ka", 1500)
+    f, _, tot = _sim(md, s, "mixed", threads_per_particle=tpp).forces()
+    fr, er, _ = oracle.forces_cells(s.params, s.box, s.species, s.pos)
+    assert _ferr(f, fr) <= TOL_F["mixed"]
+    assert abs(tot["e_pot"][0] - er.sum()) <= TOL_E["mixed"] * abs(er.sum())
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "fp32"])
+def test_state_roundtrip(md, prec):
+    s = _system("ka", 1000)
+    sim = _sim(md, s, prec)
+    pos, vel, img = sim.get_state()
+    unwrapped = pos + img * s.box
+    tol = {"fp64": 0.0, "mixed": 1e-12, "fp32": 4e-6}[prec]
+    assert np.abs(unwrapped - (s.pos + s.image * s.box)).max() <= tol
+    assert np.abs(vel - s.vel).max() <= {"fp64": 0.0, "mixed": 1e-12, "fp32": 1e-6}[prec]
+    assert (pos >= 0).all() and (pos < s.box).all()
+    # set_state with shifted positions, then read back
+    sim.set_state(s.pos + 0.5, -s.vel)
+    p2, v2, i2 = sim.get_state()
+    assert np.abs((p2 + i2 * s.box) - (s.pos + 0.5)).max() <= max(tol, 1e-12) * 10
+    assert np.abs(v2 + s.vel).max() <= {"fp64": 0.0, "mixed": 1e-12, "fp32": 1e-6}[prec]
+    sim.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_rescale_sets_temperature(md, prec):
+    s = _system("ka", 2000)
+    sim = _sim(md, s, prec)
+    sim.step(10)
+    sim.rescale(0.5)
+    _, vel, _ = sim.get_state()
+    ek, _ = oracle.kinetic(s.params, s.species, vel)
+    assert 2 * ek / (3 * s.n - 3) == pytest.approx(0.5, rel=1e-12 if prec == "fp64" else 1e-7)
+    sim.close()
+
+
+def test_replicas_match_independent_systems(md):
+    """Three replicas of different size and box in one handle: each one's forces
+    and trajectory equal those of the oracle run on it alone."""
+    systems = [_system("ka", n, seed=10 + k) for k, n in enumerate([700, 1500, 2222])]
+    sizes = [x.n for x in systems]
+    p = md.make_params(systems[0].params, 0.002, precision=md.MD_PREC_FP64, sample_interval=25)
+    sim = md.System(p, sizes, [x.box for x in systems],
+                    np.concatenate([x.species for x in systems]),
+                    np.concatenate([x.pos for x in systems]), np.concatenate([x.vel for x in systems]))
+    f, _, tot = sim.forces()
+    off = np.cumsum([0] + sizes)
+    for k, x in enumerate(systems):
+        fr, er, _ = oracle.forces_cells(x.params, x.box, x.species, x.pos)
+        assert _ferr(f[off[k]:off[k + 1]], fr) <= 1e-12
+        assert tot["e_pot"][k] == pytest.approx(er.sum(), rel=1e-13)
+    sim.step(100)
+    assert sim.sync() == md.MD_OK
+    pos, vel, img = sim.get_state()
+    obs = sim.observables()
+    for k, x in enumerate(systems):
+        rp, rv, ri, _, rec = oracle.vv_run(x.params, x.box, x.species, x.pos, x.vel, x.image, 0.002, 100,
+                                           sample=25)
+        sl = slice(off[k], off[k + 1])
+        assert np.abs((pos[sl] + img[sl] * x.box) - (rp + ri * x.box)).max() < 1e-9
+        assert np.allclose(obs[:, k]["e_pot"], rec["e_pot"], rtol=1e-11)
+    sim.close()
+
+
+def test_momentum_conserved_over_long_mixed_run(md):
+    s = _system("ka", 4000, amp=0.0, temperature=1.0)
+    sim = _sim(md, s, "mixed", dt=0.002, sample_interval=500)
+    sim.step(5000)
+    assert sim.sync() == md.MD_OK
+    obs = sim.observables()[:, 0]
+    assert np.abs(obs["p"]).max() < 1e-7 * s.n
+    e = obs["e_pot"] + obs["e_kin"]
+    assert np.abs(e[2:] - e[2]).max() < 2e-4 * abs(e[2])
+    sim.close()
+
+
+def test_capacity_overflow_is_reported(md):
+    s = _system("ka", 1000)
+    with pytest.raises(md.MDError) as ei:
+        _sim(md, s, "mixed", neigh_capacity=16)
+    assert ei.value.code == md.MD_E_CAPACITY
+
+
+def test_instability_is_reported_and_state_kept(md):
+    s = _system("lj", 864)
+    sim = _sim(md, s, "fp64", dt=50.0)
+    sim.step(5)
+    assert sim.sync() == md.MD_E_UNSTABLE
+    assert sim.sync() == md.MD_OK          # reported once
+    info = sim.info()
+    assert info["step"] <= 1
+    sim.close()
+
+
+def test_full_size_sampled_parity_ka65536(md):
+    """The benchmark's system (KA, N = 65536, mixed, default launch shape):
+    after 200 graph-driven steps, forces on 256 sampled particles equal the
+    oracle's one-by-one brute-force sums; Newton's third law holds for the
+    total; E_pot equals the oracle cell-list sum."""
+    s = synth.ka_mixture(n=65536, temperature=0.7, seed=5)
+    sim = _sim(md, s, "mixed", dt=0.001, sample_interval=100)
+    sim.step(200)
+    assert sim.sync() == md.MD_OK
+    pos, vel, img = sim.get_state()
+    f, e, tot = sim.forces()
+    idx = np.random.default_rng(0).choice(s.n, 256, replace=False)
+    fr, er = oracle.force_on(s.params, s.box, s.species, pos, idx)
+    rms = np.sqrt((f ** 2).sum(axis=1).mean())
+    assert np.abs(f[idx] - fr).max() <= TOL_F["mixed"] * rms
+    assert np.abs(e[idx] - er).max() <= TOL_F["mixed"] * np.sqrt((e ** 2).mean())
+    assert np.abs(f.sum(axis=0)).max() < 1e-3 * rms
+    _, ec, _ = oracle.forces_cells(s.params, s.box, s.species, pos)
+    assert abs(tot["e_pot"][0] - ec.sum()) <= TOL_E["mixed"] * abs(ec.sum())
+    sim.close()

@@ -336,3 +336,13 @@ def test_dimer_period_scales_with_sqrt_mass():
               for k in range(len(xs) - 1) if xs[k] > 0 >= xs[k + 1]]
         periods.append(np.diff(zc).mean())
     assert periods[1] / periods[0] == pytest.approx(math.sqrt(2.0), rel=2e-3)
+
+
+def test_single_particle_force_matches_full_sum():
+    p = synth.ka_params()
+    s = _liquid(400, p, 1.2, seed=71)
+    f, e, _ = oracle.forces_brute(p, s.box, s.species, s.pos)
+    idx = [0, 5, 17, 399]
+    f1, e1 = oracle.force_on(p, s.box, s.species, s.pos, idx)
+    assert np.allclose(f1, f[idx], rtol=0, atol=1e-12 * np.abs(f).max())
+    assert np.allclose(e1, e[idx], rtol=1e-13, atol=1e-14)

@@ -1,0 +1,407 @@
+"""Benchmark: particle-steps/s of the Kob-Andersen MD step on GB300.
+
+Workload: Kob-Andersen 80:20 mixture (Sec. 5 parameters), N = 65536,
+density 1.2, dt = 0.001, truncated-and-shifted at 2.5 sigma_ab, skin 0.3,
+mixed precision (FP32 pair forces, double-single positions/velocities and
+integration, compensated force summation, FP64 reductions).  Synthetic input:
+seeded fcc lattice, melted at T = 2 and quenched to T = 0.5 by velocity
+rescaling (4000 steps, untimed), then timed in NVE.
+
+One timed iteration ("step" of this script) = md_step(1000): 1000 MD steps
+with every neighbour-list rebuild, reorder and per-step reduction, executed
+as one CUDA graph.  The L2 cache is flushed (256 MB write) between timed
+iterations; within one the state stays on chip, as in a continuous run.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+With --gpus N > 1 (launched by torch.distributed.run) every rank advances its
+own independent replica (no data-path collective): weak scaling, "replicas
+only".  --impl reference times the FP64 CPU oracle on the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-steps/s at KA N=65536 (mixed vs FP64 on GB300) at stated energy drift/step"
+UNIT = "particle-steps/s"
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=65536)
+    ap.add_argument("--inner", type=int, default=1000, help="MD steps per timed iteration")
+    ap.add_argument("--precision", choices=["mixed", "fp64", "fp32"], default="mixed")
+    ap.add_argument("--no-extras", action="store_true", help="skip fp64 / e2e / cpu legs")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="plain stream launches instead of the CUDA graph (for per-kernel profiling)")
+    ap.add_argument("--tpp", type=int, default=0, help="force-kernel threads per particle (0 = auto)")
+    return ap.parse_args(argv)
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def aggregate(work_per_rank, seconds_per_rank):
+    """Whole-job throughput: all ranks' work over the slowest rank's time."""
+    t = max(seconds_per_rank)
+    return (sum(work_per_rank) / t if t > 0 else 0.0), t
+
+
+def allgather_floats(values, world):
+    """Gather a list of floats from every rank (identity when world == 1)."""
+    if world == 1:
+        return [list(values)]
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor(values, dtype=torch.float64, device=dev)
+    out = [torch.zeros_like(t) for _ in range(world)]
+    dist.all_gather(out, t)
+    return [o.cpu().tolist() for o in out]
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if f[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except OSError:
+        return None
+
+
+# Algorithmic FP32 work of the mixed force kernel (flops, FMA = 2), per entry of
+# a particle's list and per pair inside the cutoff; counted from the method:
+# separation from anchored double-single coordinates 3 x (sub, mul, rint, fma,
+# sub, fma, add) = 27, r^2 = 5, cutoff test = 1; inside the cutoff: reciprocal
+# 1, (sigma^2/r^2)^3 = 3, force factor 4, three products with the separation 3,
+# Kahan accumulation 3 x 4.
+FLOP_PER_ENTRY = 33
+FLOP_PER_PAIR = 23
+# per particle and step, the double-single velocity-Verlet update fused into
+# the same kernel: two half kicks 3 x 2 x (product 8 + sum 11), drift
+# 3 x (product 10 + sum 11 + re-anchor 6), displacement 15
+FLOP_PER_UPDATE = 210
+
+
+def list_statistics(sim, params):
+    """Mean list length and mean number of pairs inside the cutoff, from the
+    current lists and positions (host-side numpy)."""
+    pos, _, _ = sim.get_state()
+    counts, lists = sim.neighbours()
+    L = sim.box[0]
+    n = len(counts)
+    species = sim.species
+    rc = np.asarray(params["rcut"])
+    rows = np.repeat(np.arange(n), counts)
+    cols = lists[np.arange(lists.shape[1])[None, :] < counts[:, None]]
+    d = pos[rows] - pos[cols]
+    d -= L * np.round(d / L)
+    r2 = (d * d).sum(1)
+    inside = r2 < rc[species[rows], species[cols]] ** 2
+    return counts.mean(), inside.sum() / n
+
+
+def prepare(md, synth, n, seed, precision, device, use_graph=True, tpp=0):
+    s = synth.ka_mixture(n=n, temperature=2.0, seed=seed)
+    sim = md.System.from_synth(s, dt=0.001, precision=md.PRECISIONS[precision], sample_interval=100,
+                               device=device, use_graph=use_graph, threads_per_particle=tpp)
+    for _ in range(20):          # melt at T = 2
+        sim.step(100)
+        sim.rescale(2.0)
+    for _ in range(20):          # quench to T = 0.5 by rescaling
+        sim.step(100)
+        sim.rescale(0.5)
+    assert sim.sync() == md.MD_OK
+    sim.observables()            # drop the preparation samples
+    return s, sim
+
+
+def time_chunks(torch, sim, nsteps_inner, k, flush, stream):
+    ms = []
+    for _ in range(k):
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.step(nsteps_inner)
+        e1.record(stream)
+        ms.append((e0, e1))
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in ms)
+
+
+def energy_drift(obs, n):
+    """Least-squares slope of the total energy per particle per step, relative
+    to |E/N|, over the recorded NVE samples."""
+    if len(obs) < 3:
+        return None, None
+    e = (obs["e_pot"] + obs["e_kin"]) / n
+    t = obs["step"].astype(np.float64)
+    slope = np.polyfit(t - t[0], e, 1)[0]
+    return float(slope / abs(e.mean())), float(np.abs(e - e[0]).max() / abs(e.mean()))
+
+
+def run_ours(args, rank, world, local):
+    import torch
+    from paper_0912_3824_gb300 import build as b
+    b.build()
+    from paper_0912_3824_gb300 import md, synth
+
+    torch.cuda.set_device(local)
+    device = f"cuda:{local}"
+    stream = torch.cuda.current_stream(device)
+    s, sim = prepare(md, synth, args.n, 5 + rank, args.precision, device,
+                     use_graph=not args.no_graph, tpp=args.tpp)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=device)
+
+    for _ in range(args.warmup):
+        flush.fill_(1)
+        sim.step(args.inner)
+    assert sim.sync() == md.MD_OK
+    sim.observables()
+    info0 = sim.info()
+    clocks = ClockSampler(local)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    total_ms = time_chunks(torch, sim, args.inner, args.steps, flush, stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if world > 1:
+        torch.distributed.barrier()
+    status = sim.sync()
+    info1 = sim.info()
+    obs = sim.observables()[:, 0]
+    drift, maxdev = energy_drift(obs, args.n)
+    work = float(args.n) * args.inner * args.steps
+    gathered = allgather_floats([work, total_ms / 1e3], world)
+    value, tmax = aggregate([g[0] for g in gathered], [g[1] for g in gathered])
+    launches = int(info1["kernel_launches"] - info0["kernel_launches"])
+    rebuilds = int(info1["rebuilds"] - info0["rebuilds"])
+
+    result = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": tmax * 1e3 / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"mixed": "f32 pair math, f32x2 (double-single) state", "fp64": "f64", "fp32": "f32"}[args.precision],
+        "data": "synthetic (seeded fcc lattice, melted and quenched on the GPU)",
+        "config": {"workload": f"Kob-Andersen 80:20, N={args.n} per GPU, rho=1.2, T=0.5 after quench, "
+                               f"dt=0.001, r_c=2.5 sigma_ab shifted, skin 0.3, NVE",
+                   "precision": args.precision, "md_steps_per_iteration": args.inner,
+                   "l2": "flushed (256 MB write) between timed iterations",
+                   "parallelism": f"replicas x{world} (no collective)",
+                   "threads_per_particle": info1["threads_per_particle"],
+                   "neigh_capacity": info1["neigh_capacity"]},
+        "clocks": clk, "gpu_launches": launches,
+        "md": {"rebuilds_in_timed_region": rebuilds, "status": md._status_name(status),
+               "energy_drift_per_step_rel": drift, "energy_max_rel_dev": maxdev,
+               "samples": int(len(obs))},
+    }
+    if args.no_extras or rank != 0:
+        return result
+
+    # ---- force kernel: live per-launch duration (stream launches + CUDA events) ----
+    pos, vel, img = sim.get_state()
+    p_nog = md.make_params(s.params, 0.001, precision=md.PRECISIONS[args.precision], sample_interval=100,
+                           use_graph=False, threads_per_particle=args.tpp)
+    sim_k = md.System(p_nog, [s.n], [s.box], s.species, pos, vel, img, device=device)
+    sim_k.step(32)
+    info_a = sim_k.info()
+    sim_k.step(320)
+    info_b = sim_k.info()
+    f_ms = (info_b["step_ms"] - info_a["step_ms"]) / max(1, info_b["step_launches"] - info_a["step_launches"])
+    n_list, n_cut = list_statistics(sim_k, s.params)
+    sim_k.close()
+    flops = (FLOP_PER_ENTRY * n_list + FLOP_PER_PAIR * n_cut + FLOP_PER_UPDATE) * s.n
+    sm_mhz = clk.get("sm_mhz") or 1.9e3
+    peak_max = 152 * 128 * 2 * 2.07e9 / 1e12
+    result["roofline"] = {
+        "bound": "alu", "kernel": f"k_step<{args.precision}, {info1['threads_per_particle']}> "
+                                  "(pair forces + velocity-Verlet update)",
+        "achieved": flops / (f_ms * 1e-3) / 1e12, "peak": peak_max, "unit": "TFLOP/s",
+        "frac": flops / (f_ms * 1e-3) / 1e12 / peak_max, "traffic": None,
+        "per_launch_ms": f_ms, "flop_per_launch": flops, "mean_list": float(n_list),
+        "mean_in_cutoff": float(n_cut),
+        "peak_note": "FP32 FMA peak 152 SM x 128 lanes x 2 flop x 2.07 GHz (max clock)",
+        "frac_at_sampled_clock": flops / (f_ms * 1e-3) / (152 * 128 * 2 * sm_mhz * 1e6),
+        "hbm_view": {"algorithmic_bytes_per_launch": float(s.n * (4 * n_list + 32 + 16 + 4)),
+                     "achieved_gbs": s.n * (4 * n_list + 52) / (f_ms * 1e-3) / 1e9,
+                     "peak_gbs": (measured_peaks() or {}).get("hbm_gbs", 6800.0)},
+    }
+
+    # ---- same workload in full FP64 on the same GPU ----
+    p64 = md.make_params(s.params, 0.001, precision=md.MD_PREC_FP64, sample_interval=100)
+    sim64 = md.System(p64, [s.n], [s.box], s.species, pos, vel, img, device=device)
+    sim64.step(args.inner)
+    k64 = max(3, args.steps // 20)
+    ms64 = time_chunks(torch, sim64, args.inner, k64, flush, stream)
+    assert sim64.sync() == md.MD_OK
+    sim64.close()
+    v64 = s.n * args.inner * k64 / (ms64 / 1e3)
+    result["vs_fp64"] = {"fp64_value": v64, "speedup": value / world / v64, "fp64_iterations": k64}
+
+    # ---- end to end through the C ABI with host buffers ----
+    ke = max(3, min(args.steps, 20))
+    pos_h = np.ascontiguousarray(pos)
+    vel_h = np.ascontiguousarray(vel)
+    img_h = np.ascontiguousarray(img)
+    sim.set_state(pos_h, vel_h, img_h)
+    sim.step(args.inner)
+    sim.observables()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    nrec = 0
+    for _ in range(ke):
+        sim.set_state(pos_h, vel_h, img_h)
+        sim.step(args.inner)
+        o = sim.observables()
+        nrec += o.size
+    torch.cuda.synchronize()
+    t_e2e = time.perf_counter() - t0
+    result["e2e"] = {"value": s.n * args.inner * ke / t_e2e, "unit": UNIT,
+                     "h2d_bytes_per_step": int(pos_h.nbytes + vel_h.nbytes + img_h.nbytes),
+                     "d2h_bytes_per_step": int(nrec * 120 // ke + 104), "iterations": ke}
+    sim.close()
+
+    # ---- CPU baseline: the FP64 oracle as it stands, on the host cores ----
+    if world == 1:
+        result["cpu_baseline"] = cpu_baseline(s, pos, vel, img)
+    return result
+
+
+def cpu_baseline(s, pos, vel, img, budget_s=15.0):
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    oracle.vv_run(s.params, s.box, s.species, pos, vel, img, 0.001, 2)
+    per = (time.perf_counter() - t0) / 3.0          # 3 force evaluations
+    nsteps = max(2, int(budget_s / per))
+    t0 = time.perf_counter()
+    oracle.vv_run(s.params, s.box, s.species, pos, vel, img, 0.001, nsteps)
+    dt = time.perf_counter() - t0
+    return {"value": s.n * nsteps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{nsteps} velocity-Verlet steps of the same N={s.n} KA state, FP64 cell-list "
+                      f"oracle, single thread ({dt:.1f} s)"}
+
+
+def run_reference(args, rank, world):
+    """The FP64 CPU oracle as the reference arm: each step = one MD step of the
+    same workload on the host."""
+    if rank != 0:
+        return None
+    import oracle
+    from paper_0912_3824_gb300 import synth
+    oracle.build()
+    s = synth.ka_mixture(n=args.n, temperature=0.5, seed=5)
+    pos, vel, img = s.pos, s.vel, s.image
+    pos, vel, img, _, _ = oracle.vv_run(s.params, s.box, s.species, pos, vel, img, 0.001, args.warmup)
+    # one call for all K steps: the oracle's extra force evaluation at entry is amortised
+    t0 = time.perf_counter()
+    oracle.vv_run(s.params, s.box, s.species, pos, vel, img, 0.001, args.steps)
+    dt = time.perf_counter() - t0
+    value = s.n * args.steps / dt
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded fcc lattice)",
+            "config": {"workload": f"Kob-Andersen 80:20, N={args.n}, rho=1.2, dt=0.001, "
+                                   "r_c=2.5 sigma_ab shifted", "precision": "fp64 (CPU oracle)",
+                       "md_steps_per_iteration": 1},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} velocity-Verlet steps in one oracle call, FP64 "
+                                       "cell-list oracle, one host thread"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        backend = "gloo" if args.impl == "reference" else "nccl"
+        if args.impl != "reference":
+            import torch
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    if args.impl == "reference":
+        res = run_reference(args, rank, world)
+    else:
+        res = run_ours(args, rank, world, local)
+    if rank == 0 and res is not None:
+        print(json.dumps(res))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

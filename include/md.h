@@ -116,8 +116,12 @@ typedef struct {
     int64_t kernel_launches;  /* library kernels executed on the device since md_create         */
     int32_t max_neighbours;   /* largest list length at the last build                          */
     int32_t status;           /* pending device status (MD_OK if none)                          */
-    double  force_ms;         /* with use_graph = 0: summed CUDA-event time of the force kernel */
-    int64_t force_launches;   /* with use_graph = 0: force-kernel launches timed                */
+    double  step_ms;          /* with use_graph = 0: summed CUDA-event time of the step kernel
+                                 (pair forces + velocity-Verlet update, one launch per step)   */
+    int64_t step_launches;    /* with use_graph = 0: step-kernel launches timed                 */
+    double  rebuild_ms;       /* with use_graph = 0: summed time of the rebuild chains launched
+                                 at the check points (including those that found no rebuild) */
+    int64_t rebuild_checks;   /* with use_graph = 0: rebuild chains launched                    */
 } md_info_t;
 
 typedef struct md_handle md_handle;

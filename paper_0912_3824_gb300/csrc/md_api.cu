@@ -4,15 +4,18 @@
 // the per-replica tables there, and drives the kernels on the caller's stream.
 // md_step() runs as one CUDA graph:
 //
-//   integrate(FIRST) -> IF(rebuild){bin, scan, scatter, permute, copyback, nbuild}
-//     -> WHILE(loop){ force -> integrate(LOOP) -> IF(rebuild){...} }
+//   integrate(FIRST) -> IF(rebuild){bin, scan, scatter, permute, nbuild, flip}
+//     -> WHILE(loop){ step x kCheck -> IF(rebuild){...} -> step x kCheck -> IF ... }
 //
-// where the last block of each integrate kernel sets both conditions on the
-// device (rebuild when the largest displacement since the last build exceeds
-// skin/2; loop while steps remain), so a whole md_step of n steps is one graph
-// launch with no host round trip.  With use_graph = 0 the same kernels are
-// launched one by one and the rebuild kernels return at once when no rebuild
-// is pending.
+// with kUnroll step kernels per loop iteration and a rebuild check after every
+// kCheck of them.  The last block of each kernel sets the conditions on the
+// device (rebuild when the displacement since the last build, plus a bound on
+// the motion until the next check, could exceed skin/2; loop while steps
+// remain), so a whole md_step of n steps is one graph launch with no host
+// round trip.  Conditional nodes cost microseconds each on this hardware,
+// which is why the loop is unrolled and the check is spaced.  With
+// use_graph = 0 the same kernel sequence, with the same check points, is
+// launched from the host (the results are bitwise identical).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -34,6 +37,8 @@ namespace {
 constexpr size_t kAlign = 256;
 constexpr int kIntBlock = 256, kForceBlock = 256, kNbBlock = 256, kScanBlock = 1024;
 constexpr double kCellMargin = 1e-3;   // cell edge exceeds the largest list radius by this
+constexpr int kUnroll = 16;            // step kernels per loop iteration of the graph
+constexpr int kCheck = 4;              // rebuild check after every kCheck steps (divides kUnroll)
 
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
@@ -121,7 +126,7 @@ int make_geometry(const md_params *p, int R, const int64_t *nrep, const double *
     }
     g.R = R;
     g.rl_max = rcmax + p->skin + (double)mdk::kListMargin;
-    g.tpp = tpp ? tpp : 8;
+    g.tpp = tpp ? tpp : 4;
     g.ppb_f = kForceBlock / g.tpp;
     g.n = 0;
     g.rep.assign(R, mdk::Rep{});
@@ -244,7 +249,7 @@ Layout make_layout(const md_params *p, const Geometry &g)
     L.off_cstart = take(4 * ((size_t)g.ncell + 1));
     L.off_nbr = take(4 * n * (size_t)g.K);
     L.off_nnbr = take(4 * n);
-    L.off_part_f = take(8 * 8 * (size_t)g.nblk_f);
+    L.off_part_f = take(8 * 12 * (size_t)g.nblk_f);
     L.off_part_i = take(8 * 4 * (size_t)g.nblk_i);
     L.off_ring = take(sizeof(mdk::Obs) * (size_t)cap * g.R);
     L.off_totals = take(sizeof(mdk::Obs) * g.R);
@@ -295,9 +300,9 @@ struct md_handle {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
     // timing of the force kernel (use_graph = 0)
-    cudaEvent_t ev_f0 = nullptr, ev_f1 = nullptr;
-    double force_ms = 0.0;
-    int64_t force_launches = 0;
+    cudaEvent_t ev_f0 = nullptr, ev_f1 = nullptr, ev_i1 = nullptr;
+    double step_ms = 0.0, rebuild_ms = 0.0;
+    int64_t step_launches = 0, rebuild_checks = 0;
     int64_t obs_read = 0;
     std::string err;
 };
@@ -335,18 +340,53 @@ int launch(md_handle *h, const void *f, int grid, int block, const KArgs &a)
 
 int grid_n(int64_t n, int per) { return (int)((n + per - 1) / per); }
 
-int launch_rebuild(md_handle *h)
+// The rebuild chain: kernel, grid, block.
+struct ChainStep { const void *f; int grid, block; };
+
+int rebuild_chain(const md_handle *h, ChainStep *seq)
 {
     const KernelSet &k = *h->ks;
-    const KArgs &a = h->a;
-    int rc;
-    if ((rc = launch(h, k.bin, h->g.nblk_i, kIntBlock, a))) return rc;
-    if ((rc = launch(h, k.scan, 1, kScanBlock, a))) return rc;
-    if ((rc = launch(h, k.scatter, grid_n(h->g.n, kIntBlock), kIntBlock, a))) return rc;
-    if ((rc = launch(h, k.permute, grid_n(h->g.n, kIntBlock), kIntBlock, a))) return rc;
-    if ((rc = launch(h, k.copyback, grid_n(h->g.n, kIntBlock), kIntBlock, a))) return rc;
-    if ((rc = launch(h, k.nbuild, grid_n(h->g.n * 32, kNbBlock), kNbBlock, a))) return rc;
+    const int nb = grid_n(h->g.n, kIntBlock);
+    seq[0] = {k.bin, h->g.nblk_i, kIntBlock};
+    seq[1] = {k.scan, 1, kScanBlock};
+    seq[2] = {k.scatter, nb, kIntBlock};
+    seq[3] = {k.permute, nb, kIntBlock};
+    seq[4] = {k.nbuild, grid_n(h->g.n * 32, kNbBlock), kNbBlock};
+    seq[5] = {k.flip, std::max(1, grid_n(h->g.ncell, kIntBlock)), kIntBlock};
+    return 6;
+}
+
+int launch_rebuild(md_handle *h)
+{
+    ChainStep seq[8];
+    const int ns = rebuild_chain(h, seq);
+    for (int s = 0; s < ns; ++s) {
+        int rc = launch(h, seq[s].f, seq[s].grid, seq[s].block, h->a);
+        if (rc)
+            return rc;
+    }
     return MD_OK;
+}
+
+// Arguments of the step kernel at position `slot` of the unrolled loop.
+KArgs step_args(const md_handle *h, int slot)
+{
+    KArgs a = h->a;
+    a.imode = mdk::IM_LOOP;
+    const bool check = (slot % kCheck) == kCheck - 1;
+    a.lookahead = check ? kCheck - 1 : 0;
+    a.set_rebuild = check ? 1 : 0;
+    a.set_loop = slot == kUnroll - 1 ? 1 : 0;
+    return a;
+}
+
+KArgs first_args(const md_handle *h)
+{
+    KArgs a = h->a;
+    a.imode = mdk::IM_FIRST;
+    a.lookahead = kCheck - 1;
+    a.set_rebuild = 1;
+    return a;
 }
 
 int launch_force(md_handle *h, int fsample)
@@ -383,21 +423,13 @@ int add_kernel(md_handle *h, cudaGraph_t g, cudaGraphNode_t *node, const cudaGra
 
 int add_rebuild_chain(md_handle *h, cudaGraph_t g)
 {
-    const KernelSet &k = *h->ks;
-    const KArgs &a = h->a;
-    struct { const void *f; int grid, block; } seq[6] = {
-        {k.bin, h->g.nblk_i, kIntBlock},
-        {k.scan, 1, kScanBlock},
-        {k.scatter, grid_n(h->g.n, kIntBlock), kIntBlock},
-        {k.permute, grid_n(h->g.n, kIntBlock), kIntBlock},
-        {k.copyback, grid_n(h->g.n, kIntBlock), kIntBlock},
-        {k.nbuild, grid_n(h->g.n * 32, kNbBlock), kNbBlock},
-    };
+    ChainStep seq[8];
+    const int ns = rebuild_chain(h, seq);
     cudaGraphNode_t prev = nullptr;
-    for (int s = 0; s < 6; ++s) {
+    for (int s = 0; s < ns; ++s) {
         cudaGraphNode_t node;
         int rc = add_kernel(h, g, &node, prev ? &prev : nullptr, prev ? 1 : 0, seq[s].f, seq[s].grid,
-                            seq[s].block, a);
+                            seq[s].block, h->a);
         if (rc)
             return rc;
         prev = node;
@@ -429,8 +461,7 @@ int build_graph(md_handle *h)
     CK(h, cudaGraphConditionalHandleCreate(&c_loop, g, 1, cudaGraphCondAssignDefault));
     CK(h, cudaGraphConditionalHandleCreate(&c_reb0, g, 0, 0));
 
-    KArgs first = h->a;
-    first.imode = mdk::IM_FIRST;
+    KArgs first = first_args(h);
     first.use_cond = 1;
     first.h_rebuild = c_reb0;
     first.h_loop = c_loop;
@@ -445,26 +476,33 @@ int build_graph(md_handle *h)
     cudaGraph_t wbody;
     if ((rc = add_conditional(h, g, &n_while, n_if0, c_loop, cudaGraphCondTypeWhile, &wbody)))
         return rc;
-    cudaGraphConditionalHandle c_reb1;
-    CK(h, cudaGraphConditionalHandleCreate(&c_reb1, wbody, 0, 0));
-    KArgs fa = h->a;
-    fa.fsample = 0;
-    cudaGraphNode_t n_f, n_i, n_if1;
-    if ((rc = add_kernel(h, wbody, &n_f, nullptr, 0, h->ks->force[force_index(h->g.tpp)], h->g.nblk_f,
-                         kForceBlock, fa)))
-        return rc;
-    KArgs loop = h->a;
-    loop.imode = mdk::IM_LOOP;
-    loop.use_cond = 1;
-    loop.h_rebuild = c_reb1;
-    loop.h_loop = c_loop;
-    if ((rc = add_kernel(h, wbody, &n_i, &n_f, 1, h->ks->integrate, h->g.nblk_i, kIntBlock, loop)))
-        return rc;
-    cudaGraph_t body1;
-    if ((rc = add_conditional(h, wbody, &n_if1, n_i, c_reb1, cudaGraphCondTypeIf, &body1)))
-        return rc;
-    if ((rc = add_rebuild_chain(h, body1)))
-        return rc;
+    // loop body: kUnroll step kernels, a conditional rebuild after every kCheck
+    const void *stepk = h->ks->step[force_index(h->g.tpp)];
+    cudaGraphNode_t prev = nullptr;
+    for (int slot = 0; slot < kUnroll; ++slot) {
+        KArgs sa = step_args(h, slot);
+        sa.use_cond = 1;
+        sa.h_loop = c_loop;
+        cudaGraphConditionalHandle c_reb = 0;
+        if (sa.set_rebuild) {
+            CK(h, cudaGraphConditionalHandleCreate(&c_reb, wbody, 0, 0));
+            sa.h_rebuild = c_reb;
+        }
+        cudaGraphNode_t n_s;
+        if ((rc = add_kernel(h, wbody, &n_s, prev ? &prev : nullptr, prev ? 1 : 0, stepk, h->g.nblk_f,
+                             kForceBlock, sa)))
+            return rc;
+        prev = n_s;
+        if (sa.set_rebuild) {
+            cudaGraphNode_t n_if;
+            cudaGraph_t body;
+            if ((rc = add_conditional(h, wbody, &n_if, n_s, c_reb, cudaGraphCondTypeIf, &body)))
+                return rc;
+            if ((rc = add_rebuild_chain(h, body)))
+                return rc;
+            prev = n_if;
+        }
+    }
     CK(h, cudaGraphInstantiate(&h->gexec, g, 0));
     return MD_OK;
 }
@@ -719,6 +757,9 @@ static int create_impl(md_handle *h, const md_params *p, const int32_t *species,
     a.dt_lo = (float)(p->dt - (double)(float)p->dt);
     const double thr = std::max(0.5 * p->skin - (double)mdk::kDispMargin, 0.0);
     a.disp_thr2 = (float)(thr * thr);
+    a.disp_thr = (float)thr;
+    for (int s = 0; s < 2; ++s)
+        a.inv_mass[s] = (float)(1.0 / a.mass[s]);
     if (a.hdtm_hi[0] == 0.0f)
         return fail(h, MD_E_INVAL, "dt / (2 m) underflows single precision");
 
@@ -726,6 +767,7 @@ static int create_impl(md_handle *h, const md_params *p, const int32_t *species,
     CK(h, cudaEventCreateWithFlags(&h->ev_stage, cudaEventDisableTiming));
     CK(h, cudaEventCreate(&h->ev_f0));
     CK(h, cudaEventCreate(&h->ev_f1));
+    CK(h, cudaEventCreate(&h->ev_i1));
     CK(h, cudaEventRecord(h->ev_stage, h->s));
     size_t tbytes = sizeof(mdk::Rep) * g.R + sizeof(int4) * (g.nblk_i + g.nblk_f) +
                     sizeof(int) * g.ncell + sizeof(int4) * g.ncell;
@@ -799,20 +841,37 @@ int md_step(md_handle *h, int64_t nsteps)
         CK(h, cudaGraphLaunch(h->gexec, h->s));
         return MD_OK;
     }
-    if ((rc = launch_integrate(h, mdk::IM_FIRST)) || (rc = launch_rebuild(h)))
+    // the graph's kernel sequence, launched from the host, with per-kernel timing
+    if ((rc = launch(h, h->ks->integrate, h->g.nblk_i, kIntBlock, first_args(h))) || (rc = launch_rebuild(h)))
         return rc;
-    for (int64_t k = 0; k < nsteps; ++k) {
-        CK(h, cudaEventRecord(h->ev_f0, h->s));
-        if ((rc = launch_force(h, 0)))
-            return rc;
-        CK(h, cudaEventRecord(h->ev_f1, h->s));
-        if ((rc = launch_integrate(h, mdk::IM_LOOP)) || (rc = launch_rebuild(h)))
-            return rc;
-        CK(h, cudaEventSynchronize(h->ev_f1));
-        float ms = 0.f;
-        CK(h, cudaEventElapsedTime(&ms, h->ev_f0, h->ev_f1));
-        h->force_ms += ms;
-        h->force_launches += 1;
+    const void *stepk = h->ks->step[force_index(h->g.tpp)];
+    const int64_t iters = (nsteps + kUnroll - 1) / kUnroll;
+    for (int64_t it = 0; it < iters; ++it) {
+        for (int slot = 0; slot < kUnroll; ++slot) {
+            const KArgs sa = step_args(h, slot);
+            CK(h, cudaEventRecord(h->ev_f0, h->s));
+            if ((rc = launch(h, stepk, h->g.nblk_f, kForceBlock, sa)))
+                return rc;
+            CK(h, cudaEventRecord(h->ev_f1, h->s));
+            if (sa.set_rebuild) {
+                if ((rc = launch_rebuild(h)))
+                    return rc;
+                CK(h, cudaEventRecord(h->ev_i1, h->s));
+            }
+            CK(h, cudaEventSynchronize(h->ev_f1));
+            float ms = 0.f;
+            CK(h, cudaEventElapsedTime(&ms, h->ev_f0, h->ev_f1));
+            if (it * kUnroll + slot < nsteps) {
+                h->step_ms += ms;
+                h->step_launches += 1;
+            }
+            if (sa.set_rebuild) {
+                CK(h, cudaEventSynchronize(h->ev_i1));
+                CK(h, cudaEventElapsedTime(&ms, h->ev_f1, h->ev_i1));
+                h->rebuild_ms += ms;
+                h->rebuild_checks += 1;
+            }
+        }
     }
     return MD_OK;
 }
@@ -956,14 +1015,18 @@ int md_get_neighbours(md_handle *h, int32_t *counts, int32_t *lists, int32_t kma
         return MD_E_INVAL;
     const size_t n = (size_t)h->g.n, K = (size_t)h->g.K;
     int rc;
+    mdk::Ctl c;
+    if ((rc = read_ctl(h, &c)))
+        return rc;
     if ((rc = ensure_pinned(h, 4 * n * K + 4 * n + 16 * n + 256)) || (rc = stage_wait(h)))
         return rc;
     char *q = h->pin;
     int *nn = (int *)q;
     int4 *img = (int4 *)(q + align_up(4 * n));
     int *nb = (int *)(q + align_up(4 * n) + align_up(16 * n));
+    const int4 *dimg = c.state_par ? h->a.image2 : h->a.image;   // tags of the current order
     CK(h, cudaMemcpyAsync(nn, h->a.nnbr, 4 * n, cudaMemcpyDeviceToHost, h->s));
-    CK(h, cudaMemcpyAsync(img, h->a.image, 16 * n, cudaMemcpyDeviceToHost, h->s));
+    CK(h, cudaMemcpyAsync(img, dimg, 16 * n, cudaMemcpyDeviceToHost, h->s));
     if (lists)
         CK(h, cudaMemcpyAsync(nb, h->a.nbr, 4 * n * K, cudaMemcpyDeviceToHost, h->s));
     CK(h, cudaStreamSynchronize(h->s));
@@ -997,8 +1060,10 @@ int md_info(md_handle *h, md_info_t *out)
     out->kernel_launches = c.n_force + c.n_integrate + c.n_rebuild_k + c.n_other;
     out->max_neighbours = c.max_nbr;
     out->status = status_code(c.status);
-    out->force_ms = h->force_ms;
-    out->force_launches = h->force_launches;
+    out->step_ms = h->step_ms;
+    out->step_launches = h->step_launches;
+    out->rebuild_ms = h->rebuild_ms;
+    out->rebuild_checks = h->rebuild_checks;
     return MD_OK;
 }
 
@@ -1027,6 +1092,8 @@ int md_destroy(md_handle *h)
         cudaEventDestroy(h->ev_f0);
     if (h->ev_f1)
         cudaEventDestroy(h->ev_f1);
+    if (h->ev_i1)
+        cudaEventDestroy(h->ev_i1);
     delete h;
     return MD_OK;
 }

@@ -32,7 +32,11 @@ struct Ctl {
     unsigned int status;      // ST_* bits
     unsigned int rebuild;     // 1: lists must be rebuilt before the next force evaluation
     unsigned int maxdisp2;    // float bits of the largest squared displacement (this step)
-    unsigned int ticket;      // last-block counter of the integrate kernel
+    unsigned int ticket;      // last-block counter of the step / integrate kernels
+    unsigned int maxv2;       // float bits of the largest squared speed (this step)
+    unsigned int maxa2;       // float bits of the largest squared acceleration (this step)
+    int pos_par;              // which of the two position buffers is current
+    int state_par;            // which of the two velocity / image buffers is current
     int max_nbr;              // largest list length seen at the last build
     int pad0;
     long long step;           // time index of the current positions
@@ -73,18 +77,20 @@ struct __align__(32) d4 { double x, y, z, w; };
 struct KArgs {
     int n, nrep, ncell, K, tpp, si, obs_cap, imode, use_cond, fsample;
     int nblk_i, nblk_f;
-    void *pa, *pb, *va, *vb;          // state: MIXED pos hi/lo, vel hi/lo (float4);
+    int lookahead;                    // MD steps until the next rebuild check (after this node)
+    int set_rebuild, set_loop;        // this graph node sets the rebuild / loop condition
+    void *pa, *pb, *va, *vb;          // buffer 0: MIXED pos hi/lo, vel hi/lo (float4);
                                       // FP64 pos, vel (d4); FP32 pos, vel (float4)
-    void *pa2, *pb2, *va2, *vb2;      // permutation targets
+    void *pa2, *pb2, *va2, *vb2;      // buffer 1 (positions: Ctl::pos_par, velocities: state_par)
     void *force;                      // float4 (MIXED, FP32) or d4 (FP64): f.xyz, e_i in w
     float4 *rref;                     // positions at the last list build
-    int4 *image, *image2;             // image counters, w = original index
+    int4 *image, *image2;             // image counters (w = original index), by state_par
     int *key, *ccount, *cstart, *ccursor, *tmpidx, *cellof;
     const int *crank;                 // [global linear cell] -> global sorted cell id
     const int4 *cxyz;                 // [global sorted cell id] -> cx, cy, cz, replica
     int *nbr, *nnbr;
     const int4 *blk_i, *blk_f;        // per block: first particle, end, replica
-    double *part_f, *part_i;          // per-block partial sums [nblk][8], [nblk][4]
+    double *part_f, *part_i;          // per-block partial sums [nblk_f][12], [nblk_i][4]
     Obs *ring, *totals;
     Ctl *ctl;
     const Rep *rep;
@@ -94,8 +100,8 @@ struct KArgs {
     PairTab tab;
     double hdtm[2], dt, mass[2];      // dt / (2 m_a), dt, m_a
     long long nsteps;                 // for k_set_steps
-    float hdtm_hi[2], hdtm_lo[2], dt_hi, dt_lo;
-    float disp_thr2;
+    float hdtm_hi[2], hdtm_lo[2], dt_hi, dt_lo, inv_mass[2];
+    float disp_thr2, disp_thr;        // (skin/2 - margin)^2 and skin/2 - margin
     cudaGraphConditionalHandle h_loop, h_rebuild;
 };
 
@@ -155,7 +161,7 @@ __device__ __forceinline__ ds ds_from_double(double x)
 
 // table of kernel entry addresses for one precision (one translation unit each)
 struct KernelSet {
-    const void *integrate, *force[6], *bin, *scan, *scatter, *permute, *copyback, *nbuild;
+    const void *integrate, *force[6], *step[6], *bin, *scan, *scatter, *permute, *nbuild, *flip;
     const void *load, *getstate, *expforce, *scale, *set_steps, *reset, *mark_rebuild;
 };
 

@@ -5,23 +5,37 @@
 // kernel entry addresses.  All kernels take one KArgs by value.
 //
 // State layout in device memory (slot order = cell order after each rebuild):
-//   MIXED  pa: float4 (H.x, H.y, H.z, species bits)  pb: float4 (l.x, l.y, l.z, 0)
-//          position = H + l, H on a power-of-two grid of the box (see anchor())
-//          va / vb: float4 velocity high / low words (normalised double-single)
-//   FP64   pa: d4 (x, y, z, species bits), va: d4 velocity
-//   FP32   pa: float4 (x, y, z, species bits), va: float4 velocity
+//   MIXED  pos: float4 (H.x, H.y, H.z, species bits) + float4 (l.x, l.y, l.z, 0);
+//               position = H + l with H on a power-of-two grid (see anchor_wrap)
+//          vel: float4 high words + float4 low words (normalised double-single)
+//   FP64   pos: d4 (x, y, z, species bits), vel: d4
+//   FP32   pos: float4 (x, y, z, species bits), vel: float4
 //   force: float4 (MIXED, FP32) or d4 (FP64): (Fx, Fy, Fz, e_i)
 //   image: int4 (nx, ny, nz, original index)
+// Positions are double-buffered (Ctl::pos_par): the step kernel reads the
+// current buffer for every neighbour and writes the drifted positions into the
+// other one.  Velocities and images are double-buffered by Ctl::state_par,
+// which changes only when a rebuild permutes the particles.
+//
+// One MD step = one launch of k_step: pair forces over the neighbour list,
+// then, per particle, the velocity-Verlet half kick that completes v(t), the
+// kinetic sample, the half kick that starts the next step and the drift
+// (Sec. 2.2).  Its last block finishes the reductions and decides, with a
+// bound on how far particles can move before the next check, whether the
+// lists must be rebuilt (the displacement criterion of Sec. 2.2).
 #pragma once
+
+#include <type_traits>
 
 #include "md_common.cuh"
 
 namespace mdk {
 
 constexpr int kIntBlock = 256;   // per-particle kernels: one thread per particle
-constexpr int kForceBlock = 256; // force kernel: tpp threads per particle
+constexpr int kForceBlock = 256; // force / step kernels: tpp threads per particle
 constexpr int kNbBlock = 256;    // neighbour build: one warp per particle
 constexpr int kScanBlock = 1024;
+constexpr int kPartF = 12;       // doubles per block partial of the force / step kernels
 
 // ---------------------------------------------------------------------------
 // small helpers
@@ -67,23 +81,36 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double *sh)
     __syncthreads();
 }
 
-__device__ __forceinline__ float block_max(float v, float *sh)
+// Maxima of three non-negative floats over the block; valid in thread 0.
+__device__ __forceinline__ void block_max3(float &a, float &b, float &c, float *sh)
 {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    v = warp_max(v);
-    if (lane == 0)
-        sh[w] = v;
-    __syncthreads();
-    if (w == 0) {
-        float x = lane < nw ? sh[lane] : 0.0f;
-        v = warp_max(x);
+    a = warp_max(a);
+    b = warp_max(b);
+    c = warp_max(c);
+    if (lane == 0) {
+        sh[3 * w] = a;
+        sh[3 * w + 1] = b;
+        sh[3 * w + 2] = c;
     }
     __syncthreads();
-    return v;
+    if (w == 0) {
+        a = warp_max(lane < nw ? sh[3 * lane] : 0.f);
+        b = warp_max(lane < nw ? sh[3 * lane + 1] : 0.f);
+        c = warp_max(lane < nw ? sh[3 * lane + 2] : 0.f);
+    }
+    __syncthreads();
 }
 
 __device__ __forceinline__ int species_of(float w) { return __float_as_int(w) & 15; }
 __device__ __forceinline__ int species_of(double w) { return (int)(__double_as_longlong(w) & 15); }
+
+// buffer selection by parity
+__device__ __forceinline__ void *pos_a(const KArgs &a, int par) { return par ? a.pa2 : a.pa; }
+__device__ __forceinline__ void *pos_b(const KArgs &a, int par) { return par ? a.pb2 : a.pb; }
+__device__ __forceinline__ void *vel_a(const KArgs &a, int par) { return par ? a.va2 : a.va; }
+__device__ __forceinline__ void *vel_b(const KArgs &a, int par) { return par ? a.vb2 : a.vb; }
+__device__ __forceinline__ int4 *img_of(const KArgs &a, int par) { return par ? a.image2 : a.image; }
 
 // Re-anchor a double-single coordinate so that its high word lies on the grid
 // of spacing `grid` (a power of two chosen so that every coordinate in
@@ -145,21 +172,200 @@ __device__ __forceinline__ void kahan_add(float &s, float &c, float x)
     s = t;
 }
 
-// ---------------------------------------------------------------------------
-// state access
-// ---------------------------------------------------------------------------
-template <int P> struct Vec;
-template <> struct Vec<MIXED> { ds x, y, z; };
-template <> struct Vec<FP64> { double x, y, z; };
-template <> struct Vec<FP32> { float x, y, z; };
+template <int P> using FT = typename std::conditional<P == FP64, double, float>::type;
 
 // ---------------------------------------------------------------------------
-// integrate: velocity-Verlet half kicks and drift (Sec. 2.2), the per-step
-// maximum-displacement reduction that decides the list rebuild, and the
-// kinetic reductions; its last block finishes all reductions, advances the
-// step counter and sets the graph conditions.
+// Per-particle velocity-Verlet pieces (Sec. 2.2), in the precision's state
+// representation: MIXED updates velocities and positions in double-single
+// (Sec. 2.4), FP64 in double, FP32 in float.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void write_record(const KArgs &a, int r, const double *v, long long step,
+template <int P> struct PState;
+template <> struct PState<MIXED> { float4 H, l; ds vx, vy, vz; int sp; };
+template <> struct PState<FP64> { d4 x; double vx, vy, vz; int sp; };
+template <> struct PState<FP32> { float4 x; float vx, vy, vz; int sp; };
+
+template <int P>
+__device__ __forceinline__ void load_pos(const KArgs &a, int pp, int i, PState<P> &s)
+{
+    if constexpr (P == MIXED) {
+        s.H = ((const float4 *)pos_a(a, pp))[i];
+        s.l = ((const float4 *)pos_b(a, pp))[i];
+        s.sp = species_of(s.H.w);
+    } else if constexpr (P == FP64) {
+        s.x = ((const d4 *)pos_a(a, pp))[i];
+        s.sp = species_of(s.x.w);
+    } else {
+        s.x = ((const float4 *)pos_a(a, pp))[i];
+        s.sp = species_of(s.x.w);
+    }
+}
+
+template <int P>
+__device__ __forceinline__ void load_vel(const KArgs &a, int sp, int i, PState<P> &s)
+{
+    if constexpr (P == MIXED) {
+        const float4 h = ((const float4 *)vel_a(a, sp))[i], l = ((const float4 *)vel_b(a, sp))[i];
+        s.vx = ds_from(h.x, l.x);
+        s.vy = ds_from(h.y, l.y);
+        s.vz = ds_from(h.z, l.z);
+    } else if constexpr (P == FP64) {
+        const d4 v = ((const d4 *)vel_a(a, sp))[i];
+        s.vx = v.x; s.vy = v.y; s.vz = v.z;
+    } else {
+        const float4 v = ((const float4 *)vel_a(a, sp))[i];
+        s.vx = v.x; s.vy = v.y; s.vz = v.z;
+    }
+}
+
+template <int P>
+__device__ __forceinline__ void store_vel(const KArgs &a, int sp, int i, const PState<P> &s)
+{
+    if constexpr (P == MIXED) {
+        ((float4 *)vel_a(a, sp))[i] = make_float4(s.vx.hi, s.vy.hi, s.vz.hi, 0.f);
+        ((float4 *)vel_b(a, sp))[i] = make_float4(s.vx.lo, s.vy.lo, s.vz.lo, 0.f);
+    } else if constexpr (P == FP64) {
+        d4 v;
+        v.x = s.vx; v.y = s.vy; v.z = s.vz; v.w = 0.0;
+        ((d4 *)vel_a(a, sp))[i] = v;
+    } else {
+        ((float4 *)vel_a(a, sp))[i] = make_float4(s.vx, s.vy, s.vz, 0.f);
+    }
+}
+
+// v += dt/(2m) f
+template <int P>
+__device__ __forceinline__ void half_kick(const KArgs &a, PState<P> &s, FT<P> fx, FT<P> fy, FT<P> fz)
+{
+    if constexpr (P == MIXED) {
+        const ds hk = ds_from(a.hdtm_hi[s.sp], a.hdtm_lo[s.sp]);
+        s.vx = ds_add(s.vx, ds_mul_f(hk, fx));
+        s.vy = ds_add(s.vy, ds_mul_f(hk, fy));
+        s.vz = ds_add(s.vz, ds_mul_f(hk, fz));
+    } else if constexpr (P == FP64) {
+        const double hk = a.hdtm[s.sp];
+        s.vx += hk * fx;
+        s.vy += hk * fy;
+        s.vz += hk * fz;
+    } else {
+        const float hk = a.hdtm_hi[s.sp];
+        s.vx += hk * fx;
+        s.vy += hk * fy;
+        s.vz += hk * fz;
+    }
+}
+
+// kinetic energy and momentum of the particle in FP64: kin[0..3]
+template <int P>
+__device__ __forceinline__ void kinetic(const KArgs &a, const PState<P> &s, double *kin)
+{
+    double vx, vy, vz;
+    if constexpr (P == MIXED) {
+        vx = ds_to_double(s.vx); vy = ds_to_double(s.vy); vz = ds_to_double(s.vz);
+    } else {
+        vx = s.vx; vy = s.vy; vz = s.vz;
+    }
+    const double m = a.mass[s.sp];
+    kin[0] = 0.5 * m * (vx * vx + vy * vy + vz * vz);
+    kin[1] = m * vx;
+    kin[2] = m * vy;
+    kin[3] = m * vz;
+}
+
+__device__ __forceinline__ float speed2(const PState<MIXED> &s)
+{
+    return s.vx.hi * s.vx.hi + s.vy.hi * s.vy.hi + s.vz.hi * s.vz.hi;
+}
+__device__ __forceinline__ float speed2(const PState<FP64> &s) { return (float)(s.vx * s.vx + s.vy * s.vy + s.vz * s.vz); }
+__device__ __forceinline__ float speed2(const PState<FP32> &s) { return s.vx * s.vx + s.vy * s.vy + s.vz * s.vz; }
+
+// r += dt v, wrapped into [0, L) with image counting; writes the new position
+// into buffer `dst`, updates the image counter in the state buffers `spar`,
+// returns the squared displacement since the last list build.
+template <int P>
+__device__ __forceinline__ float drift(const KArgs &a, const Rep &rp, PState<P> &s, int dst, int spar, int i,
+                                       unsigned int &bad)
+{
+    int ix, iy, iz;
+    float dd;
+    if constexpr (P == MIXED) {
+        const ds dt = ds_from(a.dt_hi, a.dt_lo);
+        const ds sx = ds_mul(dt, s.vx), sy = ds_mul(dt, s.vy), sz = ds_mul(dt, s.vz);
+        const float lim = 0.25f * rp.Lhi;
+        if (fabsf(sx.hi) > lim || fabsf(sy.hi) > lim || fabsf(sz.hi) > lim)
+            bad |= ST_UNSTABLE;
+        const ds nx = ds_add(ds_from(s.H.x, s.l.x), sx);
+        const ds ny = ds_add(ds_from(s.H.y, s.l.y), sy);
+        const ds nz = ds_add(ds_from(s.H.z, s.l.z), sz);
+        ix = anchor_wrap(nx, rp.grid, rp.inv_grid, rp.Lhi, rp.Llo, s.H.x, s.l.x);
+        iy = anchor_wrap(ny, rp.grid, rp.inv_grid, rp.Lhi, rp.Llo, s.H.y, s.l.y);
+        iz = anchor_wrap(nz, rp.grid, rp.inv_grid, rp.Lhi, rp.Llo, s.H.z, s.l.z);
+        if (!isfinite(s.H.x) || !isfinite(s.H.y) || !isfinite(s.H.z))
+            bad |= ST_NONFINITE;
+        ((float4 *)pos_a(a, dst))[i] = s.H;
+        ((float4 *)pos_b(a, dst))[i] = s.l;
+        const float4 rr = a.rref[i];
+        const float ex = __fadd_rn(sep_f(s.H.x, rr.x, rp.Lhi, rp.invLf), s.l.x);
+        const float ey = __fadd_rn(sep_f(s.H.y, rr.y, rp.Lhi, rp.invLf), s.l.y);
+        const float ez = __fadd_rn(sep_f(s.H.z, rr.z, rp.Lhi, rp.invLf), s.l.z);
+        dd = ex * ex + ey * ey + ez * ez;
+    } else if constexpr (P == FP64) {
+        const double sx = a.dt * s.vx, sy = a.dt * s.vy, sz = a.dt * s.vz;
+        const double lim = 0.25 * rp.L;
+        if (fabs(sx) > lim || fabs(sy) > lim || fabs(sz) > lim)
+            bad |= ST_UNSTABLE;
+        double x = s.x.x + sx, y = s.x.y + sy, z = s.x.z + sz;
+        ix = iy = iz = 0;
+        if (x >= rp.L) { x -= rp.L; ix = 1; } else if (x < 0.0) { x += rp.L; ix = -1; }
+        if (y >= rp.L) { y -= rp.L; iy = 1; } else if (y < 0.0) { y += rp.L; iy = -1; }
+        if (z >= rp.L) { z -= rp.L; iz = 1; } else if (z < 0.0) { z += rp.L; iz = -1; }
+        if (!isfinite(x) || !isfinite(y) || !isfinite(z))
+            bad |= ST_NONFINITE;
+        s.x.x = x; s.x.y = y; s.x.z = z;
+        ((d4 *)pos_a(a, dst))[i] = s.x;
+        const float4 rr = a.rref[i];
+        const float ex = sep_f(__double2float_rn(x), rr.x, rp.Lhi, rp.invLf);
+        const float ey = sep_f(__double2float_rn(y), rr.y, rp.Lhi, rp.invLf);
+        const float ez = sep_f(__double2float_rn(z), rr.z, rp.Lhi, rp.invLf);
+        dd = ex * ex + ey * ey + ez * ez;
+    } else {
+        const float dt = a.dt_hi;
+        const float sx = dt * s.vx, sy = dt * s.vy, sz = dt * s.vz;
+        const float L = rp.Lhi;
+        if (fabsf(sx) > 0.25f * L || fabsf(sy) > 0.25f * L || fabsf(sz) > 0.25f * L)
+            bad |= ST_UNSTABLE;
+        float x = s.x.x + sx, y = s.x.y + sy, z = s.x.z + sz;
+        ix = iy = iz = 0;
+        if (x >= L) { x -= L; ix = 1; } else if (x < 0.f) { x += L; ix = -1; }
+        if (y >= L) { y -= L; iy = 1; } else if (y < 0.f) { y += L; iy = -1; }
+        if (z >= L) { z -= L; iz = 1; } else if (z < 0.f) { z += L; iz = -1; }
+        if (x >= L) x = 0.f;   // a coordinate just below 0 can round to L when wrapped
+        if (y >= L) y = 0.f;
+        if (z >= L) z = 0.f;
+        if (!isfinite(x) || !isfinite(y) || !isfinite(z))
+            bad |= ST_NONFINITE;
+        s.x.x = x; s.x.y = y; s.x.z = z;
+        ((float4 *)pos_a(a, dst))[i] = s.x;
+        const float4 rr = a.rref[i];
+        const float ex = sep_f(x, rr.x, L, rp.invLf);
+        const float ey = sep_f(y, rr.y, L, rp.invLf);
+        const float ez = sep_f(z, rr.z, L, rp.invLf);
+        dd = ex * ex + ey * ey + ez * ez;
+    }
+    if (ix | iy | iz) {
+        int4 *im = img_of(a, spar);
+        int4 q = im[i];
+        q.x += ix;
+        q.y += iy;
+        q.z += iz;
+        im[i] = q;
+    }
+    return dd;
+}
+
+// ---------------------------------------------------------------------------
+// reductions finished by the last block of a step / integrate kernel
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void write_record(const KArgs &a, int mode, int r, const double *v, long long step,
                                              float md2, long long rebuilds, long long slot)
 {
     Obs o;
@@ -174,9 +380,9 @@ __device__ __forceinline__ void write_record(const KArgs &a, int r, const double
     o.p[2] = v[11];
     o.max_disp = sqrt((double)md2);
     o.rebuilds = rebuilds;
-    if (a.imode == IM_TOTALS)
+    if (mode == IM_TOTALS)
         a.totals[r] = o;
-    else if (a.imode == IM_KE) {
+    else if (mode == IM_KE) {
         const Rep &rp = a.rep[r];
         double dof = 3.0 * (double)rp.n - 3.0;
         double target = a.scale[r];
@@ -185,14 +391,16 @@ __device__ __forceinline__ void write_record(const KArgs &a, int r, const double
         a.ring[slot * a.nrep + r] = o;
 }
 
-// Per-replica reduction of the force-kernel and integrate-kernel block partials,
-// in a fixed order (deterministic).  Runs in the last block of k_integrate.
-static __device__ void finish_reductions(const KArgs &a, long long step, float md2, double *sh)
+// Per-replica sums of the block partials, in a fixed order (deterministic).
+// Potential-side values come from part_f[.][0..7]; kinetic values from
+// part_f[.][8..11] (step kernel, from_f = true) or part_i[.][0..3].
+static __device__ void finish_reductions(const KArgs &a, int mode, bool from_f, long long step, float md2,
+                                         double *sh)
 {
     const Ctl *ctl = a.ctl;
     const long long slot = ctl->obs_count % (long long)a.obs_cap;
     const long long rebuilds = ctl->rebuilds;
-    const bool want_f = a.imode != IM_KE;
+    const bool want_f = mode != IM_KE;
     if (a.nrep <= 8) {
         for (int r = 0; r < a.nrep; ++r) {
             const Rep rp = a.rep[r];
@@ -200,18 +408,23 @@ static __device__ void finish_reductions(const KArgs &a, long long step, float m
 #pragma unroll
             for (int k = 0; k < 12; ++k)
                 v[k] = 0.0;
-            if (want_f)
+            if (want_f || from_f)
                 for (int b = rp.bf0 + threadIdx.x; b < rp.bf1; b += blockDim.x)
 #pragma unroll
-                    for (int k = 0; k < 8; ++k)
-                        v[k] += a.part_f[(size_t)b * 8 + k];
-            for (int b = rp.bi0 + threadIdx.x; b < rp.bi1; b += blockDim.x)
+                    for (int k = 0; k < kPartF; ++k)
+                        v[k] += a.part_f[(size_t)b * kPartF + k];
+            if (!from_f) {
 #pragma unroll
-                for (int k = 0; k < 4; ++k)
-                    v[8 + k] += a.part_i[(size_t)b * 4 + k];
+                for (int k = 8; k < 12; ++k)
+                    v[k] = 0.0;
+                for (int b = rp.bi0 + threadIdx.x; b < rp.bi1; b += blockDim.x)
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        v[8 + k] += a.part_i[(size_t)b * 4 + k];
+            }
             block_sum<12>(v, sh);
             if (threadIdx.x == 0)
-                write_record(a, r, v, step, md2, rebuilds, slot);
+                write_record(a, mode, r, v, step, md2, rebuilds, slot);
         }
     } else {
         for (int r = threadIdx.x; r < a.nrep; r += blockDim.x) {
@@ -219,316 +432,59 @@ static __device__ void finish_reductions(const KArgs &a, long long step, float m
             double v[12];
             for (int k = 0; k < 12; ++k)
                 v[k] = 0.0;
-            if (want_f)
+            if (want_f || from_f)
                 for (int b = rp.bf0; b < rp.bf1; ++b)
-                    for (int k = 0; k < 8; ++k)
-                        v[k] += a.part_f[(size_t)b * 8 + k];
-            for (int b = rp.bi0; b < rp.bi1; ++b)
-                for (int k = 0; k < 4; ++k)
-                    v[8 + k] += a.part_i[(size_t)b * 4 + k];
-            write_record(a, r, v, step, md2, rebuilds, slot);
+                    for (int k = 0; k < kPartF; ++k)
+                        v[k] += a.part_f[(size_t)b * kPartF + k];
+            if (!from_f) {
+                for (int k = 8; k < 12; ++k)
+                    v[k] = 0.0;
+                for (int b = rp.bi0; b < rp.bi1; ++b)
+                    for (int k = 0; k < 4; ++k)
+                        v[8 + k] += a.part_i[(size_t)b * 4 + k];
+            }
+            write_record(a, mode, r, v, step, md2, rebuilds, slot);
         }
         __syncthreads();
     }
 }
 
-template <int P>
-__global__ void __launch_bounds__(kIntBlock) k_integrate(KArgs a)
+// Rebuild decision: the list built at the last rebuild holds every pair
+// within r_c + skin, so it stays complete while no particle has moved more
+// than skin/2.  The next check comes after `look` further drifts, each at
+// most dt (v + look dt a) per particle: rebuild now if the largest
+// displacement plus that bound could exceed skin/2 (with a rounding margin).
+__device__ __forceinline__ unsigned int need_rebuild(const KArgs &a, float md2, float mv2, float ma2)
 {
-    __shared__ double sh[32 * 12];
-    __shared__ float shf[32];
-    __shared__ int s_last;
-    __shared__ float s_md2;
-    Ctl *ctl = a.ctl;
-
-    const unsigned int st0 = ctl->status;
-    const bool halted = st0 != 0u;
-    const long long step = ctl->step;
-    const long long remaining = ctl->remaining;
-    const int mode = a.imode;
-    const bool kickA = (mode == IM_LOOP);                              // completes v(t)
-    const bool last = (mode == IM_LOOP) && remaining <= 1;
-    const bool kickB = (mode == IM_FIRST) || (mode == IM_LOOP && !last); // starts step t+1
-    const bool rec = (mode == IM_LOOP && (step % a.si) == 0) || mode == IM_SAMPLE ||
-                     mode == IM_TOTALS || mode == IM_KE;
-
-    const int4 b = a.blk_i[blockIdx.x];
-    const Rep rp = a.rep[b.z];
-    const int i = b.x + threadIdx.x;
-    const bool valid = (i < b.y) && !halted;
-
-    float disp2 = 0.0f;
-    double kin[4] = {0.0, 0.0, 0.0, 0.0};
-    unsigned int bad = 0u;
-
-    if (valid) {
-        if constexpr (P == MIXED) {
-            float4 H = ((float4 *)a.pa)[i], l = ((float4 *)a.pb)[i];
-            float4 vh = ((float4 *)a.va)[i], vl = ((float4 *)a.vb)[i];
-            const int sp = species_of(H.w);
-            Vec<MIXED> v{ds_from(vh.x, vl.x), ds_from(vh.y, vl.y), ds_from(vh.z, vl.z)};
-            const ds hk = ds_from(a.hdtm_hi[sp], a.hdtm_lo[sp]);
-            float4 f = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (kickA || kickB)
-                f = ((const float4 *)a.force)[i];
-            if (kickA) {
-                v.x = ds_add(v.x, ds_mul_f(hk, f.x));
-                v.y = ds_add(v.y, ds_mul_f(hk, f.y));
-                v.z = ds_add(v.z, ds_mul_f(hk, f.z));
-            }
-            if (rec) {
-                const double m = a.mass[sp];
-                double dx = ds_to_double(v.x), dy = ds_to_double(v.y), dz = ds_to_double(v.z);
-                kin[0] = 0.5 * m * (dx * dx + dy * dy + dz * dz);
-                kin[1] = m * dx;
-                kin[2] = m * dy;
-                kin[3] = m * dz;
-            }
-            if (kickB) {
-                v.x = ds_add(v.x, ds_mul_f(hk, f.x));
-                v.y = ds_add(v.y, ds_mul_f(hk, f.y));
-                v.z = ds_add(v.z, ds_mul_f(hk, f.z));
-                const ds dt = ds_from(a.dt_hi, a.dt_lo);
-                ds sx = ds_mul(dt, v.x), sy = ds_mul(dt, v.y), sz = ds_mul(dt, v.z);
-                const float lim = 0.25f * rp.Lhi;
-                if (fabsf(sx.hi) > lim || fabsf(sy.hi) > lim || fabsf(sz.hi) > lim)
-                    bad |= ST_UNSTABLE;
-                ds nx = ds_add(ds_from(H.x, l.x), sx);
-                ds ny = ds_add(ds_from(H.y, l.y), sy);
-                ds nz = ds_add(ds_from(H.z, l.z), sz);
-                int ix = anchor_wrap(nx, rp.grid, rp.inv_grid, rp.Lhi, rp.Llo, H.x, l.x);
-                int iy = anchor_wrap(ny, rp.grid, rp.inv_grid, rp.Lhi, rp.Llo, H.y, l.y);
-                int iz = anchor_wrap(nz, rp.grid, rp.inv_grid, rp.Lhi, rp.Llo, H.z, l.z);
-                if (!isfinite(H.x) || !isfinite(H.y) || !isfinite(H.z))
-                    bad |= ST_NONFINITE;
-                if (ix | iy | iz) {
-                    int4 im = a.image[i];
-                    im.x += ix;
-                    im.y += iy;
-                    im.z += iz;
-                    a.image[i] = im;
-                }
-                ((float4 *)a.pa)[i] = H;
-                ((float4 *)a.pb)[i] = l;
-                const float4 rr = a.rref[i];
-                float ddx = __fadd_rn(sep_f(H.x, rr.x, rp.Lhi, rp.invLf), l.x);
-                float ddy = __fadd_rn(sep_f(H.y, rr.y, rp.Lhi, rp.invLf), l.y);
-                float ddz = __fadd_rn(sep_f(H.z, rr.z, rp.Lhi, rp.invLf), l.z);
-                disp2 = ddx * ddx + ddy * ddy + ddz * ddz;
-            }
-            if (kickA || kickB) {
-                ((float4 *)a.va)[i] = make_float4(v.x.hi, v.y.hi, v.z.hi, 0.f);
-                ((float4 *)a.vb)[i] = make_float4(v.x.lo, v.y.lo, v.z.lo, 0.f);
-            }
-        } else if constexpr (P == FP64) {
-            d4 x = ((d4 *)a.pa)[i], v = ((d4 *)a.va)[i];
-            const int sp = species_of(x.w);
-            const double hk = a.hdtm[sp];
-            d4 f = {0.0, 0.0, 0.0, 0.0};
-            if (kickA || kickB)
-                f = ((const d4 *)a.force)[i];
-            if (kickA) {
-                v.x += hk * f.x;
-                v.y += hk * f.y;
-                v.z += hk * f.z;
-            }
-            if (rec) {
-                const double m = a.mass[sp];
-                kin[0] = 0.5 * m * (v.x * v.x + v.y * v.y + v.z * v.z);
-                kin[1] = m * v.x;
-                kin[2] = m * v.y;
-                kin[3] = m * v.z;
-            }
-            if (kickB) {
-                v.x += hk * f.x;
-                v.y += hk * f.y;
-                v.z += hk * f.z;
-                double sx = a.dt * v.x, sy = a.dt * v.y, sz = a.dt * v.z;
-                const double lim = 0.25 * rp.L;
-                if (fabs(sx) > lim || fabs(sy) > lim || fabs(sz) > lim)
-                    bad |= ST_UNSTABLE;
-                x.x += sx;
-                x.y += sy;
-                x.z += sz;
-                int ix = 0, iy = 0, iz = 0;
-                if (x.x >= rp.L) { x.x -= rp.L; ix = 1; } else if (x.x < 0.0) { x.x += rp.L; ix = -1; }
-                if (x.y >= rp.L) { x.y -= rp.L; iy = 1; } else if (x.y < 0.0) { x.y += rp.L; iy = -1; }
-                if (x.z >= rp.L) { x.z -= rp.L; iz = 1; } else if (x.z < 0.0) { x.z += rp.L; iz = -1; }
-                if (!isfinite(x.x) || !isfinite(x.y) || !isfinite(x.z))
-                    bad |= ST_NONFINITE;
-                if (ix | iy | iz) {
-                    int4 im = a.image[i];
-                    im.x += ix;
-                    im.y += iy;
-                    im.z += iz;
-                    a.image[i] = im;
-                }
-                ((d4 *)a.pa)[i] = x;
-                const float4 rr = a.rref[i];
-                float ddx = sep_f(__double2float_rn(x.x), rr.x, rp.Lhi, rp.invLf);
-                float ddy = sep_f(__double2float_rn(x.y), rr.y, rp.Lhi, rp.invLf);
-                float ddz = sep_f(__double2float_rn(x.z), rr.z, rp.Lhi, rp.invLf);
-                disp2 = ddx * ddx + ddy * ddy + ddz * ddz;
-            }
-            if (kickA || kickB)
-                ((d4 *)a.va)[i] = v;
-        } else {  // FP32
-            float4 x = ((float4 *)a.pa)[i], v = ((float4 *)a.va)[i];
-            const int sp = species_of(x.w);
-            const float hk = (float)a.hdtm[sp];
-            float4 f = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (kickA || kickB)
-                f = ((const float4 *)a.force)[i];
-            if (kickA) {
-                v.x += hk * f.x;
-                v.y += hk * f.y;
-                v.z += hk * f.z;
-            }
-            if (rec) {
-                const double m = a.mass[sp];
-                double dx = v.x, dy = v.y, dz = v.z;
-                kin[0] = 0.5 * m * (dx * dx + dy * dy + dz * dz);
-                kin[1] = m * dx;
-                kin[2] = m * dy;
-                kin[3] = m * dz;
-            }
-            if (kickB) {
-                v.x += hk * f.x;
-                v.y += hk * f.y;
-                v.z += hk * f.z;
-                const float dt = (float)a.dt;
-                float sx = dt * v.x, sy = dt * v.y, sz = dt * v.z;
-                const float lim = 0.25f * rp.Lhi;
-                if (fabsf(sx) > lim || fabsf(sy) > lim || fabsf(sz) > lim)
-                    bad |= ST_UNSTABLE;
-                x.x += sx;
-                x.y += sy;
-                x.z += sz;
-                const float L = rp.Lhi;
-                int ix = 0, iy = 0, iz = 0;
-                if (x.x >= L) { x.x -= L; ix = 1; } else if (x.x < 0.f) { x.x += L; ix = -1; }
-                if (x.y >= L) { x.y -= L; iy = 1; } else if (x.y < 0.f) { x.y += L; iy = -1; }
-                if (x.z >= L) { x.z -= L; iz = 1; } else if (x.z < 0.f) { x.z += L; iz = -1; }
-                if (x.x >= L) x.x = 0.f;   // x just below 0 can round to L when wrapped
-                if (x.y >= L) x.y = 0.f;
-                if (x.z >= L) x.z = 0.f;
-                if (!isfinite(x.x) || !isfinite(x.y) || !isfinite(x.z))
-                    bad |= ST_NONFINITE;
-                if (ix | iy | iz) {
-                    int4 im = a.image[i];
-                    im.x += ix;
-                    im.y += iy;
-                    im.z += iz;
-                    a.image[i] = im;
-                }
-                ((float4 *)a.pa)[i] = x;
-                const float4 rr = a.rref[i];
-                float ddx = sep_f(x.x, rr.x, L, rp.invLf);
-                float ddy = sep_f(x.y, rr.y, L, rp.invLf);
-                float ddz = sep_f(x.z, rr.z, L, rp.invLf);
-                disp2 = ddx * ddx + ddy * ddy + ddz * ddz;
-            }
-            if (kickA || kickB)
-                ((float4 *)a.va)[i] = v;
-        }
-    }
-    if (bad)
-        atomicOr(&ctl->status, bad);
-
-    // block reductions
-    const float bmax = block_max(disp2, shf);
-    if (rec)
-        block_sum<4>(kin, sh);
-    if (threadIdx.x == 0) {
-        if (rec) {
-#pragma unroll
-            for (int k = 0; k < 4; ++k)
-                a.part_i[(size_t)blockIdx.x * 4 + k] = kin[k];
-        }
-        if (bmax > 0.0f)
-            atomicMax(&ctl->maxdisp2, __float_as_uint(bmax));
-        __threadfence();
-        const unsigned int t = atomicAdd(&ctl->ticket, 1u);
-        s_last = (t == gridDim.x - 1);
-    }
-    __syncthreads();
-    if (!s_last)
-        return;
-
-    // ---- last block: all blocks' partials and flags are visible ----
-    __threadfence();
-    if (threadIdx.x == 0)
-        s_md2 = __uint_as_float(atomicExch(&ctl->maxdisp2, 0u));
-    __syncthreads();
-    const unsigned int st = atomicOr(&ctl->status, 0u);
-    const float md2 = s_md2;
-    if (rec && st == 0u)
-        finish_reductions(a, step, md2, sh);
-    if (threadIdx.x == 0) {
-        const bool drifted = kickB && !halted;
-        unsigned int reb = (drifted && st == 0u && md2 > a.disp_thr2) ? 1u : 0u;
-        ctl->rebuild = reb;
-        if (drifted) {
-            ctl->step = step + 1;
-            ctl->last_maxdisp2 = md2;
-        }
-        if (rec && st == 0u && (mode == IM_LOOP || mode == IM_SAMPLE))
-            ctl->obs_count += 1;
-        unsigned int loop = 0u;
-        if (mode == IM_LOOP) {
-            long long rem = remaining - 1, bud = ctl->budget - 1;
-            ctl->remaining = rem;
-            ctl->budget = bud;
-            unsigned int s2 = st;
-            if (bud <= 0 && rem > 0) {
-                atomicOr(&ctl->status, ST_TIMEOUT);
-                s2 |= ST_TIMEOUT;
-            }
-            loop = (s2 == 0u && rem > 0) ? 1u : 0u;
-        }
-        ctl->ticket = 0u;
-        ctl->n_integrate += 1;
-        if (a.use_cond) {
-            cudaGraphSetConditional(a.h_rebuild, reb);
-            if (mode == IM_LOOP)
-                cudaGraphSetConditional(a.h_loop, loop);
-        }
-    }
+    const float ahead = (float)a.lookahead * (float)a.dt * (sqrtf(mv2) + 2.0f * (float)a.lookahead *
+                                                                              (float)a.dt * sqrtf(ma2));
+    const float d = sqrtf(md2) + ahead;
+    return d > a.disp_thr ? 1u : 0u;
 }
 
 // ---------------------------------------------------------------------------
-// force: pair force, potential and virial over the neighbour list (Sec. 2.2),
-// 12-6 potential cut (and shifted) at r_c,ab (Sec. 3, Sec. 5).
-// TPP threads share one particle, each taking every TPP-th list entry; the
-// lanes' partial sums are combined by shuffles.  MIXED accumulates the force
-// with Kahan compensation and combines lanes in double-single (the
-// compensated force summation of Sec. 2.4); energies and the virial are
-// accumulated only on sample steps and go to per-block FP64 partials.
+// pair forces over the neighbour list (Sec. 2.2), 12-6 potential cut (and
+// shifted) at r_c,ab (Sec. 3, Sec. 5).  TPP threads share one particle; each
+// lane takes 4 consecutive list entries at a time (one 16-byte load) and
+// issues their gathers together.  Single precision: the 4 contributions are
+// summed branch-free (zero factor outside the cutoff) and the group sum enters
+// a Kahan accumulator (MIXED; plain sum for FP32); lanes are combined in
+// double-single.  Energies and the virial are accumulated on sample steps only.
+// On return every lane of the particle holds the total force; acc[] (SAMPLE)
+// holds the particle's share of E_pot, W and W_ab.
 // ---------------------------------------------------------------------------
 template <typename T> struct PairRow {   // parameters of (species i, species j = 0 / 1)
     T rc2[2], sig2[2], eps4[2], eps48[2], shift[2];
 };
 
 template <int P, int TPP, bool SAMPLE>
-__device__ __forceinline__ void force_impl(const KArgs &a)
+__device__ __forceinline__ void pair_forces(const KArgs &a, const Rep &rp, int pp, int ii, int nn,
+                                            FT<P> &fx, FT<P> &fy, FT<P> &fz, double *acc)
 {
-    __shared__ double sh[32 * 8];
-    const int4 b = a.blk_f[blockIdx.x];
-    const Rep rp = a.rep[b.z];
     const int lane = threadIdx.x & (TPP - 1);
-    const int i = b.x + (int)(threadIdx.x / TPP);
-    const bool valid = i < b.y;
-    const int ii = valid ? i : b.x;
-    const int nn = valid ? a.nnbr[ii] : 0;
     const int *lst = a.nbr + (size_t)ii * (size_t)a.K;
-
-    double acc[8];   // e, virial, wxx, wyy, wzz, wxy, wxz, wyz (lane-0 values, SAMPLE only)
-#pragma unroll
-    for (int k = 0; k < 8; ++k)
-        acc[k] = 0.0;
-
     if constexpr (P == FP64) {
-        const d4 *pos = (const d4 *)a.pa;
+        const d4 *pos = (const d4 *)pos_a(a, pp);
         const d4 xi = pos[ii];
         const int ti = species_of(xi.w);
         PairRow<double> pr;
@@ -540,63 +496,66 @@ __device__ __forceinline__ void force_impl(const KArgs &a)
             pr.eps48[tj] = a.tab.eps48d[ti * 2 + tj];
             pr.shift[tj] = a.tab.shiftd[ti * 2 + tj];
         }
-        double fx = 0, fy = 0, fz = 0, en = 0, vir = 0, wxx = 0, wyy = 0, wzz = 0, wxy = 0, wxz = 0, wyz = 0;
-        for (int k = lane; k < nn; k += TPP) {
-            const int j = __ldg(lst + k);
-            const d4 xj = pos[j];
-            const int tj = species_of(xj.w);
-            const double dx = sep_d(xi.x, xj.x, rp.L, rp.invL);
-            const double dy = sep_d(xi.y, xj.y, rp.L, rp.invL);
-            const double dz = sep_d(xi.z, xj.z, rp.L, rp.invL);
-            const double r2 = dx * dx + dy * dy + dz * dz;
-            if (r2 < pr.rc2[tj]) {
-                const double ir2 = 1.0 / r2;
-                const double s2 = pr.sig2[tj] * ir2;
-                const double s6 = s2 * s2 * s2;
-                const double fr = pr.eps48[tj] * ir2 * s6 * (s6 - 0.5);
-                fx += fr * dx;
-                fy += fr * dy;
-                fz += fr * dz;
-                if (SAMPLE) {
-                    en += pr.eps4[tj] * s6 * (s6 - 1.0) - pr.shift[tj];
-                    vir += fr * r2;
-                    wxx += fr * dx * dx; wyy += fr * dy * dy; wzz += fr * dz * dz;
-                    wxy += fr * dx * dy; wxz += fr * dx * dz; wyz += fr * dy * dz;
+        double sx = 0, sy = 0, sz = 0, en = 0, vir = 0, wxx = 0, wyy = 0, wzz = 0, wxy = 0, wxz = 0, wyz = 0;
+        for (int k0 = 4 * lane; k0 < nn; k0 += 4 * TPP) {
+            const int4 q = __ldg((const int4 *)(lst + k0));
+            const int jj[4] = {q.x, q.y, q.z, q.w};
+            d4 xs[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                xs[u] = pos[k0 + u < nn ? jj[u] : ii];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (k0 + u >= nn)
+                    break;
+                const d4 xj = xs[u];
+                const int tj = species_of(xj.w);
+                const double dx = sep_d(xi.x, xj.x, rp.L, rp.invL);
+                const double dy = sep_d(xi.y, xj.y, rp.L, rp.invL);
+                const double dz = sep_d(xi.z, xj.z, rp.L, rp.invL);
+                const double r2 = dx * dx + dy * dy + dz * dz;
+                if (r2 < pr.rc2[tj]) {
+                    const double ir2 = 1.0 / r2;
+                    const double s2 = pr.sig2[tj] * ir2;
+                    const double s6 = s2 * s2 * s2;
+                    const double fr = pr.eps48[tj] * ir2 * s6 * (s6 - 0.5);
+                    sx += fr * dx;
+                    sy += fr * dy;
+                    sz += fr * dz;
+                    if (SAMPLE) {
+                        en += pr.eps4[tj] * s6 * (s6 - 1.0) - pr.shift[tj];
+                        vir += fr * r2;
+                        wxx += fr * dx * dx; wyy += fr * dy * dy; wzz += fr * dz * dz;
+                        wxy += fr * dx * dy; wxz += fr * dx * dz; wyz += fr * dy * dz;
+                    }
                 }
             }
         }
 #pragma unroll
         for (int o = TPP / 2; o > 0; o >>= 1) {
-            fx += __shfl_xor_sync(0xffffffffu, fx, o);
-            fy += __shfl_xor_sync(0xffffffffu, fy, o);
-            fz += __shfl_xor_sync(0xffffffffu, fz, o);
-            if (SAMPLE) {
-                en += __shfl_xor_sync(0xffffffffu, en, o);
-                vir += __shfl_xor_sync(0xffffffffu, vir, o);
-                wxx += __shfl_xor_sync(0xffffffffu, wxx, o);
-                wyy += __shfl_xor_sync(0xffffffffu, wyy, o);
-                wzz += __shfl_xor_sync(0xffffffffu, wzz, o);
-                wxy += __shfl_xor_sync(0xffffffffu, wxy, o);
-                wxz += __shfl_xor_sync(0xffffffffu, wxz, o);
-                wyz += __shfl_xor_sync(0xffffffffu, wyz, o);
-            }
+            sx += __shfl_xor_sync(0xffffffffu, sx, o);
+            sy += __shfl_xor_sync(0xffffffffu, sy, o);
+            sz += __shfl_xor_sync(0xffffffffu, sz, o);
         }
-        if (valid && lane == 0) {
-            d4 f;
-            f.x = fx; f.y = fy; f.z = fz; f.w = SAMPLE ? 0.5 * en : 0.0;
-            ((d4 *)a.force)[i] = f;
-            if (SAMPLE) {
-                acc[0] = 0.5 * en; acc[1] = 0.5 * vir;
-                acc[2] = 0.5 * wxx; acc[3] = 0.5 * wyy; acc[4] = 0.5 * wzz;
-                acc[5] = 0.5 * wxy; acc[6] = 0.5 * wxz; acc[7] = 0.5 * wyz;
-            }
+        fx = sx; fy = sy; fz = sz;
+        if (SAMPLE) {
+            double d[8] = {en, vir, wxx, wyy, wzz, wxy, wxz, wyz};
+#pragma unroll
+            for (int o = TPP / 2; o > 0; o >>= 1)
+#pragma unroll
+                for (int k = 0; k < 8; ++k)
+                    d[k] += __shfl_xor_sync(0xffffffffu, d[k], o);
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                acc[k] = 0.5 * d[k];
         }
     } else {
-        const float4 *pos = (const float4 *)a.pa;
+        const float4 *pos = (const float4 *)pos_a(a, pp);
+        const float4 *posl = (const float4 *)pos_b(a, pp);
         const float4 Hi = pos[ii];
         float4 li = make_float4(0.f, 0.f, 0.f, 0.f);
         if constexpr (P == MIXED)
-            li = ((const float4 *)a.pb)[ii];
+            li = posl[ii];
         const int ti = species_of(Hi.w);
         PairRow<float> pr;
 #pragma unroll
@@ -609,51 +568,63 @@ __device__ __forceinline__ void force_impl(const KArgs &a)
         }
         float sx = 0.f, sy = 0.f, sz = 0.f, cx = 0.f, cy = 0.f, cz = 0.f;
         float en = 0.f, vir = 0.f, wxx = 0.f, wyy = 0.f, wzz = 0.f, wxy = 0.f, wxz = 0.f, wyz = 0.f;
-        for (int k = lane; k < nn; k += TPP) {
-            const int j = __ldg(lst + k);
-            const float4 Hj = __ldg(pos + j);
-            const int tj = species_of(Hj.w);
-            float dx, dy, dz;
-            if constexpr (P == MIXED) {
-                const float4 lj = __ldg((const float4 *)a.pb + j);
-                dx = sep_ds(Hi.x, li.x, Hj.x, lj.x, rp.Lhi, rp.Llo, rp.invLf);
-                dy = sep_ds(Hi.y, li.y, Hj.y, lj.y, rp.Lhi, rp.Llo, rp.invLf);
-                dz = sep_ds(Hi.z, li.z, Hj.z, lj.z, rp.Lhi, rp.Llo, rp.invLf);
-            } else {
-                dx = sep_f(Hi.x, Hj.x, rp.Lhi, rp.invLf);
-                dy = sep_f(Hi.y, Hj.y, rp.Lhi, rp.invLf);
-                dz = sep_f(Hi.z, Hj.z, rp.Lhi, rp.invLf);
+        for (int k0 = 4 * lane; k0 < nn; k0 += 4 * TPP) {
+            const int4 q = __ldg((const int4 *)(lst + k0));
+            const int jj[4] = {q.x, q.y, q.z, q.w};
+            float4 Hs[4], Ls[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int j = k0 + u < nn ? jj[u] : ii;
+                Hs[u] = __ldg(pos + j);
+                if constexpr (P == MIXED)
+                    Ls[u] = __ldg(posl + j);
             }
-            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            const float rc2 = tj ? pr.rc2[1] : pr.rc2[0];
-            if (r2 < rc2) {
+            float gx = 0.f, gy = 0.f, gz = 0.f;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const float4 Hj = Hs[u];
+                const int tj = species_of(Hj.w);
+                float dx, dy, dz;
+                if constexpr (P == MIXED) {
+                    const float4 lj = Ls[u];
+                    dx = sep_ds(Hi.x, li.x, Hj.x, lj.x, rp.Lhi, rp.Llo, rp.invLf);
+                    dy = sep_ds(Hi.y, li.y, Hj.y, lj.y, rp.Lhi, rp.Llo, rp.invLf);
+                    dz = sep_ds(Hi.z, li.z, Hj.z, lj.z, rp.Lhi, rp.Llo, rp.invLf);
+                } else {
+                    dx = sep_f(Hi.x, Hj.x, rp.Lhi, rp.invLf);
+                    dy = sep_f(Hi.y, Hj.y, rp.Lhi, rp.invLf);
+                    dz = sep_f(Hi.z, Hj.z, rp.Lhi, rp.invLf);
+                }
+                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                const bool in = (k0 + u < nn) && (r2 < (tj ? pr.rc2[1] : pr.rc2[0]));
                 const float sig2 = tj ? pr.sig2[1] : pr.sig2[0];
                 const float eps48 = tj ? pr.eps48[1] : pr.eps48[0];
-                const float ir2 = __frcp_rn(r2);
+                const float ir2 = __fdividef(1.0f, in ? r2 : 1.0f);
                 const float s2 = sig2 * ir2;
                 const float s6 = s2 * s2 * s2;
-                const float fr = eps48 * ir2 * s6 * (s6 - 0.5f);
-                if constexpr (P == MIXED) {
-                    kahan_add(sx, cx, fr * dx);
-                    kahan_add(sy, cy, fr * dy);
-                    kahan_add(sz, cz, fr * dz);
-                } else {
-                    sx += fr * dx;
-                    sy += fr * dy;
-                    sz += fr * dz;
-                }
+                const float fr = in ? eps48 * ir2 * s6 * (s6 - 0.5f) : 0.0f;
+                gx = fmaf(fr, dx, gx);
+                gy = fmaf(fr, dy, gy);
+                gz = fmaf(fr, dz, gz);
                 if (SAMPLE) {
                     const float eps4 = tj ? pr.eps4[1] : pr.eps4[0];
                     const float shift = tj ? pr.shift[1] : pr.shift[0];
-                    en += eps4 * s6 * (s6 - 1.0f) - shift;
+                    en += in ? eps4 * s6 * (s6 - 1.0f) - shift : 0.0f;
                     vir += fr * r2;
                     wxx += fr * dx * dx; wyy += fr * dy * dy; wzz += fr * dz * dz;
                     wxy += fr * dx * dy; wxz += fr * dx * dz; wyz += fr * dy * dz;
                 }
             }
+            if constexpr (P == MIXED) {
+                kahan_add(sx, cx, gx);
+                kahan_add(sy, cy, gy);
+                kahan_add(sz, cz, gz);
+            } else {
+                sx += gx;
+                sy += gy;
+                sz += gz;
+            }
         }
-        // combine the lanes of one particle
-        float fx, fy, fz;
         if constexpr (P == MIXED) {
             ds ax = ds_from(sx, -cx), ay = ds_from(sy, -cy), az = ds_from(sz, -cz);
 #pragma unroll
@@ -684,20 +655,141 @@ __device__ __forceinline__ void force_impl(const KArgs &a)
 #pragma unroll
                 for (int k = 0; k < 8; ++k)
                     d[k] += __shfl_xor_sync(0xffffffffu, d[k], o);
-            if (valid && lane == 0)
-#pragma unroll
-                for (int k = 0; k < 8; ++k)
-                    acc[k] = 0.5 * d[k];
-        }
-        if (valid && lane == 0)
-            ((float4 *)a.force)[i] = make_float4(fx, fy, fz, SAMPLE ? (float)acc[0] : 0.0f);
-    }
-    if (SAMPLE) {
-        block_sum<8>(acc, sh);
-        if (threadIdx.x == 0)
 #pragma unroll
             for (int k = 0; k < 8; ++k)
-                a.part_f[(size_t)blockIdx.x * 8 + k] = acc[k];
+                acc[k] = 0.5 * d[k];
+        }
+    }
+}
+
+// Potential energy, virial and virial tensor of particle ii (half of each pair,
+// Sec. 2.2 reductions), as a separate pass over the list on sample steps so
+// that the force loop carries no energy accumulators.  acc[0..7] = E, W, W_ab.
+template <int P, int TPP>
+__device__ __forceinline__ void pair_energy(const KArgs &a, const Rep &rp, int pp, int ii, int nn, double *acc)
+{
+    const int lane = threadIdx.x & (TPP - 1);
+    const int *lst = a.nbr + (size_t)ii * (size_t)a.K;
+    FT<P> d8[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    if constexpr (P == FP64) {
+        const d4 *pos = (const d4 *)pos_a(a, pp);
+        const d4 xi = pos[ii];
+        const int ti = species_of(xi.w);
+        for (int k = lane; k < nn; k += TPP) {
+            const d4 xj = pos[__ldg(lst + k)];
+            const int ab = ti * 2 + species_of(xj.w);
+            const double dx = sep_d(xi.x, xj.x, rp.L, rp.invL);
+            const double dy = sep_d(xi.y, xj.y, rp.L, rp.invL);
+            const double dz = sep_d(xi.z, xj.z, rp.L, rp.invL);
+            const double r2 = dx * dx + dy * dy + dz * dz;
+            if (r2 < a.tab.rc2d[ab]) {
+                const double ir2 = 1.0 / r2;
+                const double s2 = a.tab.sig2d[ab] * ir2;
+                const double s6 = s2 * s2 * s2;
+                const double fr = a.tab.eps48d[ab] * ir2 * s6 * (s6 - 0.5);
+                d8[0] += a.tab.eps4d[ab] * s6 * (s6 - 1.0) - a.tab.shiftd[ab];
+                d8[1] += fr * r2;
+                d8[2] += fr * dx * dx; d8[3] += fr * dy * dy; d8[4] += fr * dz * dz;
+                d8[5] += fr * dx * dy; d8[6] += fr * dx * dz; d8[7] += fr * dy * dz;
+            }
+        }
+    } else {
+        const float4 *pos = (const float4 *)pos_a(a, pp);
+        const float4 *posl = (const float4 *)pos_b(a, pp);
+        const float4 Hi = pos[ii];
+        float4 li = make_float4(0.f, 0.f, 0.f, 0.f);
+        if constexpr (P == MIXED)
+            li = posl[ii];
+        const int ti = species_of(Hi.w);
+        for (int k = lane; k < nn; k += TPP) {
+            const int j = __ldg(lst + k);
+            const float4 Hj = __ldg(pos + j);
+            const int ab = ti * 2 + species_of(Hj.w);
+            float dx, dy, dz;
+            if constexpr (P == MIXED) {
+                const float4 lj = __ldg(posl + j);
+                dx = sep_ds(Hi.x, li.x, Hj.x, lj.x, rp.Lhi, rp.Llo, rp.invLf);
+                dy = sep_ds(Hi.y, li.y, Hj.y, lj.y, rp.Lhi, rp.Llo, rp.invLf);
+                dz = sep_ds(Hi.z, li.z, Hj.z, lj.z, rp.Lhi, rp.Llo, rp.invLf);
+            } else {
+                dx = sep_f(Hi.x, Hj.x, rp.Lhi, rp.invLf);
+                dy = sep_f(Hi.y, Hj.y, rp.Lhi, rp.invLf);
+                dz = sep_f(Hi.z, Hj.z, rp.Lhi, rp.invLf);
+            }
+            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            if (r2 < a.tab.rc2[ab]) {
+                const float ir2 = __fdividef(1.0f, r2);
+                const float s2 = a.tab.sig2[ab] * ir2;
+                const float s6 = s2 * s2 * s2;
+                const float fr = a.tab.eps48[ab] * ir2 * s6 * (s6 - 0.5f);
+                d8[0] += a.tab.eps4[ab] * s6 * (s6 - 1.0f) - a.tab.shift[ab];
+                d8[1] += fr * r2;
+                d8[2] += fr * dx * dx; d8[3] += fr * dy * dy; d8[4] += fr * dz * dz;
+                d8[5] += fr * dx * dy; d8[6] += fr * dx * dz; d8[7] += fr * dy * dz;
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        double v = (double)d8[k];
+#pragma unroll
+        for (int o = TPP / 2; o > 0; o >>= 1)
+            v += __shfl_xor_sync(0xffffffffu, v, o);
+        acc[k] = 0.5 * v;
+    }
+}
+
+template <int P>
+__device__ __forceinline__ void store_force(const KArgs &a, int i, FT<P> fx, FT<P> fy, FT<P> fz, double e)
+{
+    if constexpr (P == FP64) {
+        d4 f;
+        f.x = fx; f.y = fy; f.z = fz; f.w = e;
+        ((d4 *)a.force)[i] = f;
+    } else {
+        ((float4 *)a.force)[i] = make_float4(fx, fy, fz, (float)e);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_force: forces (and on request the potential-side reductions) at the
+// current positions; used when a handle is created or its state replaced and
+// by md_compute_forces.
+// ---------------------------------------------------------------------------
+template <int P, int TPP, bool SAMPLE>
+__device__ __forceinline__ void force_only(const KArgs &a)
+{
+    __shared__ double sh[32 * kPartF];
+    const Ctl *ctl = a.ctl;
+    const int pp = ctl->pos_par;
+    const int4 b = a.blk_f[blockIdx.x];
+    const Rep rp = a.rep[b.z];
+    const int lane = threadIdx.x & (TPP - 1);
+    const int i = b.x + (int)(threadIdx.x / TPP);
+    const bool valid = i < b.y;
+    const int ii = valid ? i : b.x;
+    const int nn = valid ? a.nnbr[ii] : 0;
+    FT<P> fx, fy, fz;
+    double acc[kPartF];
+#pragma unroll
+    for (int k = 0; k < kPartF; ++k)
+        acc[k] = 0.0;
+    pair_forces<P, TPP, false>(a, rp, pp, ii, nn, fx, fy, fz, acc);
+    if (SAMPLE)
+        pair_energy<P, TPP>(a, rp, pp, ii, nn, acc);
+    if (!(valid && lane == 0)) {
+#pragma unroll
+        for (int k = 0; k < kPartF; ++k)
+            acc[k] = 0.0;
+    }
+    if (valid && lane == 0)
+        store_force<P>(a, i, fx, fy, fz, SAMPLE ? acc[0] : 0.0);
+    if (SAMPLE) {
+        block_sum<kPartF>(acc, sh);
+        if (threadIdx.x == 0)
+#pragma unroll
+            for (int k = 0; k < kPartF; ++k)
+                a.part_f[(size_t)blockIdx.x * kPartF + k] = acc[k];
     }
 }
 
@@ -709,11 +801,459 @@ __global__ void __launch_bounds__(kForceBlock) k_force(KArgs a)
         return;
     if (blockIdx.x == 0 && threadIdx.x == 0)
         atomicAdd((unsigned long long *)&a.ctl->n_force, 1ull);
-    const bool sample = a.fsample || (ctl->step % a.si) == 0;
-    if (sample)
-        force_impl<P, TPP, true>(a);
+    if (a.fsample || (ctl->step % a.si) == 0)
+        force_only<P, TPP, true>(a);
     else
-        force_impl<P, TPP, false>(a);
+        force_only<P, TPP, false>(a);
+}
+
+// ---------------------------------------------------------------------------
+// k_step: one whole MD step.  Positions r(t) (current buffer), forces f(t)
+// from the list, then per particle: v(t) = v(t-1/2) + dt/2m f(t) [sample],
+// and unless this is the last step of md_step: v(t+1/2) = v(t) + dt/2m f(t),
+// r(t+1) = r(t) + dt v(t+1/2) into the other buffer.  Last block: step
+// counter, buffer flip, sample record, rebuild decision, graph conditions.
+// ---------------------------------------------------------------------------
+// One Cartesian component of the velocity-Verlet update, done by lane c of
+// the particle's group: half kick(s), drift, re-anchor / wrap, displacement
+// from the build position.  vh/vl: velocity component (hi/lo for MIXED, vh
+// alone otherwise); returns the squared displacement component.
+template <int P>
+__device__ __forceinline__ void component_update(const KArgs &a, const Rep &rp, int pp, int spar, int i, int c,
+                                                 int sp, float f_c, double f_cd, bool sample, bool last,
+                                                 float &vh, float &vl, double &vd, float rr,
+                                                 double &ke, double &pc, float &dd, float &vv, unsigned int &bad)
+{
+    const size_t e = 4 * (size_t)i + c;
+    if constexpr (P == MIXED) {
+        const ds hk = ds_from(a.hdtm_hi[sp], a.hdtm_lo[sp]);
+        ds v = ds_add(ds_from(vh, vl), ds_mul_f(hk, f_c));
+        if (sample) {
+            const double x = ds_to_double(v);
+            ke = 0.5 * a.mass[sp] * x * x;
+            pc = a.mass[sp] * x;
+        }
+        if (!last) {
+            v = ds_add(v, ds_mul_f(hk, f_c));
+            const ds s = ds_mul(ds_from(a.dt_hi, a.dt_lo), v);
+            if (fabsf(s.hi) > 0.25f * rp.Lhi)
+                bad |= ST_UNSTABLE;
+            const float H = ((const float *)pos_a(a, pp))[e], l = ((const float *)pos_b(a, pp))[e];
+            float Hn, ln;
+            const int dimg = anchor_wrap(ds_add(ds_from(H, l), s), rp.grid, rp.inv_grid, rp.Lhi, rp.Llo, Hn, ln);
+            if (!isfinite(Hn))
+                bad |= ST_NONFINITE;
+            ((float *)pos_a(a, pp ^ 1))[e] = Hn;
+            ((float *)pos_b(a, pp ^ 1))[e] = ln;
+            const float dx = __fadd_rn(sep_f(Hn, rr, rp.Lhi, rp.invLf), ln);
+            dd = dx * dx;
+            vv = v.hi * v.hi;
+            if (dimg)
+                ((int *)img_of(a, spar))[e] += dimg;
+        }
+        vh = v.hi;
+        vl = v.lo;
+    } else if constexpr (P == FP64) {
+        const double hk = a.hdtm[sp];
+        double v = vd + hk * f_cd;
+        if (sample) {
+            ke = 0.5 * a.mass[sp] * v * v;
+            pc = a.mass[sp] * v;
+        }
+        if (!last) {
+            v += hk * f_cd;
+            const double s = a.dt * v;
+            if (fabs(s) > 0.25 * rp.L)
+                bad |= ST_UNSTABLE;
+            double x = ((const double *)pos_a(a, pp))[e] + s;
+            int dimg = 0;
+            if (x >= rp.L) { x -= rp.L; dimg = 1; } else if (x < 0.0) { x += rp.L; dimg = -1; }
+            if (!isfinite(x))
+                bad |= ST_NONFINITE;
+            ((double *)pos_a(a, pp ^ 1))[e] = x;
+            const float dx = sep_f(__double2float_rn(x), rr, rp.Lhi, rp.invLf);
+            dd = dx * dx;
+            vv = (float)(v * v);
+            if (dimg)
+                ((int *)img_of(a, spar))[e] += dimg;
+        }
+        vd = v;
+    } else {
+        const float hk = a.hdtm_hi[sp];
+        float v = vh + hk * f_c;
+        if (sample) {
+            ke = 0.5 * a.mass[sp] * (double)v * (double)v;
+            pc = a.mass[sp] * (double)v;
+        }
+        if (!last) {
+            v += hk * f_c;
+            const float s = a.dt_hi * v;
+            const float L = rp.Lhi;
+            if (fabsf(s) > 0.25f * L)
+                bad |= ST_UNSTABLE;
+            float x = ((const float *)pos_a(a, pp))[e] + s;
+            int dimg = 0;
+            if (x >= L) { x -= L; dimg = 1; } else if (x < 0.f) { x += L; dimg = -1; }
+            if (x >= L) x = 0.f;
+            if (!isfinite(x))
+                bad |= ST_NONFINITE;
+            ((float *)pos_a(a, pp ^ 1))[e] = x;
+            const float dx = sep_f(x, rr, L, rp.invLf);
+            dd = dx * dx;
+            vv = v * v;
+            if (dimg)
+                ((int *)img_of(a, spar))[e] += dimg;
+        }
+        vh = v;
+    }
+}
+
+// Step body for groups of at least 4 lanes: lanes 0-2 own one component each
+// of the update, lane 3 copies the species word; the operands of the update
+// are loaded before the neighbour loop so their latency is hidden.
+template <int P, int TPP, bool SAMPLE>
+__device__ __forceinline__ void step_body_split(const KArgs &a, bool active, bool last, int pp, int spar,
+                                                double *part, float &d2, float &v2, float &a2, unsigned int &bad)
+{
+    const int4 b = a.blk_f[blockIdx.x];
+    const Rep rp = a.rep[b.z];
+    const int lane = threadIdx.x & (TPP - 1);
+    const int i = b.x + (int)(threadIdx.x / TPP);
+    const bool valid = active && i < b.y;
+    const int ii = (i < b.y) ? i : b.x;
+    const int nn = valid ? a.nnbr[ii] : 0;
+    const int c = lane;
+    const size_t e = 4 * (size_t)ii + (c < 4 ? c : 0);
+    float vh = 0.f, vl = 0.f, rr = 0.f;
+    double vd = 0.0;
+    if (valid && c < 3) {
+        if constexpr (P == FP64) {
+            vd = ((const double *)vel_a(a, spar))[e];
+        } else {
+            vh = ((const float *)vel_a(a, spar))[e];
+            if constexpr (P == MIXED)
+                vl = ((const float *)vel_b(a, spar))[e];
+        }
+        rr = ((const float *)a.rref)[e];
+    }
+    FT<P> fx = 0, fy = 0, fz = 0;
+#pragma unroll
+    for (int k = 0; k < kPartF; ++k)
+        part[k] = 0.0;
+    pair_forces<P, TPP, false>(a, rp, pp, ii, nn, fx, fy, fz, part);
+    if (SAMPLE)
+        pair_energy<P, TPP>(a, rp, pp, ii, nn, part);
+    // Every lane of the warp must reach the shuffles below, including the
+    // lanes of padding particles past the end of a replica's range: they skip
+    // the update and contribute zeros.
+    int sp = 0;
+    if (valid) {
+        if constexpr (P == FP64)
+            sp = species_of(((const double *)pos_a(a, pp))[4 * (size_t)i + 3]);
+        else
+            sp = species_of(((const float *)pos_a(a, pp))[4 * (size_t)i + 3]);
+    }
+    if (valid && lane == 0)
+        store_force<P>(a, i, fx, fy, fz, SAMPLE ? part[0] : 0.0);
+    double ke = 0.0, p3[3] = {0.0, 0.0, 0.0};
+    float dd = 0.f, vv = 0.f;
+    if (!valid) {
+        // no update
+    } else if (c < 3) {
+        const FT<P> f_c = c == 0 ? fx : (c == 1 ? fy : fz);
+        double pc = 0.0;
+        component_update<P>(a, rp, pp, spar, i, c, sp, (float)f_c, (double)f_c, SAMPLE, last, vh, vl, vd, rr,
+                            ke, pc, dd, vv, bad);
+        p3[0] = c == 0 ? pc : 0.0;
+        p3[1] = c == 1 ? pc : 0.0;
+        p3[2] = c == 2 ? pc : 0.0;
+        if constexpr (P == FP64) {
+            ((double *)vel_a(a, spar))[e] = vd;
+        } else {
+            ((float *)vel_a(a, spar))[e] = vh;
+            if constexpr (P == MIXED)
+                ((float *)vel_b(a, spar))[e] = vl;
+        }
+    } else if (c == 3 && !last) {
+        // the species word travels with the position
+        if constexpr (P == FP64)
+            ((double *)pos_a(a, pp ^ 1))[4 * (size_t)i + 3] = ((const double *)pos_a(a, pp))[4 * (size_t)i + 3];
+        else
+            ((float *)pos_a(a, pp ^ 1))[4 * (size_t)i + 3] = ((const float *)pos_a(a, pp))[4 * (size_t)i + 3];
+    }
+    // combine the component lanes (the first four lanes of the group)
+#pragma unroll
+    for (int o = 2; o > 0; o >>= 1) {
+        dd += __shfl_xor_sync(0xffffffffu, dd, o);
+        vv += __shfl_xor_sync(0xffffffffu, vv, o);
+        if (SAMPLE) {
+            ke += __shfl_xor_sync(0xffffffffu, ke, o);
+            p3[0] += __shfl_xor_sync(0xffffffffu, p3[0], o);
+            p3[1] += __shfl_xor_sync(0xffffffffu, p3[1], o);
+            p3[2] += __shfl_xor_sync(0xffffffffu, p3[2], o);
+        }
+    }
+    if (!valid || lane != 0) {
+#pragma unroll
+        for (int k = 0; k < kPartF; ++k)
+            part[k] = 0.0;
+        return;
+    }
+    if (SAMPLE) {
+        part[8] = ke;
+        part[9] = p3[0];
+        part[10] = p3[1];
+        part[11] = p3[2];
+    }
+    if (!last) {
+        d2 = dd;
+        v2 = vv;
+        const float im = a.inv_mass[sp];
+        const float f2 = (float)(fx * fx + fy * fy + fz * fz);
+        a2 = f2 * im * im;
+    }
+}
+
+template <int P, int TPP, bool SAMPLE>
+__device__ __forceinline__ void step_body(const KArgs &a, bool active, bool last, int pp, int spar,
+                                          double *part, float &d2, float &v2, float &a2, unsigned int &bad)
+{
+    if constexpr (TPP >= 4) {
+        step_body_split<P, TPP, SAMPLE>(a, active, last, pp, spar, part, d2, v2, a2, bad);
+        return;
+    }
+    const int4 b = a.blk_f[blockIdx.x];
+    const Rep rp = a.rep[b.z];
+    const int lane = threadIdx.x & (TPP - 1);
+    const int i = b.x + (int)(threadIdx.x / TPP);
+    const bool valid = active && i < b.y;
+    const int ii = (i < b.y) ? i : b.x;
+    const int nn = valid ? a.nnbr[ii] : 0;
+    FT<P> fx = 0, fy = 0, fz = 0;
+#pragma unroll
+    for (int k = 0; k < kPartF; ++k)
+        part[k] = 0.0;
+    pair_forces<P, TPP, false>(a, rp, pp, ii, nn, fx, fy, fz, part);
+    if (SAMPLE)
+        pair_energy<P, TPP>(a, rp, pp, ii, nn, part);
+    if (!(valid && lane == 0)) {
+#pragma unroll
+        for (int k = 0; k < kPartF; ++k)
+            part[k] = 0.0;
+        return;
+    }
+    store_force<P>(a, i, fx, fy, fz, SAMPLE ? part[0] : 0.0);
+    PState<P> s;
+    load_pos<P>(a, pp, i, s);
+    load_vel<P>(a, spar, i, s);
+    half_kick<P>(a, s, fx, fy, fz);                 // completes v(t)
+    if (SAMPLE)
+        kinetic<P>(a, s, part + 8);
+    if (!last) {
+        half_kick<P>(a, s, fx, fy, fz);             // v(t + 1/2)
+        d2 = drift<P>(a, rp, s, pp ^ 1, spar, i, bad);
+        v2 = speed2(s);
+        const float im = a.inv_mass[s.sp];
+        const float f2 = (float)(fx * fx + fy * fy + fz * fz);
+        a2 = f2 * im * im;
+    }
+    store_vel<P>(a, spar, i, s);
+}
+
+template <int P, int TPP>
+__global__ void __launch_bounds__(kForceBlock) k_step(KArgs a)
+{
+    __shared__ double sh[32 * kPartF];
+    __shared__ float shf[96];
+    __shared__ int s_last;
+    __shared__ float s_m[3];
+    Ctl *ctl = a.ctl;
+    const unsigned int st0 = ctl->status;
+    const long long step = ctl->step;
+    const long long remaining = ctl->remaining;
+    const int pp = ctl->pos_par, spar = ctl->state_par;
+    const bool active = st0 == 0u && remaining > 0;
+    const bool last = remaining == 1;
+    const bool sample = active && (step % a.si) == 0;
+
+    double part[kPartF];
+    float d2 = 0.f, v2 = 0.f, a2 = 0.f;
+    unsigned int bad = 0u;
+    if (sample)
+        step_body<P, TPP, true>(a, active, last, pp, spar, part, d2, v2, a2, bad);
+    else
+        step_body<P, TPP, false>(a, active, last, pp, spar, part, d2, v2, a2, bad);
+    if (bad)
+        atomicOr(&ctl->status, bad);
+
+    block_max3(d2, v2, a2, shf);
+    if (sample)
+        block_sum<kPartF>(part, sh);
+    if (threadIdx.x == 0) {
+        if (sample)
+#pragma unroll
+            for (int k = 0; k < kPartF; ++k)
+                a.part_f[(size_t)blockIdx.x * kPartF + k] = part[k];
+        if (d2 > 0.f)
+            atomicMax(&ctl->maxdisp2, __float_as_uint(d2));
+        if (v2 > 0.f)
+            atomicMax(&ctl->maxv2, __float_as_uint(v2));
+        if (a2 > 0.f)
+            atomicMax(&ctl->maxa2, __float_as_uint(a2));
+        __threadfence();
+        const unsigned int t = atomicAdd(&ctl->ticket, 1u);
+        s_last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!s_last)
+        return;
+
+    // ---- last block ----
+    __threadfence();
+    if (threadIdx.x == 0) {
+        s_m[0] = __uint_as_float(atomicExch(&ctl->maxdisp2, 0u));
+        s_m[1] = __uint_as_float(atomicExch(&ctl->maxv2, 0u));
+        s_m[2] = __uint_as_float(atomicExch(&ctl->maxa2, 0u));
+    }
+    __syncthreads();
+    const unsigned int st = atomicOr(&ctl->status, 0u);
+    if (sample && st == 0u)
+        finish_reductions(a, IM_LOOP, true, step, s_m[0], sh);
+    if (threadIdx.x == 0) {
+        const bool drifted = active && !last;
+        unsigned int reb = 0u;
+        if (drifted && st == 0u) {
+            reb = need_rebuild(a, s_m[0], s_m[1], s_m[2]);
+            ctl->step = step + 1;
+            ctl->pos_par = pp ^ 1;
+            ctl->last_maxdisp2 = s_m[0];
+        }
+        ctl->rebuild = reb;
+        if (sample && st == 0u)
+            ctl->obs_count += 1;
+        long long rem = remaining;
+        if (active)
+            rem -= 1;
+        ctl->remaining = rem;
+        const long long bud = ctl->budget - 1;
+        ctl->budget = bud;
+        unsigned int s2 = st;
+        if (bud <= 0 && rem > 0) {
+            atomicOr(&ctl->status, ST_TIMEOUT);
+            s2 |= ST_TIMEOUT;
+        }
+        ctl->ticket = 0u;
+        ctl->n_integrate += 1;
+        if (a.use_cond) {
+            if (a.set_rebuild)
+                cudaGraphSetConditional(a.h_rebuild, reb);
+            if (a.set_loop)
+                cudaGraphSetConditional(a.h_loop, (s2 == 0u && rem > 0) ? 1u : 0u);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_integrate: the per-particle half kick + drift that opens md_step
+// (IM_FIRST), and the kinetic reductions alone (IM_SAMPLE, IM_TOTALS, IM_KE).
+// ---------------------------------------------------------------------------
+template <int P>
+__global__ void __launch_bounds__(kIntBlock) k_integrate(KArgs a)
+{
+    __shared__ double sh[32 * 12];
+    __shared__ float shf[96];
+    __shared__ int s_last;
+    __shared__ float s_m[3];
+    Ctl *ctl = a.ctl;
+    const unsigned int st0 = ctl->status;
+    const bool halted = st0 != 0u;
+    const long long step = ctl->step;
+    const int pp = ctl->pos_par, spar = ctl->state_par;
+    const int mode = a.imode;
+    const bool first = mode == IM_FIRST;
+    const bool rec = !first;
+
+    const int4 b = a.blk_i[blockIdx.x];
+    const Rep rp = a.rep[b.z];
+    const int i = b.x + threadIdx.x;
+    const bool valid = (i < b.y) && !halted;
+    float d2 = 0.f, v2 = 0.f, a2 = 0.f;
+    double kin[4] = {0.0, 0.0, 0.0, 0.0};
+    unsigned int bad = 0u;
+    if (valid) {
+        PState<P> s;
+        load_pos<P>(a, pp, i, s);
+        load_vel<P>(a, spar, i, s);
+        if (rec)
+            kinetic<P>(a, s, kin);
+        if (first) {
+            FT<P> f[3];
+            if constexpr (P == FP64) {
+                const d4 q = ((const d4 *)a.force)[i];
+                f[0] = q.x; f[1] = q.y; f[2] = q.z;
+            } else {
+                const float4 q = ((const float4 *)a.force)[i];
+                f[0] = q.x; f[1] = q.y; f[2] = q.z;
+            }
+            half_kick<P>(a, s, f[0], f[1], f[2]);
+            d2 = drift<P>(a, rp, s, pp ^ 1, spar, i, bad);
+            v2 = speed2(s);
+            const float im = a.inv_mass[s.sp];
+            const float f2 = (float)(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
+            a2 = f2 * im * im;
+            store_vel<P>(a, spar, i, s);
+        }
+    }
+    if (bad)
+        atomicOr(&ctl->status, bad);
+    block_max3(d2, v2, a2, shf);
+    if (rec)
+        block_sum<4>(kin, sh);
+    if (threadIdx.x == 0) {
+        if (rec)
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                a.part_i[(size_t)blockIdx.x * 4 + k] = kin[k];
+        if (d2 > 0.f)
+            atomicMax(&ctl->maxdisp2, __float_as_uint(d2));
+        if (v2 > 0.f)
+            atomicMax(&ctl->maxv2, __float_as_uint(v2));
+        if (a2 > 0.f)
+            atomicMax(&ctl->maxa2, __float_as_uint(a2));
+        __threadfence();
+        const unsigned int t = atomicAdd(&ctl->ticket, 1u);
+        s_last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!s_last)
+        return;
+    __threadfence();
+    if (threadIdx.x == 0) {
+        s_m[0] = __uint_as_float(atomicExch(&ctl->maxdisp2, 0u));
+        s_m[1] = __uint_as_float(atomicExch(&ctl->maxv2, 0u));
+        s_m[2] = __uint_as_float(atomicExch(&ctl->maxa2, 0u));
+    }
+    __syncthreads();
+    const unsigned int st = atomicOr(&ctl->status, 0u);
+    if (rec && st == 0u)
+        finish_reductions(a, mode, false, step, s_m[0], sh);
+    if (threadIdx.x == 0) {
+        unsigned int reb = 0u;
+        if (first && !halted && st == 0u) {
+            reb = need_rebuild(a, s_m[0], s_m[1], s_m[2]);
+            ctl->step = step + 1;
+            ctl->pos_par = pp ^ 1;
+            ctl->last_maxdisp2 = s_m[0];
+        }
+        if (first)
+            ctl->rebuild = reb;
+        if (mode == IM_SAMPLE && st == 0u)
+            ctl->obs_count += 1;
+        ctl->ticket = 0u;
+        ctl->n_integrate += 1;
+        if (a.use_cond && a.set_rebuild)
+            cudaGraphSetConditional(a.h_rebuild, reb);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -721,8 +1261,9 @@ __global__ void __launch_bounds__(kForceBlock) k_force(KArgs a)
 // particles sorted by cell, start index of each cell) with the cells ordered
 // along a space-filling curve (the periodic reorder of Sec. 2.2).
 // Kernels: k_bin (cell key + histogram) -> k_scan -> k_scatter ->
-// k_permute (deterministic order inside a cell, gather of the state) ->
-// k_copyback -> k_nbuild.  Each returns at once unless a rebuild is pending.
+// k_permute (deterministic order inside a cell; gather of the state into the
+// other buffers) -> k_nbuild (lists from the permuted positions) -> k_flip.
+// Each returns at once unless a rebuild is pending.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ bool rebuild_pending(const Ctl *ctl)
 {
@@ -756,14 +1297,15 @@ __global__ void __launch_bounds__(kIntBlock) k_bin(KArgs a)
     if (i >= b.y)
         return;
     const Rep rp = a.rep[b.z];
+    const int pp = ctl->pos_par;
     int cx, cy, cz;
     if constexpr (P == FP64) {
-        const d4 x = ((const d4 *)a.pa)[i];
+        const d4 x = ((const d4 *)pos_a(a, pp))[i];
         cx = cell_coord(x.x, rp.cscale, rp.nc);
         cy = cell_coord(x.y, rp.cscale, rp.nc);
         cz = cell_coord(x.z, rp.cscale, rp.nc);
     } else {
-        const float4 x = ((const float4 *)a.pa)[i];
+        const float4 x = ((const float4 *)pos_a(a, pp))[i];
         cx = cell_coord_f(x.x, rp.cscalef, rp.nc);
         cy = cell_coord_f(x.y, rp.cscalef, rp.nc);
         cz = cell_coord_f(x.z, rp.cscalef, rp.nc);
@@ -839,7 +1381,7 @@ __global__ void __launch_bounds__(kIntBlock) k_scatter(KArgs a)
 
 // Final slot of each particle: its cell's start plus the number of particles
 // of the same cell with a smaller current index (stable, deterministic), then
-// gather of the whole state into the second buffers.
+// gather of the whole state into the other buffers.
 template <int P>
 __global__ void __launch_bounds__(kIntBlock) k_permute(KArgs a)
 {
@@ -851,6 +1393,7 @@ __global__ void __launch_bounds__(kIntBlock) k_permute(KArgs a)
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= a.n)
         return;
+    const int pp = ctl->pos_par, spar = ctl->state_par;
     const int i = a.tmpidx[s];
     const int k = a.key[i];
     const int b0 = a.cstart[k], b1 = a.cstart[k + 1];
@@ -859,49 +1402,22 @@ __global__ void __launch_bounds__(kIntBlock) k_permute(KArgs a)
         rank += (a.tmpidx[t] < i) ? 1 : 0;
     const int d = b0 + rank;
     if constexpr (P == FP64) {
-        const d4 x = ((const d4 *)a.pa)[i];
-        ((d4 *)a.pa2)[d] = x;
-        ((d4 *)a.va2)[d] = ((const d4 *)a.va)[i];
+        const d4 x = ((const d4 *)pos_a(a, pp))[i];
+        ((d4 *)pos_a(a, pp ^ 1))[d] = x;
+        ((d4 *)vel_a(a, spar ^ 1))[d] = ((const d4 *)vel_a(a, spar))[i];
         a.rref[d] = make_float4(__double2float_rn(x.x), __double2float_rn(x.y), __double2float_rn(x.z), 0.f);
     } else {
-        const float4 x = ((const float4 *)a.pa)[i];
-        ((float4 *)a.pa2)[d] = x;
-        ((float4 *)a.va2)[d] = ((const float4 *)a.va)[i];
+        const float4 x = ((const float4 *)pos_a(a, pp))[i];
+        ((float4 *)pos_a(a, pp ^ 1))[d] = x;
+        ((float4 *)vel_a(a, spar ^ 1))[d] = ((const float4 *)vel_a(a, spar))[i];
         if constexpr (P == MIXED) {
-            ((float4 *)a.pb2)[d] = ((const float4 *)a.pb)[i];
-            ((float4 *)a.vb2)[d] = ((const float4 *)a.vb)[i];
+            ((float4 *)pos_b(a, pp ^ 1))[d] = ((const float4 *)pos_b(a, pp))[i];
+            ((float4 *)vel_b(a, spar ^ 1))[d] = ((const float4 *)vel_b(a, spar))[i];
         }
         a.rref[d] = make_float4(x.x, x.y, x.z, 0.f);
     }
-    a.image2[d] = a.image[i];
+    img_of(a, spar ^ 1)[d] = img_of(a, spar)[i];
     a.cellof[d] = k;
-}
-
-template <int P>
-__global__ void __launch_bounds__(kIntBlock) k_copyback(KArgs a)
-{
-    Ctl *ctl = a.ctl;
-    if (!rebuild_pending(ctl))
-        return;
-    if (blockIdx.x == 0 && threadIdx.x == 0)
-        atomicAdd((unsigned long long *)&ctl->n_rebuild_k, 1ull);
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    for (int c = s; c < a.ncell; c += gridDim.x * blockDim.x)
-        a.ccount[c] = 0;
-    if (s >= a.n)
-        return;
-    if constexpr (P == FP64) {
-        ((d4 *)a.pa)[s] = ((const d4 *)a.pa2)[s];
-        ((d4 *)a.va)[s] = ((const d4 *)a.va2)[s];
-    } else {
-        ((float4 *)a.pa)[s] = ((const float4 *)a.pa2)[s];
-        ((float4 *)a.va)[s] = ((const float4 *)a.va2)[s];
-        if constexpr (P == MIXED) {
-            ((float4 *)a.pb)[s] = ((const float4 *)a.pb2)[s];
-            ((float4 *)a.vb)[s] = ((const float4 *)a.vb2)[s];
-        }
-    }
-    a.image[s] = a.image2[s];
 }
 
 // ---------------------------------------------------------------------------
@@ -909,6 +1425,9 @@ __global__ void __launch_bounds__(kIntBlock) k_copyback(KArgs a)
 // of its own and the adjacent cells (27, or all cells when fewer than three
 // fit along the box edge) and keeps those closer than r_c,ab + skin (plus a
 // rounding margin).  Particle-major list: nbr[i*K + k], coalesced per warp.
+// Distances are single precision in every mode (FP64 positions are rounded):
+// the list only has to contain every pair within r_c + skin, which the
+// margin guarantees.  Reads the permuted positions (other buffer).
 // ---------------------------------------------------------------------------
 template <int P>
 __global__ void __launch_bounds__(kNbBlock) k_nbuild(KArgs a)
@@ -924,6 +1443,7 @@ __global__ void __launch_bounds__(kNbBlock) k_nbuild(KArgs a)
     const int i = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
     if (i >= a.n)
         return;   // whole warp
+    const int pn = ctl->pos_par ^ 1;
     const int c = a.cellof[i];
     const int4 cc = a.cxyz[c];
     const Rep rp = a.rep[cc.w];
@@ -933,20 +1453,17 @@ __global__ void __launch_bounds__(kNbBlock) k_nbuild(KArgs a)
     const unsigned lt_mask = (1u << lane) - 1u;
     int cnt = 0;
 
-    // own position
-    double xd = 0, yd = 0, zd = 0;
-    float4 Hi = make_float4(0.f, 0.f, 0.f, 0.f), li = make_float4(0.f, 0.f, 0.f, 0.f);
-    int ti;
+    float4 Hi, li = make_float4(0.f, 0.f, 0.f, 0.f);
     if constexpr (P == FP64) {
-        const d4 x = ((const d4 *)a.pa)[i];
-        xd = x.x; yd = x.y; zd = x.z;
-        ti = species_of(x.w);
+        const d4 x = ((const d4 *)pos_a(a, pn))[i];
+        Hi = make_float4(__double2float_rn(x.x), __double2float_rn(x.y), __double2float_rn(x.z),
+                         __int_as_float(species_of(x.w)));
     } else {
-        Hi = ((const float4 *)a.pa)[i];
+        Hi = ((const float4 *)pos_a(a, pn))[i];
         if constexpr (P == MIXED)
-            li = ((const float4 *)a.pb)[i];
-        ti = species_of(Hi.w);
+            li = ((const float4 *)pos_b(a, pn))[i];
     }
+    const int ti = species_of(Hi.w);
     for (int dz = lo; dz <= hi; ++dz)
     for (int dy = lo; dy <= hi; ++dy)
     for (int dx = lo; dx <= hi; ++dx) {
@@ -957,17 +1474,18 @@ __global__ void __launch_bounds__(kNbBlock) k_nbuild(KArgs a)
             const int j = jb + lane;
             bool in = false;
             if (j < j1 && j != i) {
+                float ex, ey, ez;
+                int tj;
                 if constexpr (P == FP64) {
-                    const d4 y4 = ((const d4 *)a.pa)[j];
-                    const double ex = sep_d(xd, y4.x, rp.L, rp.invL);
-                    const double ey = sep_d(yd, y4.y, rp.L, rp.invL);
-                    const double ez = sep_d(zd, y4.z, rp.L, rp.invL);
-                    in = ex * ex + ey * ey + ez * ez < a.tab.rl2d[ti * 2 + species_of(y4.w)];
+                    const d4 y4 = ((const d4 *)pos_a(a, pn))[j];
+                    ex = sep_f(Hi.x, __double2float_rn(y4.x), rp.Lhi, rp.invLf);
+                    ey = sep_f(Hi.y, __double2float_rn(y4.y), rp.Lhi, rp.invLf);
+                    ez = sep_f(Hi.z, __double2float_rn(y4.z), rp.Lhi, rp.invLf);
+                    tj = species_of(y4.w);
                 } else {
-                    const float4 Hj = ((const float4 *)a.pa)[j];
-                    float ex, ey, ez;
+                    const float4 Hj = ((const float4 *)pos_a(a, pn))[j];
                     if constexpr (P == MIXED) {
-                        const float4 lj = ((const float4 *)a.pb)[j];
+                        const float4 lj = ((const float4 *)pos_b(a, pn))[j];
                         ex = sep_ds(Hi.x, li.x, Hj.x, lj.x, rp.Lhi, rp.Llo, rp.invLf);
                         ey = sep_ds(Hi.y, li.y, Hj.y, lj.y, rp.Lhi, rp.Llo, rp.invLf);
                         ez = sep_ds(Hi.z, li.z, Hj.z, lj.z, rp.Lhi, rp.Llo, rp.invLf);
@@ -976,8 +1494,9 @@ __global__ void __launch_bounds__(kNbBlock) k_nbuild(KArgs a)
                         ey = sep_f(Hi.y, Hj.y, rp.Lhi, rp.invLf);
                         ez = sep_f(Hi.z, Hj.z, rp.Lhi, rp.invLf);
                     }
-                    in = fmaf(ex, ex, fmaf(ey, ey, ez * ez)) < a.tab.rl2[ti * 2 + species_of(Hj.w)];
+                    tj = species_of(Hj.w);
                 }
+                in = fmaf(ex, ex, fmaf(ey, ey, ez * ez)) < a.tab.rl2[ti * 2 + tj];
             }
             const unsigned m = __ballot_sync(0xffffffffu, in);
             const int pre = __popc(m & lt_mask);
@@ -994,23 +1513,42 @@ __global__ void __launch_bounds__(kNbBlock) k_nbuild(KArgs a)
     }
 }
 
+// End of a rebuild: the permuted buffers become current; clear the histogram.
+template <int P>
+__global__ void __launch_bounds__(kIntBlock) k_flip(KArgs a)
+{
+    Ctl *ctl = a.ctl;
+    if (!rebuild_pending(ctl))
+        return;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    for (int c = t; c < a.ncell; c += gridDim.x * blockDim.x)
+        a.ccount[c] = 0;
+    if (t == 0) {
+        ctl->pos_par ^= 1;
+        ctl->state_par ^= 1;
+        atomicAdd((unsigned long long *)&ctl->n_rebuild_k, 1ull);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // state transfer between the staging area (original order, float64) and the
 // working layout; misc. control kernels
 // ---------------------------------------------------------------------------
-// Load the staged state into slot order = original order, wrap into [0, L),
-// split into the precision's representation and request a rebuild.
+// Load the staged state into the current buffers in the original order, wrap
+// into [0, L), split into the precision's representation, request a rebuild.
 template <int P>
 __global__ void __launch_bounds__(kIntBlock) k_load(KArgs a)
 {
+    Ctl *ctl = a.ctl;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        a.ctl->rebuild = 1u;
-        atomicAdd((unsigned long long *)&a.ctl->n_other, 1ull);
+        ctl->rebuild = 1u;
+        atomicAdd((unsigned long long *)&ctl->n_other, 1ull);
     }
     const int4 b = a.blk_i[blockIdx.x];
     const int i = b.x + threadIdx.x;
     if (i >= b.y)
         return;
+    const int pp = ctl->pos_par, spar = ctl->state_par;
     const Rep rp = a.rep[b.z];
     const int sp = a.st_code[i];
     double x[3];
@@ -1030,8 +1568,8 @@ __global__ void __launch_bounds__(kIntBlock) k_load(KArgs a)
         d4 p, v;
         p.x = x[0]; p.y = x[1]; p.z = x[2]; p.w = __longlong_as_double((long long)sp);
         v.x = vv[0]; v.y = vv[1]; v.z = vv[2]; v.w = 0.0;
-        ((d4 *)a.pa)[i] = p;
-        ((d4 *)a.va)[i] = v;
+        ((d4 *)pos_a(a, pp))[i] = p;
+        ((d4 *)vel_a(a, spar))[i] = v;
     } else if constexpr (P == MIXED) {
         float H[3], l[3];
         for (int k = 0; k < 3; ++k) {
@@ -1040,46 +1578,48 @@ __global__ void __launch_bounds__(kIntBlock) k_load(KArgs a)
             H[k] = (float)h;
             l[k] = __double2float_rn(x[k] - h);
         }
-        ((float4 *)a.pa)[i] = make_float4(H[0], H[1], H[2], __int_as_float(sp));
-        ((float4 *)a.pb)[i] = make_float4(l[0], l[1], l[2], 0.f);
+        ((float4 *)pos_a(a, pp))[i] = make_float4(H[0], H[1], H[2], __int_as_float(sp));
+        ((float4 *)pos_b(a, pp))[i] = make_float4(l[0], l[1], l[2], 0.f);
         ds vx = ds_from_double(vv[0]), vy = ds_from_double(vv[1]), vz = ds_from_double(vv[2]);
-        ((float4 *)a.va)[i] = make_float4(vx.hi, vy.hi, vz.hi, 0.f);
-        ((float4 *)a.vb)[i] = make_float4(vx.lo, vy.lo, vz.lo, 0.f);
+        ((float4 *)vel_a(a, spar))[i] = make_float4(vx.hi, vy.hi, vz.hi, 0.f);
+        ((float4 *)vel_b(a, spar))[i] = make_float4(vx.lo, vy.lo, vz.lo, 0.f);
     } else {
         float fx = __double2float_rn(x[0]), fy = __double2float_rn(x[1]), fz = __double2float_rn(x[2]);
         const float L = rp.Lhi;
         if (fx >= L) fx = 0.f;
         if (fy >= L) fy = 0.f;
         if (fz >= L) fz = 0.f;
-        ((float4 *)a.pa)[i] = make_float4(fx, fy, fz, __int_as_float(sp));
-        ((float4 *)a.va)[i] = make_float4((float)vv[0], (float)vv[1], (float)vv[2], 0.f);
+        ((float4 *)pos_a(a, pp))[i] = make_float4(fx, fy, fz, __int_as_float(sp));
+        ((float4 *)vel_a(a, spar))[i] = make_float4((float)vv[0], (float)vv[1], (float)vv[2], 0.f);
     }
-    a.image[i] = make_int4(im[0], im[1], im[2], i);
+    img_of(a, spar)[i] = make_int4(im[0], im[1], im[2], i);
 }
 
 // Write the state back to the staging area in the original order.
 template <int P>
 __global__ void __launch_bounds__(kIntBlock) k_getstate(KArgs a)
 {
+    const Ctl *ctl = a.ctl;
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (blockIdx.x == 0 && threadIdx.x == 0)
         atomicAdd((unsigned long long *)&a.ctl->n_other, 1ull);
     if (s >= a.n)
         return;
-    const int4 im = a.image[s];
+    const int pp = ctl->pos_par, spar = ctl->state_par;
+    const int4 im = img_of(a, spar)[s];
     const size_t t = (size_t)im.w;
     double x[3], v[3];
     if constexpr (P == FP64) {
-        const d4 p = ((const d4 *)a.pa)[s], w = ((const d4 *)a.va)[s];
+        const d4 p = ((const d4 *)pos_a(a, pp))[s], w = ((const d4 *)vel_a(a, spar))[s];
         x[0] = p.x; x[1] = p.y; x[2] = p.z;
         v[0] = w.x; v[1] = w.y; v[2] = w.z;
     } else if constexpr (P == MIXED) {
-        const float4 H = ((const float4 *)a.pa)[s], l = ((const float4 *)a.pb)[s];
-        const float4 vh = ((const float4 *)a.va)[s], vl = ((const float4 *)a.vb)[s];
+        const float4 H = ((const float4 *)pos_a(a, pp))[s], l = ((const float4 *)pos_b(a, pp))[s];
+        const float4 vh = ((const float4 *)vel_a(a, spar))[s], vl = ((const float4 *)vel_b(a, spar))[s];
         x[0] = (double)H.x + (double)l.x; x[1] = (double)H.y + (double)l.y; x[2] = (double)H.z + (double)l.z;
         v[0] = (double)vh.x + (double)vl.x; v[1] = (double)vh.y + (double)vl.y; v[2] = (double)vh.z + (double)vl.z;
     } else {
-        const float4 p = ((const float4 *)a.pa)[s], w = ((const float4 *)a.va)[s];
+        const float4 p = ((const float4 *)pos_a(a, pp))[s], w = ((const float4 *)vel_a(a, spar))[s];
         x[0] = p.x; x[1] = p.y; x[2] = p.z;
         v[0] = w.x; v[1] = w.y; v[2] = w.z;
     }
@@ -1095,12 +1635,13 @@ __global__ void __launch_bounds__(kIntBlock) k_getstate(KArgs a)
 template <int P>
 __global__ void __launch_bounds__(kIntBlock) k_expforce(KArgs a)
 {
+    const Ctl *ctl = a.ctl;
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (blockIdx.x == 0 && threadIdx.x == 0)
         atomicAdd((unsigned long long *)&a.ctl->n_other, 1ull);
     if (s >= a.n)
         return;
-    const size_t t = (size_t)a.image[s].w;
+    const size_t t = (size_t)img_of(a, ctl->state_par)[s].w;
     double f[4];
     if constexpr (P == FP64) {
         const d4 q = ((const d4 *)a.force)[s];
@@ -1119,7 +1660,8 @@ __global__ void __launch_bounds__(kIntBlock) k_expforce(KArgs a)
 template <int P>
 __global__ void __launch_bounds__(kIntBlock) k_scale(KArgs a)
 {
-    if (a.ctl->status)
+    const Ctl *ctl = a.ctl;
+    if (ctl->status)
         return;
     if (blockIdx.x == 0 && threadIdx.x == 0)
         atomicAdd((unsigned long long *)&a.ctl->n_other, 1ull);
@@ -1127,23 +1669,24 @@ __global__ void __launch_bounds__(kIntBlock) k_scale(KArgs a)
     const int i = b.x + threadIdx.x;
     if (i >= b.y)
         return;
+    const int spar = ctl->state_par;
     const double f = a.scale[b.z];
     if constexpr (P == FP64) {
-        d4 v = ((d4 *)a.va)[i];
+        d4 v = ((d4 *)vel_a(a, spar))[i];
         v.x *= f; v.y *= f; v.z *= f;
-        ((d4 *)a.va)[i] = v;
+        ((d4 *)vel_a(a, spar))[i] = v;
     } else if constexpr (P == MIXED) {
         const ds fs = ds_from_double(f);
-        float4 vh = ((float4 *)a.va)[i], vl = ((float4 *)a.vb)[i];
+        float4 vh = ((float4 *)vel_a(a, spar))[i], vl = ((float4 *)vel_b(a, spar))[i];
         ds x = ds_mul(ds_from(vh.x, vl.x), fs), y = ds_mul(ds_from(vh.y, vl.y), fs),
            z = ds_mul(ds_from(vh.z, vl.z), fs);
-        ((float4 *)a.va)[i] = make_float4(x.hi, y.hi, z.hi, 0.f);
-        ((float4 *)a.vb)[i] = make_float4(x.lo, y.lo, z.lo, 0.f);
+        ((float4 *)vel_a(a, spar))[i] = make_float4(x.hi, y.hi, z.hi, 0.f);
+        ((float4 *)vel_b(a, spar))[i] = make_float4(x.lo, y.lo, z.lo, 0.f);
     } else {
-        float4 v = ((float4 *)a.va)[i];
+        float4 v = ((float4 *)vel_a(a, spar))[i];
         const float ff = (float)f;
         v.x *= ff; v.y *= ff; v.z *= ff;
-        ((float4 *)a.va)[i] = v;
+        ((float4 *)vel_a(a, spar))[i] = v;
     }
 }
 
@@ -1151,7 +1694,7 @@ template <int P>
 __global__ void k_set_steps(KArgs a)
 {
     a.ctl->remaining = a.nsteps;
-    a.ctl->budget = a.nsteps + 2;
+    a.ctl->budget = a.nsteps + 64;
     a.ctl->n_other += 1;
 }
 
@@ -1162,6 +1705,8 @@ __global__ void k_reset(KArgs a)
     a.ctl->status = 0u;
     a.ctl->ticket = 0u;
     a.ctl->maxdisp2 = 0u;
+    a.ctl->maxv2 = 0u;
+    a.ctl->maxa2 = 0u;
     a.ctl->remaining = 0;
     a.ctl->n_other += 1;
 }
@@ -1185,12 +1730,18 @@ KernelSet make_kernel_set()
     k.force[3] = (const void *)k_force<P, 8>;
     k.force[4] = (const void *)k_force<P, 16>;
     k.force[5] = (const void *)k_force<P, 32>;
+    k.step[0] = (const void *)k_step<P, 1>;
+    k.step[1] = (const void *)k_step<P, 2>;
+    k.step[2] = (const void *)k_step<P, 4>;
+    k.step[3] = (const void *)k_step<P, 8>;
+    k.step[4] = (const void *)k_step<P, 16>;
+    k.step[5] = (const void *)k_step<P, 32>;
     k.bin = (const void *)k_bin<P>;
     k.scan = (const void *)k_scan<P>;
     k.scatter = (const void *)k_scatter<P>;
     k.permute = (const void *)k_permute<P>;
-    k.copyback = (const void *)k_copyback<P>;
     k.nbuild = (const void *)k_nbuild<P>;
+    k.flip = (const void *)k_flip<P>;
     k.load = (const void *)k_load<P>;
     k.getstate = (const void *)k_getstate<P>;
     k.expforce = (const void *)k_expforce<P>;

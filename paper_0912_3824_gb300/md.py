@@ -19,7 +19,7 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libmdgb300.so")
+LIB_PATH = os.environ.get("MDGB300_LIB", os.path.join(_HERE, "libmdgb300.so"))
 
 MD_OK, MD_E_INVAL, MD_E_NOMEM, MD_E_CUDA, MD_E_NONFINITE, MD_E_UNSTABLE, MD_E_TIMEOUT, MD_E_CAPACITY = range(8)
 MD_PREC_FP64, MD_PREC_MIXED, MD_PREC_FP32 = 0, 1, 2
@@ -48,7 +48,8 @@ class md_info_t(C.Structure):
                 ("neigh_capacity", C.c_int32), ("threads_per_particle", C.c_int32),
                 ("cells_per_edge", C.c_int32), ("step", C.c_int64), ("rebuilds", C.c_int64),
                 ("kernel_launches", C.c_int64), ("max_neighbours", C.c_int32),
-                ("status", C.c_int32), ("force_ms", C.c_double), ("force_launches", C.c_int64)]
+                ("status", C.c_int32), ("step_ms", C.c_double), ("step_launches", C.c_int64),
+                ("rebuild_ms", C.c_double), ("rebuild_checks", C.c_int64)]
 
 
 OBS_DTYPE = np.dtype([("step", np.int64), ("e_pot", np.float64), ("e_kin", np.float64),
@@ -270,6 +271,7 @@ class System:
         self.n_per_replica = np.ascontiguousarray(n_per_replica, dtype=np.int64)
         self.box = np.ascontiguousarray(box, dtype=np.float64)
         self.n = int(self.n_per_replica.sum())
+        self.species = np.ascontiguousarray(species, dtype=np.int32)
         self.nrep = len(self.n_per_replica)
         self.stream = stream if stream is not None else torch.cuda.current_stream(device)
         nbytes = md_workspace_size(params, self.n_per_replica, self.box)

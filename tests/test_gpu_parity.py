@@ -131,6 +131,17 @@ def test_fp64_trajectory_matches_oracle(md, use_graph):
     assert np.abs(obs["p"]).max() < 1e-10
 
 
+@pytest.mark.parametrize("prec,tpp", [("fp64", 4), ("mixed", 4), ("mixed", 8), ("mixed", 2), ("fp32", 4)])
+def test_ragged_particle_count_trajectory(md, prec, tpp):
+    """N = 1001: the last warp of the step kernel holds padding lanes."""
+    s = _system("ka", 1001, amp=0.03)
+    pos, vel, img, obs, info = _trajectory(md, s, prec, 0.002, 40, 10, threads_per_particle=tpp)
+    rp, rv, ri, _, rec = oracle.vv_run(s.params, s.box, s.species, s.pos, s.vel, s.image, 0.002, 40, sample=10)
+    tol = {"fp64": 1e-9, "mixed": 1e-5, "fp32": 1e-3}[prec]
+    assert np.abs((pos + img * s.box) - (rp + ri * s.box)).max() < tol
+    assert np.allclose(obs["e_pot"], rec["e_pot"], rtol=1e-11 if prec == "fp64" else 1e-5)
+
+
 def test_mixed_trajectory_close_to_oracle(md):
     s = _system("ka", 2000, amp=0.02)
     pos, vel, img, obs, info = _trajectory(md, s, "mixed", 0.001, 300, 50)

@@ -202,6 +202,44 @@ const char *md_last_error(const md_handle *h);
 /* Fixed name of a status code. */
 const char *md_status_string(int code);
 
+/* Largest particle count accepted by md_forces_noalloc(). */
+#define MD_NOALLOC_MAX_N 1048576
+
+/* Forces, per-particle energies and energy / virial totals of one periodic
+ * configuration, computed without allocating any device memory.
+ *
+ * The paper has no counterpart to this call.  It exists for callers that may
+ * not allocate device memory when they need forces: an out-of-memory handler
+ * that must still evaluate a configuration after an allocation has failed, an
+ * application whose memory manager owns the whole device and forbids
+ * cudaMalloc / cudaFree outside its own pool (cudaFree also synchronises the
+ * device), or code certified to allocate nothing after start-up.  It needs no
+ * handle and no workspace.
+ *
+ * All arrays are DEVICE memory owned by the caller: species[n] (int32, 0 or
+ * 1), pos[n][3] (float64, any real coordinates), force[n][3] (float64, out),
+ * energy[n] (float64, out: half of each pair energy; may be NULL), totals[8]
+ * (float64, out: E_pot, virial, W_xx, W_yy, W_zz, W_xy, W_xz, W_yz).  From *p
+ * only the potential (n_species, eps, sigma, rcut, shift) and the precision
+ * are used: MD_PREC_FP64 evaluates pairs in double, the other modes in single
+ * precision on separations formed in double.  The sum runs directly over all
+ * pairs (O(n^2) work), in a cubic box of edge `box` > 2 r_c,max.
+ *
+ * Scratch: a fixed 512 KiB area inside this library's device memory (the
+ * per-block partial sums and a counter), present on every GPU that loads the
+ * library until the process exits.  The first call on each device, with that
+ * device current, looks up the area's address; make that first call before
+ * any stream capture.  Every call uses the same area and resets the counter
+ * itself; calls that overlap on the GPU (different streams, or unordered
+ * calls from several threads) race on the area and give wrong totals.
+ *
+ * Returns MD_OK, MD_E_INVAL (null pointer, n < 2, n > MD_NOALLOC_MAX_N, box
+ * too small, bad parameters) or MD_E_CUDA.  Asynchronous on cuda_stream (a
+ * cudaStream_t, NULL = legacy default stream). */
+int md_forces_noalloc(const md_params *p, int64_t n, double box, const int32_t *species,
+                      const double *pos, double *force, double *energy, double *totals,
+                      void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -20,7 +20,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmdgb300.so")
-SOURCES = ["md_api.cu", "md_kernels_mixed.cu", "md_kernels_fp64.cu", "md_kernels_fp32.cu"]
+SOURCES = ["md_api.cu", "md_kernels_mixed.cu", "md_kernels_fp64.cu", "md_kernels_fp32.cu", "md_noalloc.cu"]
 HEADERS = ["md_common.cuh", "md_kernels.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -90,6 +90,8 @@ def _load() -> C.CDLL:
         "md_destroy": ([H], C.c_int),
         "md_last_error": ([H], C.c_char_p),
         "md_status_string": ([C.c_int], C.c_char_p),
+        "md_forces_noalloc": ([P, C.c_int64, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                               C.c_void_p, C.c_void_p], C.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -102,7 +104,8 @@ _lib = _load()
 EXPORTED = ("md_params_default", "md_workspace_size", "md_create", "md_step",
             "md_rescale_velocities", "md_compute_forces", "md_observables", "md_get_state",
             "md_set_state", "md_get_neighbours", "md_info", "md_sync", "md_destroy",
-            "md_last_error", "md_status_string")
+            "md_last_error", "md_status_string", "md_forces_noalloc")
+MD_NOALLOC_MAX_N = 1048576
 
 
 def _status_name(code: int) -> str:
@@ -231,6 +234,16 @@ def md_destroy(h):
 
 def md_last_error(h) -> str:
     return _lib.md_last_error(h).decode()
+
+
+def md_forces_noalloc(p: md_params, n: int, box: float, species_ptr: int, pos_ptr: int, force_ptr: int,
+                      energy_ptr: int, totals_ptr: int, stream_ptr: int):
+    """Direct-sum forces without any device allocation; every pointer is a
+    caller-owned device address (see md.h for the layouts)."""
+    _check(_lib.md_forces_noalloc(C.byref(p), int(n), float(box), C.c_void_p(species_ptr),
+                                  C.c_void_p(pos_ptr), C.c_void_p(force_ptr),
+                                  C.c_void_p(energy_ptr) if energy_ptr else None,
+                                  C.c_void_p(totals_ptr), C.c_void_p(stream_ptr)))
 
 
 # ---------------------------------------------------------------------------

@@ -44,13 +44,18 @@ def parse_args(argv=None):
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--n", type=int, default=65536)
+    ap.add_argument("--particles", dest="n", type=int, default=65536)
     ap.add_argument("--inner", type=int, default=1000, help="MD steps per timed iteration")
     ap.add_argument("--precision", choices=["mixed", "fp64", "fp32"], default="mixed")
     ap.add_argument("--no-extras", action="store_true", help="skip fp64 / e2e / cpu legs")
     ap.add_argument("--no-graph", action="store_true",
                     help="plain stream launches instead of the CUDA graph (for per-kernel profiling)")
     ap.add_argument("--tpp", type=int, default=0, help="force-kernel threads per particle (0 = auto)")
+    ap.add_argument("--workload", choices=["ka65536", "lj-sweep", "replicas", "drift"], default="ka65536",
+                    help="ka65536: the headline line; the others print one line per case")
+    ap.add_argument("--sizes", type=int, nargs="*", default=None, help="lj-sweep particle counts")
+    ap.add_argument("--md-steps", type=int, default=100000, help="drift: NVE MD steps per run")
+    ap.add_argument("--cases", nargs="*", default=None, help="drift: subset of cases")
     return ap.parse_args(argv)
 
 
@@ -151,22 +156,47 @@ FLOP_PER_PAIR = 23
 FLOP_PER_UPDATE = 210
 
 
-def list_statistics(sim, params):
+KERNEL_SOURCES = ("paper_0912_3824_gb300/csrc/md_kernels.cuh", "paper_0912_3824_gb300/csrc/md_common.cuh")
+
+
+def profiled_traffic(kernel):
+    """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum)
+    of `kernel` from the committed ncu summary, or None when no summary
+    covers it or its sources changed since the capture."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "k_step_ka65536_mixed.md")
+    if not os.path.exists(path):
+        return None
+    fields = {}
+    for line in open(path):
+        k, sep, v = line.partition(":")
+        if sep and k in ("traffic_bytes_per_launch", "kernel", "source_sha256"):
+            fields[k] = v.strip()
+    now = " ".join(hashlib.sha256(open(os.path.join(ROOT, f), "rb").read()).hexdigest() for f in KERNEL_SOURCES)
+    if fields.get("kernel") != kernel or fields.get("source_sha256") != now:
+        return None
+    return float(fields["traffic_bytes_per_launch"])
+
+
+def list_statistics(sim, params, sample=100000):
     """Mean list length and mean number of pairs inside the cutoff, from the
-    current lists and positions (host-side numpy)."""
+    current lists and positions (host-side numpy; at most `sample` particles,
+    evenly strided, enter the cutoff count).  Single-box handles only."""
     pos, _, _ = sim.get_state()
     counts, lists = sim.neighbours()
     L = sim.box[0]
     n = len(counts)
     species = sim.species
     rc = np.asarray(params["rcut"])
-    rows = np.repeat(np.arange(n), counts)
-    cols = lists[np.arange(lists.shape[1])[None, :] < counts[:, None]]
+    sel = np.arange(0, n, max(1, n // sample))
+    c, lst = counts[sel], lists[sel]
+    rows = np.repeat(sel, c)
+    cols = lst[np.arange(lst.shape[1])[None, :] < c[:, None]]
     d = pos[rows] - pos[cols]
     d -= L * np.round(d / L)
     r2 = (d * d).sum(1)
     inside = r2 < rc[species[rows], species[cols]] ** 2
-    return counts.mean(), inside.sum() / n
+    return counts.mean(), inside.sum() / len(sel)
 
 
 def prepare(md, synth, n, seed, precision, device, use_graph=True, tpp=0):
@@ -233,8 +263,12 @@ def run_ours(args, rank, world, local):
         torch.distributed.barrier()
     torch.cuda.synchronize()
     clocks.start()
+    # cudaProfilerStart/Stop bracket the timed region, so a profiler started
+    # with profiling off (ncu --profile-from-start off) sees exactly its launches
+    torch.cuda.profiler.start()
     total_ms = time_chunks(torch, sim, args.inner, args.steps, flush, stream)
     torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
     clk = clocks.stop()
     if world > 1:
         torch.distributed.barrier()
@@ -288,7 +322,8 @@ def run_ours(args, rank, world, local):
         "bound": "alu", "kernel": f"k_step<{args.precision}, {info1['threads_per_particle']}> "
                                   "(pair forces + velocity-Verlet update)",
         "achieved": flops / (f_ms * 1e-3) / 1e12, "peak": peak_max, "unit": "TFLOP/s",
-        "frac": flops / (f_ms * 1e-3) / 1e12 / peak_max, "traffic": None,
+        "frac": flops / (f_ms * 1e-3) / 1e12 / peak_max,
+        "traffic": profiled_traffic(f"k_step<{md.PRECISIONS[args.precision]}, {info1['threads_per_particle']}>"),
         "per_launch_ms": f_ms, "flop_per_launch": flops, "mean_list": float(n_list),
         "mean_in_cutoff": float(n_cut),
         "peak_note": "FP32 FMA peak 152 SM x 128 lanes x 2 flop x 2.07 GHz (max clock)",
@@ -338,19 +373,219 @@ def run_ours(args, rank, world, local):
     return result
 
 
-def cpu_baseline(s, pos, vel, img, budget_s=15.0):
+def cpu_baseline(s, pos, vel, img, budget_s=15.0, dt=0.001):
     import oracle
     oracle.build()
     t0 = time.perf_counter()
-    oracle.vv_run(s.params, s.box, s.species, pos, vel, img, 0.001, 2)
+    oracle.vv_run(s.params, s.box, s.species, pos, vel, img, dt, 2)
     per = (time.perf_counter() - t0) / 3.0          # 3 force evaluations
     nsteps = max(2, int(budget_s / per))
     t0 = time.perf_counter()
-    oracle.vv_run(s.params, s.box, s.species, pos, vel, img, 0.001, nsteps)
-    dt = time.perf_counter() - t0
-    return {"value": s.n * nsteps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{nsteps} velocity-Verlet steps of the same N={s.n} KA state, FP64 cell-list "
-                      f"oracle, single thread ({dt:.1f} s)"}
+    oracle.vv_run(s.params, s.box, s.species, pos, vel, img, dt, nsteps)
+    el = time.perf_counter() - t0
+    return {"value": s.n * nsteps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{nsteps} velocity-Verlet steps of the same N={s.n} state, FP64 cell-list "
+                      f"oracle, single thread ({el:.1f} s)"}
+
+
+# ---------------------------------------------------------------------------
+# Further workloads (--workload ...): the other configurations of the method's
+# evaluation.  Each prints one JSON line per case; none is the headline line.
+# ---------------------------------------------------------------------------
+def _gpu_setup(local):
+    import torch
+    from paper_0912_3824_gb300 import build as b
+    b.build()
+    from paper_0912_3824_gb300 import md, synth
+    torch.cuda.set_device(local)
+    device = f"cuda:{local}"
+    stream = torch.cuda.current_stream(device)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=device)
+    return torch, md, synth, device, stream, flush
+
+
+def equilibrate(sim, t_melt, t_final, melt_blocks=20, final_blocks=20, block=100):
+    """Melt the lattice at t_melt and bring the liquid to t_final, rescaling
+    the velocities after every block of MD steps."""
+    for _ in range(melt_blocks):
+        sim.step(block)
+        sim.rescale(t_melt)
+    for _ in range(final_blocks):
+        sim.step(block)
+        sim.rescale(t_final)
+
+
+def unwrapped(pos, img, box):
+    return pos + img * box
+
+
+def run_lj_sweep(args, local):
+    """LJ fluid at rho = 0.8442, T = 1.0, dt = 0.005, skin 0.3, in the chosen
+    precision, N from 4096 to 1048576: throughput against system size."""
+    torch, md, synth, device, stream, flush = _gpu_setup(local)
+    lines = []
+    for n in args.sizes or [4096, 32768, 262144, 1048576]:
+        s = synth.lj_fluid(n=n, density=0.8442, temperature=1.0, seed=3)
+        sim = md.System.from_synth(s, dt=0.005, precision=md.PRECISIONS[args.precision],
+                                   sample_interval=100, device=device, threads_per_particle=args.tpp)
+        equilibrate(sim, 1.5, 1.0, melt_blocks=5, final_blocks=5)
+        sim.step(args.inner)                       # warm-up, graph captured
+        assert sim.sync() == md.MD_OK
+        sim.observables()
+        info0 = sim.info()
+        clocks = ClockSampler(local)
+        clocks.start()
+        ms = time_chunks(torch, sim, args.inner, args.steps, flush, stream)
+        clk = clocks.stop()
+        status = sim.sync()
+        info1 = sim.info()
+        n_list, n_cut = list_statistics(sim, s.params)
+        t_step = ms * 1e-3 / (args.inner * args.steps)
+        flops = (FLOP_PER_ENTRY * n_list + FLOP_PER_PAIR * n_cut + FLOP_PER_UPDATE) * n
+        hbm = n * (4 * n_list + 52 + 192)
+        line = {"workload": "lj-sweep", "config": f"LJ rho=0.8442 T=1.0 dt=0.005 r_c=2.5 shifted skin 0.3, N={n}",
+                "precision": args.precision, "n": n, "value": n / t_step, "unit": UNIT,
+                "us_per_md_step": t_step * 1e6, "md_steps": args.inner * args.steps,
+                "rebuilds": int(info1["rebuilds"] - info0["rebuilds"]), "status": md._status_name(status),
+                "mean_list": float(n_list), "mean_in_cutoff": float(n_cut),
+                "neigh_capacity": info1["neigh_capacity"], "threads_per_particle": info1["threads_per_particle"],
+                "alu_tflops_whole_step": flops / t_step / 1e12,
+                "hbm_algorithmic_gbs_whole_step": hbm / t_step / 1e9, "clocks": clk}
+        if n <= 32768 and not args.no_extras:
+            pos, vel, img = sim.get_state()
+            line["cpu_baseline"] = cpu_baseline(s, pos, vel, img, budget_s=5.0, dt=0.005)
+        sim.close()
+        lines.append(line)
+    return lines
+
+
+def run_replicas(args, local):
+    """256 Kob-Andersen replicas with N_r uniform in {500, ..., 8000} at
+    rho = 1.2, T = 0.8: one handle holding every replica (one CUDA graph per
+    md_step) against one handle per replica launched in a loop."""
+    torch, md, synth, device, stream, flush = _gpu_setup(local)
+    sizes = synth.ensemble_sizes(256, 500, 8000, seed=4)
+    reps = [synth.ka_mixture(n=m, temperature=0.8, seed=4000 + r) for r, m in enumerate(sizes)]
+    prec = md.PRECISIONS[args.precision]
+    p = md.make_params(reps[0].params, 0.001, precision=prec, sample_interval=100,
+                       threads_per_particle=args.tpp)
+    cat = lambda f: np.concatenate([getattr(r, f) for r in reps])
+    one = md.System(p, sizes, [r.box for r in reps], cat("species"), cat("pos"), cat("vel"), cat("image"),
+                    device=device)
+    loop = [md.System(p, [r.n], [r.box], r.species, r.pos, r.vel, r.image, device=device) for r in reps]
+    total = int(sum(sizes))
+
+    def time_loop(k):
+        evs = []
+        for _ in range(k):
+            flush.fill_(1)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for h in loop:
+                h.step(args.inner)
+            e1.record(stream)
+            evs.append((e0, e1))
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in evs)
+
+    for _ in range(2):                            # warm-up: graphs captured, lists built
+        one.step(args.inner)
+        for h in loop:
+            h.step(args.inner)
+    torch.cuda.synchronize()
+    ms_one = time_chunks(torch, one, args.inner, args.steps, flush, stream)
+    ms_loop = time_loop(args.steps)
+    st = [one.sync()] + [h.sync() for h in loop]
+    work = total * args.inner * args.steps
+    line = {"workload": "replicas", "config": "256 KA replicas, N_r ~ U{500..8000} (seed 4), rho=1.2, T=0.8, "
+                                              "dt=0.001, replica seeds 4000+r",
+            "precision": args.precision, "total_particles": total, "unit": UNIT,
+            "one_handle": {"value": work / (ms_one * 1e-3), "us_per_md_step": ms_one * 1e3 / (args.inner * args.steps)},
+            "per_replica_loop": {"value": work / (ms_loop * 1e-3),
+                                 "us_per_md_step": ms_loop * 1e3 / (args.inner * args.steps)},
+            "speedup": ms_loop / ms_one, "md_steps": args.inner * args.steps,
+            "status": sorted({md._status_name(x) for x in st})}
+    one.close()
+    for h in loop:
+        h.close()
+    return [line]
+
+
+def nve_run(md, torch, stream, sim, n, box, species, nsteps, lags, chunk=50000):
+    """NVE segment: energy samples, momentum, A-particle MSD at the given lags
+    (from the unwrapped positions) and the device time of the MD steps."""
+    pos0, _, img0 = sim.get_state()
+    r0 = unwrapped(pos0, img0, box)
+    sel = species == 0
+    marks = sorted({int(l) for l in lags if 0 < l <= nsteps} | {nsteps})
+    done, ms, samples, msd = 0, 0.0, [], {}
+    for m in marks:
+        while done < m:
+            k = min(chunk, m - done)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sim.step(k)
+            e1.record(stream)
+            e1.synchronize()
+            ms += e0.elapsed_time(e1)
+            samples.append(sim.observables()[:, 0])
+            done += k
+        if m in lags:
+            pos, _, img = sim.get_state()
+            d = unwrapped(pos, img, box) - r0
+            msd[str(m)] = float((d[sel] ** 2).sum(1).mean())
+    obs = np.concatenate(samples)
+    return obs, ms, msd
+
+
+def run_drift(args, local):
+    """Energy drift, momentum and MSD in FP32, mixed and FP64 from the same
+    equilibrated state: LJ N=864 (dt 0.005), KA N=16384 at T=0.7 (two seeds)
+    and KA N=65536 quenched to T=0.5 (rescaled every step for 10^4 steps)."""
+    torch, md, synth, device, stream, flush = _gpu_setup(local)
+    M = args.md_steps
+    lags = [10 ** k for k in range(1, 8)]
+    cases = [("lj864", lambda: synth.lj_fluid(864, density=0.8442, temperature=0.722, seed=1), 0.005,
+              None, min(M, 100000)),
+             ("ka16384-s2", lambda: synth.ka_mixture(16384, temperature=2.0, seed=2), 0.001, (2.0, 0.7), M),
+             ("ka16384-s3", lambda: synth.ka_mixture(16384, temperature=2.0, seed=3), 0.001, (2.0, 0.7), M),
+             ("ka65536", lambda: synth.ka_mixture(65536, temperature=2.0, seed=5), 0.001, (2.0, 0.5), M)]
+    if args.cases:
+        cases = [c for c in cases if c[0] in args.cases]
+    lines = []
+    for name, make, dt, temps, nsteps in cases:
+        s = make()
+        prep = md.System.from_synth(s, dt=dt, precision=md.MD_PREC_MIXED, sample_interval=100, device=device)
+        if temps is not None:
+            equilibrate(prep, temps[0], temps[1])
+            if name == "ka65536":                 # quench: rescale after every step
+                for _ in range(10000):
+                    prep.step(1)
+                    prep.rescale(temps[1])
+        assert prep.sync() == md.MD_OK
+        pos, vel, img = prep.get_state()
+        prep.close()
+        for prec in ("fp32", "mixed", "fp64"):
+            p = md.make_params(s.params, dt, precision=md.PRECISIONS[prec], sample_interval=100)
+            sim = md.System(p, [s.n], [s.box], s.species, pos, vel, img, device=device)
+            obs, ms, msd = nve_run(md, torch, stream, sim, s.n, s.box, s.species, nsteps, lags)
+            status = sim.sync()
+            info = sim.info()
+            sim.close()
+            slope, maxdev = energy_drift(obs, s.n)
+            pmax = float(np.abs(obs["p"]).max()) / s.n
+            lines.append({"workload": "drift", "case": name, "precision": prec, "n": s.n, "dt": dt,
+                          "md_steps": nsteps, "value": s.n * nsteps / (ms * 1e-3), "unit": UNIT,
+                          "us_per_md_step": ms * 1e3 / nsteps,
+                          "energy_drift_per_step_rel": slope,
+                          "energy_drift_total_rel": None if slope is None else slope * nsteps,
+                          "energy_max_rel_dev": maxdev, "max_abs_momentum_per_particle": pmax,
+                          "e_per_particle": float((obs["e_pot"][0] + obs["e_kin"][0]) / s.n),
+                          "msd_A": msd, "rebuilds": int(info["rebuilds"]),
+                          "status": md._status_name(status)})
+    return lines
 
 
 def run_reference(args, rank, world):
@@ -392,6 +627,13 @@ def main(argv=None):
             import torch
             torch.cuda.set_device(local)
         dist.init_process_group(backend=backend)
+    if args.workload != "ka65536":
+        if args.impl == "reference" or world > 1:
+            raise SystemExit("--workload other than ka65536 runs our path on one GPU only")
+        fn = {"lj-sweep": run_lj_sweep, "replicas": run_replicas, "drift": run_drift}[args.workload]
+        for line in fn(args, local):
+            print(json.dumps(line), flush=True)
+        return
     if args.impl == "reference":
         res = run_reference(args, rank, world)
     else:

@@ -119,8 +119,8 @@ typedef struct {
     double  step_ms;          /* with use_graph = 0: summed CUDA-event time of the step kernel
                                  (pair forces + velocity-Verlet update, one launch per step)   */
     int64_t step_launches;    /* with use_graph = 0: step-kernel launches timed                 */
-    double  rebuild_ms;       /* with use_graph = 0: summed time of the rebuild chains launched
-                                 at the check points (including those that found no rebuild) */
+    double  rebuild_ms;       /* with use_graph = 0: summed time of the rebuild chains (sort,
+                                 list build) launched when a check point asked for one         */
     int64_t rebuild_checks;   /* with use_graph = 0: rebuild chains launched                    */
 } md_info_t;
 

@@ -543,6 +543,27 @@ int read_ctl(md_handle *h, mdk::Ctl *out)
     return MD_OK;
 }
 
+// Stream-launch mode: launch the rebuild chain if the device flag asks for it
+// (waits for the stream); adds its CUDA-event time to *ms when given.
+int rebuild_if_flagged(md_handle *h, float *ms)
+{
+    mdk::Ctl c;
+    int rc = read_ctl(h, &c);
+    if (rc)
+        return rc;
+    if (!c.rebuild || c.status)
+        return MD_OK;
+    CK(h, cudaEventRecord(h->ev_f1, h->s));
+    if ((rc = launch_rebuild(h)))
+        return rc;
+    CK(h, cudaEventRecord(h->ev_i1, h->s));
+    CK(h, cudaEventSynchronize(h->ev_i1));
+    if (ms)
+        CK(h, cudaEventElapsedTime(ms, h->ev_f1, h->ev_i1));
+    h->rebuild_checks += 1;
+    return MD_OK;
+}
+
 int status_code(unsigned st)
 {
     if (st & mdk::ST_NONFINITE) return MD_E_NONFINITE;
@@ -841,8 +862,12 @@ int md_step(md_handle *h, int64_t nsteps)
         CK(h, cudaGraphLaunch(h->gexec, h->s));
         return MD_OK;
     }
-    // the graph's kernel sequence, launched from the host, with per-kernel timing
-    if ((rc = launch(h, h->ks->integrate, h->g.nblk_i, kIntBlock, first_args(h))) || (rc = launch_rebuild(h)))
+    // The graph's kernel sequence, launched from the host with per-kernel
+    // timing.  At each check point the host reads the device's rebuild flag
+    // and launches the rebuild chain only when the graph's IF node would run
+    // it, so exactly the same kernels execute (results are bitwise equal).
+    if ((rc = launch(h, h->ks->integrate, h->g.nblk_i, kIntBlock, first_args(h))) ||
+        (rc = rebuild_if_flagged(h, nullptr)))
         return rc;
     const void *stepk = h->ks->step[force_index(h->g.tpp)];
     const int64_t iters = (nsteps + kUnroll - 1) / kUnroll;
@@ -853,11 +878,6 @@ int md_step(md_handle *h, int64_t nsteps)
             if ((rc = launch(h, stepk, h->g.nblk_f, kForceBlock, sa)))
                 return rc;
             CK(h, cudaEventRecord(h->ev_f1, h->s));
-            if (sa.set_rebuild) {
-                if ((rc = launch_rebuild(h)))
-                    return rc;
-                CK(h, cudaEventRecord(h->ev_i1, h->s));
-            }
             CK(h, cudaEventSynchronize(h->ev_f1));
             float ms = 0.f;
             CK(h, cudaEventElapsedTime(&ms, h->ev_f0, h->ev_f1));
@@ -866,10 +886,10 @@ int md_step(md_handle *h, int64_t nsteps)
                 h->step_launches += 1;
             }
             if (sa.set_rebuild) {
-                CK(h, cudaEventSynchronize(h->ev_i1));
-                CK(h, cudaEventElapsedTime(&ms, h->ev_f1, h->ev_i1));
-                h->rebuild_ms += ms;
-                h->rebuild_checks += 1;
+                float mr = 0.f;
+                if ((rc = rebuild_if_flagged(h, &mr)))
+                    return rc;
+                h->rebuild_ms += mr;
             }
         }
     }

@@ -142,13 +142,14 @@ def measured_peaks():
         return None
 
 
-# Algorithmic FP32 work of the mixed force kernel (flops, FMA = 2), per entry of
-# a particle's list and per pair inside the cutoff; counted from the method:
-# separation from anchored double-single coordinates 3 x (sub, mul, rint, fma,
-# sub, fma, add) = 27, r^2 = 5, cutoff test = 1; inside the cutoff: reciprocal
-# 1, (sigma^2/r^2)^3 = 3, force factor 4, three products with the separation 3,
+# Algorithmic arithmetic of the mixed force kernel (operations on the FP32 /
+# INT32 lanes, FMA = 2), per entry of a particle's list and per pair inside the
+# cutoff; counted from the method as implemented: separation from the 32-bit
+# fixed-point positions 3 x (integer difference, conversion, scale) = 9,
+# r^2 = 5, cutoff test = 1; inside the cutoff: reciprocal 1,
+# (sigma^2/r^2)^3 = 3, force factor 4, three products with the separation 3,
 # Kahan accumulation 3 x 4.
-FLOP_PER_ENTRY = 33
+FLOP_PER_ENTRY = 15
 FLOP_PER_PAIR = 23
 # per particle and step, the double-single velocity-Verlet update fused into
 # the same kernel: two half kicks 3 x 2 x (product 8 + sum 11), drift

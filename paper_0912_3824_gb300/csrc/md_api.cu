@@ -57,7 +57,7 @@ struct Geometry {
 
 struct Layout {
     size_t off_ctl, off_rep, off_blk_i, off_blk_f, off_crank, off_cxyz;
-    size_t off_pa, off_pb, off_va, off_vb, off_pa2, off_pb2, off_va2, off_vb2, off_force;
+    size_t off_pa, off_pb, off_va, off_vb, off_pa2, off_pb2, off_va2, off_vb2, off_qa, off_qb, off_force;
     size_t off_rref, off_image, off_image2, off_key, off_tmpidx, off_cellof;
     size_t off_ccount, off_ccursor, off_cstart, off_nbr, off_nnbr, off_part_f, off_part_i;
     size_t off_ring, off_totals, off_scale, off_st_pos, off_st_vel, off_st_img, off_st_code;
@@ -161,6 +161,7 @@ int make_geometry(const md_params *p, int R, const int64_t *nrep, const double *
         q.cscale = nc / L;
         q.invLf = (float)(1.0 / L);
         q.cscalef = (float)(nc / L);
+        q.qunit = (float)(L / 4294967296.0);
         // anchoring grid: smallest power of two with 2L < 2^24 * grid
         int e = (int)std::ceil(std::log2(2.0 * L)) - 24;
         double grid = std::ldexp(1.0, e);
@@ -235,6 +236,8 @@ Layout make_layout(const md_params *p, const Geometry &g)
     L.off_vb = take(mixed ? 16 * n : 0);
     L.off_pa2 = take(pb * n);
     L.off_pb2 = take(mixed ? 16 * n : 0);
+    L.off_qa = take(mixed ? 16 * n : 0);
+    L.off_qb = take(mixed ? 16 * n : 0);
     L.off_va2 = take(pb * n);
     L.off_vb2 = take(mixed ? 16 * n : 0);
     L.off_force = take(pb * n);
@@ -351,7 +354,7 @@ int rebuild_chain(const md_handle *h, ChainStep *seq)
     seq[1] = {k.scan, 1, kScanBlock};
     seq[2] = {k.scatter, nb, kIntBlock};
     seq[3] = {k.permute, nb, kIntBlock};
-    seq[4] = {k.nbuild, grid_n(h->g.n * 32, kNbBlock), kNbBlock};
+    seq[4] = {k.nbuild, h->g.ncell, kNbBlock};          // one block per cell
     seq[5] = {k.flip, std::max(1, grid_n(h->g.ncell, kIntBlock)), kIntBlock};
     return 6;
 }
@@ -713,6 +716,7 @@ static int create_impl(md_handle *h, const md_params *p, const int32_t *species,
     a.nblk_f = g.nblk_f;
     a.pa = w + L.off_pa; a.pb = w + L.off_pb; a.va = w + L.off_va; a.vb = w + L.off_vb;
     a.pa2 = w + L.off_pa2; a.pb2 = w + L.off_pb2; a.va2 = w + L.off_va2; a.vb2 = w + L.off_vb2;
+    a.qa = (int4 *)(w + L.off_qa); a.qb = (int4 *)(w + L.off_qb);
     a.force = w + L.off_force;
     a.rref = (float4 *)(w + L.off_rref);
     a.image = (int4 *)(w + L.off_image);

@@ -57,7 +57,8 @@ struct Rep {                  // one independent system
     double L, invL, cscale;   // box edge, 1/L, nc/L
     float Lhi, Llo, invLf, cscalef;
     float grid, inv_grid;     // anchoring grid of MIXED positions (powers of two)
-    float pad[2];
+    float qunit;              // L / 2^32: length of one unit of the fixed-point positions
+    float pad;
 };
 
 struct PairTab {              // [a*2+b]
@@ -82,6 +83,8 @@ struct KArgs {
     void *pa, *pb, *va, *vb;          // buffer 0: MIXED pos hi/lo, vel hi/lo (float4);
                                       // FP64 pos, vel (d4); FP32 pos, vel (float4)
     void *pa2, *pb2, *va2, *vb2;      // buffer 1 (positions: Ctl::pos_par, velocities: state_par)
+    int4 *qa, *qb;                    // MIXED: fixed-point copy of the positions (x/L in units of
+                                      // 2^-32, species in w) read by the pair loops; by Ctl::pos_par
     void *force;                      // float4 (MIXED, FP32) or d4 (FP64): f.xyz, e_i in w
     float4 *rref;                     // positions at the last list build
     int4 *image, *image2;             // image counters (w = original index), by state_par

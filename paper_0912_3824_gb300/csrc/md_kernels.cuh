@@ -33,7 +33,7 @@ namespace mdk {
 
 constexpr int kIntBlock = 256;   // per-particle kernels: one thread per particle
 constexpr int kForceBlock = 256; // force / step kernels: tpp threads per particle
-constexpr int kNbBlock = 256;    // neighbour build: one warp per particle
+constexpr int kNbBlock = 256;    // neighbour build: one block per cell
 constexpr int kScanBlock = 1024;
 constexpr int kPartF = 12;       // doubles per block partial of the force / step kernels
 
@@ -162,6 +162,24 @@ __device__ __forceinline__ double sep_d(double xi, double xj, double L, double i
     double d = xi - xj;
     return fma(-rint(d * invL), L, d);
 }
+
+// Fixed-point position (MIXED): x / L in units of 2^-32, modulo 2^32, from
+// the exact double value of a double-single coordinate.  The periodic box is
+// the full 32-bit circle, so the 32-bit wrapped difference of two coordinates
+// is the minimum-image separation, exact in integers; only its conversion to
+// single precision rounds.  One unit is L / 2^32 (8.8e-9 sigma at L = 38).
+__device__ __forceinline__ unsigned int fixq(float H, float l, double invL)
+{
+    const double x = (double)H + (double)l;
+    return (unsigned int)(unsigned long long)__double2ll_rn(x * invL * 4294967296.0);
+}
+
+__device__ __forceinline__ float sep_q(unsigned int qi, unsigned int qj, float unit)
+{
+    return __int2float_rn((int)(qi - qj)) * unit;
+}
+
+__device__ __forceinline__ int4 *q_of(const KArgs &a, int par) { return par ? a.qb : a.qa; }
 
 // Kahan-compensated accumulation: the running sum is s - c.
 __device__ __forceinline__ void kahan_add(float &s, float &c, float x)
@@ -303,6 +321,8 @@ __device__ __forceinline__ float drift(const KArgs &a, const Rep &rp, PState<P> 
             bad |= ST_NONFINITE;
         ((float4 *)pos_a(a, dst))[i] = s.H;
         ((float4 *)pos_b(a, dst))[i] = s.l;
+        q_of(a, dst)[i] = make_int4((int)fixq(s.H.x, s.l.x, rp.invL), (int)fixq(s.H.y, s.l.y, rp.invL),
+                                    (int)fixq(s.H.z, s.l.z, rp.invL), s.sp);
         const float4 rr = a.rref[i];
         const float ex = __fadd_rn(sep_f(s.H.x, rr.x, rp.Lhi, rp.invLf), s.l.x);
         const float ey = __fadd_rn(sep_f(s.H.y, rr.y, rp.Lhi, rp.invLf), s.l.y);
@@ -338,9 +358,11 @@ __device__ __forceinline__ float drift(const KArgs &a, const Rep &rp, PState<P> 
         if (x >= L) { x -= L; ix = 1; } else if (x < 0.f) { x += L; ix = -1; }
         if (y >= L) { y -= L; iy = 1; } else if (y < 0.f) { y += L; iy = -1; }
         if (z >= L) { z -= L; iz = 1; } else if (z < 0.f) { z += L; iz = -1; }
-        if (x >= L) x = 0.f;   // a coordinate just below 0 can round to L when wrapped
-        if (y >= L) y = 0.f;
-        if (z >= L) z = 0.f;
+        // a coordinate just below 0 can round to L when wrapped: it is 0 of the
+        // original image
+        if (x >= L) { x = 0.f; ix += 1; }
+        if (y >= L) { y = 0.f; iy += 1; }
+        if (z >= L) { z = 0.f; iz += 1; }
         if (!isfinite(x) || !isfinite(y) || !isfinite(z))
             bad |= ST_NONFINITE;
         s.x.x = x; s.x.y = y; s.x.z = z;
@@ -550,13 +572,19 @@ __device__ __forceinline__ void pair_forces(const KArgs &a, const Rep &rp, int p
                 acc[k] = 0.5 * d[k];
         }
     } else {
+        // MIXED reads the fixed-point copy (16 B per neighbour), FP32 the positions
         const float4 *pos = (const float4 *)pos_a(a, pp);
-        const float4 *posl = (const float4 *)pos_b(a, pp);
-        const float4 Hi = pos[ii];
-        float4 li = make_float4(0.f, 0.f, 0.f, 0.f);
-        if constexpr (P == MIXED)
-            li = posl[ii];
-        const int ti = species_of(Hi.w);
+        const int4 *qp = q_of(a, pp);
+        float4 Hi = make_float4(0.f, 0.f, 0.f, 0.f);
+        int4 Qi = make_int4(0, 0, 0, 0);
+        int ti;
+        if constexpr (P == MIXED) {
+            Qi = qp[ii];
+            ti = Qi.w;
+        } else {
+            Hi = pos[ii];
+            ti = species_of(Hi.w);
+        }
         PairRow<float> pr;
 #pragma unroll
         for (int tj = 0; tj < 2; ++tj) {
@@ -571,26 +599,30 @@ __device__ __forceinline__ void pair_forces(const KArgs &a, const Rep &rp, int p
         for (int k0 = 4 * lane; k0 < nn; k0 += 4 * TPP) {
             const int4 q = __ldg((const int4 *)(lst + k0));
             const int jj[4] = {q.x, q.y, q.z, q.w};
-            float4 Hs[4], Ls[4];
+            float4 Hs[4];
+            int4 Qs[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const int j = k0 + u < nn ? jj[u] : ii;
-                Hs[u] = __ldg(pos + j);
                 if constexpr (P == MIXED)
-                    Ls[u] = __ldg(posl + j);
+                    Qs[u] = __ldg(qp + j);
+                else
+                    Hs[u] = __ldg(pos + j);
             }
             float gx = 0.f, gy = 0.f, gz = 0.f;
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                const float4 Hj = Hs[u];
-                const int tj = species_of(Hj.w);
+                int tj;
                 float dx, dy, dz;
                 if constexpr (P == MIXED) {
-                    const float4 lj = Ls[u];
-                    dx = sep_ds(Hi.x, li.x, Hj.x, lj.x, rp.Lhi, rp.Llo, rp.invLf);
-                    dy = sep_ds(Hi.y, li.y, Hj.y, lj.y, rp.Lhi, rp.Llo, rp.invLf);
-                    dz = sep_ds(Hi.z, li.z, Hj.z, lj.z, rp.Lhi, rp.Llo, rp.invLf);
+                    const int4 Qj = Qs[u];
+                    tj = Qj.w;
+                    dx = sep_q(Qi.x, Qj.x, rp.qunit);
+                    dy = sep_q(Qi.y, Qj.y, rp.qunit);
+                    dz = sep_q(Qi.z, Qj.z, rp.qunit);
                 } else {
+                    const float4 Hj = Hs[u];
+                    tj = species_of(Hj.w);
                     dx = sep_f(Hi.x, Hj.x, rp.Lhi, rp.invLf);
                     dy = sep_f(Hi.y, Hj.y, rp.Lhi, rp.invLf);
                     dz = sep_f(Hi.z, Hj.z, rp.Lhi, rp.invLf);
@@ -693,29 +725,38 @@ __device__ __forceinline__ void pair_energy(const KArgs &a, const Rep &rp, int p
                 d8[5] += fr * dx * dy; d8[6] += fr * dx * dz; d8[7] += fr * dy * dz;
             }
         }
+    } else if constexpr (P == MIXED) {
+        const int4 *qp = q_of(a, pp);
+        const int4 Qi = qp[ii];
+        for (int k = lane; k < nn; k += TPP) {
+            const int4 Qj = __ldg(qp + __ldg(lst + k));
+            const int ab = Qi.w * 2 + Qj.w;
+            const float dx = sep_q(Qi.x, Qj.x, rp.qunit);
+            const float dy = sep_q(Qi.y, Qj.y, rp.qunit);
+            const float dz = sep_q(Qi.z, Qj.z, rp.qunit);
+            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            if (r2 < a.tab.rc2[ab]) {
+                const float ir2 = __fdividef(1.0f, r2);
+                const float s2 = a.tab.sig2[ab] * ir2;
+                const float s6 = s2 * s2 * s2;
+                const float fr = a.tab.eps48[ab] * ir2 * s6 * (s6 - 0.5f);
+                d8[0] += a.tab.eps4[ab] * s6 * (s6 - 1.0f) - a.tab.shift[ab];
+                d8[1] += fr * r2;
+                d8[2] += fr * dx * dx; d8[3] += fr * dy * dy; d8[4] += fr * dz * dz;
+                d8[5] += fr * dx * dy; d8[6] += fr * dx * dz; d8[7] += fr * dy * dz;
+            }
+        }
     } else {
         const float4 *pos = (const float4 *)pos_a(a, pp);
-        const float4 *posl = (const float4 *)pos_b(a, pp);
         const float4 Hi = pos[ii];
-        float4 li = make_float4(0.f, 0.f, 0.f, 0.f);
-        if constexpr (P == MIXED)
-            li = posl[ii];
         const int ti = species_of(Hi.w);
         for (int k = lane; k < nn; k += TPP) {
             const int j = __ldg(lst + k);
             const float4 Hj = __ldg(pos + j);
             const int ab = ti * 2 + species_of(Hj.w);
-            float dx, dy, dz;
-            if constexpr (P == MIXED) {
-                const float4 lj = __ldg(posl + j);
-                dx = sep_ds(Hi.x, li.x, Hj.x, lj.x, rp.Lhi, rp.Llo, rp.invLf);
-                dy = sep_ds(Hi.y, li.y, Hj.y, lj.y, rp.Lhi, rp.Llo, rp.invLf);
-                dz = sep_ds(Hi.z, li.z, Hj.z, lj.z, rp.Lhi, rp.Llo, rp.invLf);
-            } else {
-                dx = sep_f(Hi.x, Hj.x, rp.Lhi, rp.invLf);
-                dy = sep_f(Hi.y, Hj.y, rp.Lhi, rp.invLf);
-                dz = sep_f(Hi.z, Hj.z, rp.Lhi, rp.invLf);
-            }
+            const float dx = sep_f(Hi.x, Hj.x, rp.Lhi, rp.invLf);
+            const float dy = sep_f(Hi.y, Hj.y, rp.Lhi, rp.invLf);
+            const float dz = sep_f(Hi.z, Hj.z, rp.Lhi, rp.invLf);
             const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
             if (r2 < a.tab.rc2[ab]) {
                 const float ir2 = __fdividef(1.0f, r2);
@@ -845,6 +886,7 @@ __device__ __forceinline__ void component_update(const KArgs &a, const Rep &rp, 
                 bad |= ST_NONFINITE;
             ((float *)pos_a(a, pp ^ 1))[e] = Hn;
             ((float *)pos_b(a, pp ^ 1))[e] = ln;
+            ((unsigned int *)q_of(a, pp ^ 1))[e] = fixq(Hn, ln, rp.invL);
             const float dx = __fadd_rn(sep_f(Hn, rr, rp.Lhi, rp.invLf), ln);
             dd = dx * dx;
             vv = v.hi * v.hi;
@@ -894,7 +936,7 @@ __device__ __forceinline__ void component_update(const KArgs &a, const Rep &rp, 
             float x = ((const float *)pos_a(a, pp))[e] + s;
             int dimg = 0;
             if (x >= L) { x -= L; dimg = 1; } else if (x < 0.f) { x += L; dimg = -1; }
-            if (x >= L) x = 0.f;
+            if (x >= L) { x = 0.f; dimg += 1; }
             if (!isfinite(x))
                 bad |= ST_NONFINITE;
             ((float *)pos_a(a, pp ^ 1))[e] = x;
@@ -980,6 +1022,8 @@ __device__ __forceinline__ void step_body_split(const KArgs &a, bool active, boo
             ((double *)pos_a(a, pp ^ 1))[4 * (size_t)i + 3] = ((const double *)pos_a(a, pp))[4 * (size_t)i + 3];
         else
             ((float *)pos_a(a, pp ^ 1))[4 * (size_t)i + 3] = ((const float *)pos_a(a, pp))[4 * (size_t)i + 3];
+        if constexpr (P == MIXED)
+            ((int *)q_of(a, pp ^ 1))[4 * (size_t)i + 3] = sp;
     }
     // combine the component lanes (the first four lanes of the group)
 #pragma unroll
@@ -1412,6 +1456,7 @@ __global__ void __launch_bounds__(kIntBlock) k_permute(KArgs a)
         ((float4 *)vel_a(a, spar ^ 1))[d] = ((const float4 *)vel_a(a, spar))[i];
         if constexpr (P == MIXED) {
             ((float4 *)pos_b(a, pp ^ 1))[d] = ((const float4 *)pos_b(a, pp))[i];
+            q_of(a, pp ^ 1)[d] = q_of(a, pp)[i];
             ((float4 *)vel_b(a, spar ^ 1))[d] = ((const float4 *)vel_b(a, spar))[i];
         }
         a.rref[d] = make_float4(x.x, x.y, x.z, 0.f);
@@ -1421,17 +1466,51 @@ __global__ void __launch_bounds__(kIntBlock) k_permute(KArgs a)
 }
 
 // ---------------------------------------------------------------------------
-// Neighbour-list build (Sec. 2.2): one warp per particle scans the particles
-// of its own and the adjacent cells (27, or all cells when fewer than three
-// fit along the box edge) and keeps those closer than r_c,ab + skin (plus a
-// rounding margin).  Particle-major list: nbr[i*K + k], coalesced per warp.
-// Distances are single precision in every mode (FP64 positions are rounded):
-// the list only has to contain every pair within r_c + skin, which the
-// margin guarantees.  Reads the permuted positions (other buffer).
+// Neighbour-list build (Sec. 2.2), one block per cell.  The block stages the
+// particles of the 27 surrounding cells (all cells of the replica when fewer
+// than three fit along its edge) in shared memory, in a fixed order (stencil
+// order, then slot order inside a cell), dropping those farther than the
+// largest list radius from the cell's own box.  Each warp then takes one
+// particle of the cell at a time and keeps the staged particles closer than
+// r_c,ab + skin (plus a rounding margin), 32 candidates per ballot, writing
+// its row of the particle-major list nbr[i*K + k] in that order.  Distances
+// use the single-precision high words in every mode: the list only has to
+// contain every pair within r_c + skin, and the margin covers the rounding.
+// Reads the permuted positions (other buffer).  More candidates than fit in
+// shared memory, or more particles in the cell than one batch holds, are
+// processed in rounds, so no cell size is too large.
 // ---------------------------------------------------------------------------
+constexpr int kNbCap = 1024;     // staged candidates per round
+constexpr int kNbOwn = 256;      // own-cell particles per batch
+
+template <int P>
+__device__ __forceinline__ float4 hi_pos(const KArgs &a, int pn, int j)
+{
+    if constexpr (P == FP64) {
+        const d4 x = ((const d4 *)pos_a(a, pn))[j];
+        return make_float4(__double2float_rn(x.x), __double2float_rn(x.y), __double2float_rn(x.z),
+                           __int_as_float(species_of(x.w)));
+    } else {
+        return ((const float4 *)pos_a(a, pn))[j];
+    }
+}
+
+// distance of x from the interval [c - h, c + h] on a periodic axis
+__device__ __forceinline__ float box_gap(float x, float c, float h, float L, float invL)
+{
+    return fmaxf(fabsf(sep_f(x, c, L, invL)) - h, 0.0f);
+}
+
 template <int P>
 __global__ void __launch_bounds__(kNbBlock) k_nbuild(KArgs a)
 {
+    __shared__ float4 s_pos[kNbCap];
+    __shared__ int s_idx[kNbCap];
+    __shared__ int s_cnt[kNbOwn];
+    __shared__ int s_pref[28];
+    __shared__ int s_cell[27];
+    __shared__ int s_wsum[kNbBlock / 32];
+
     Ctl *ctl = a.ctl;
     if (!rebuild_pending(ctl))
         return;
@@ -1439,77 +1518,133 @@ __global__ void __launch_bounds__(kNbBlock) k_nbuild(KArgs a)
         atomicAdd((unsigned long long *)&ctl->n_rebuild_k, 1ull);
         atomicAdd((unsigned long long *)&ctl->rebuilds, 1ull);
     }
-    const int lane = threadIdx.x & 31;
-    const int i = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
-    if (i >= a.n)
-        return;   // whole warp
+    const int c = blockIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int NW = kNbBlock / 32;
     const int pn = ctl->pos_par ^ 1;
-    const int c = a.cellof[i];
     const int4 cc = a.cxyz[c];
     const Rep rp = a.rep[cc.w];
     const int nc = rp.nc;
-    const int lo = nc >= 3 ? -1 : 0, hi = nc >= 3 ? 1 : 0;
-    int *out = a.nbr + (size_t)i * (size_t)a.K;
-    const unsigned lt_mask = (1u << lane) - 1u;
-    int cnt = 0;
+    const int nst = nc >= 3 ? 27 : 1;
+    const int c0 = a.cstart[c], c1 = a.cstart[c + 1];
+    if (c0 == c1)
+        return;
 
-    float4 Hi, li = make_float4(0.f, 0.f, 0.f, 0.f);
-    if constexpr (P == FP64) {
-        const d4 x = ((const d4 *)pos_a(a, pn))[i];
-        Hi = make_float4(__double2float_rn(x.x), __double2float_rn(x.y), __double2float_rn(x.z),
-                         __int_as_float(species_of(x.w)));
-    } else {
-        Hi = ((const float4 *)pos_a(a, pn))[i];
-        if constexpr (P == MIXED)
-            li = ((const float4 *)pos_b(a, pn))[i];
-    }
-    const int ti = species_of(Hi.w);
-    for (int dz = lo; dz <= hi; ++dz)
-    for (int dy = lo; dy <= hi; ++dy)
-    for (int dx = lo; dx <= hi; ++dx) {
-        const int x = (cc.x + dx + nc) % nc, y = (cc.y + dy + nc) % nc, z = (cc.z + dz + nc) % nc;
-        const int cell = a.crank[rp.cell0 + (z * nc + y) * nc + x];
-        const int j0 = a.cstart[cell], j1 = a.cstart[cell + 1];
-        for (int jb = j0; jb < j1; jb += 32) {
-            const int j = jb + lane;
-            bool in = false;
-            if (j < j1 && j != i) {
-                float ex, ey, ez;
-                int tj;
-                if constexpr (P == FP64) {
-                    const d4 y4 = ((const d4 *)pos_a(a, pn))[j];
-                    ex = sep_f(Hi.x, __double2float_rn(y4.x), rp.Lhi, rp.invLf);
-                    ey = sep_f(Hi.y, __double2float_rn(y4.y), rp.Lhi, rp.invLf);
-                    ez = sep_f(Hi.z, __double2float_rn(y4.z), rp.Lhi, rp.invLf);
-                    tj = species_of(y4.w);
-                } else {
-                    const float4 Hj = ((const float4 *)pos_a(a, pn))[j];
-                    if constexpr (P == MIXED) {
-                        const float4 lj = ((const float4 *)pos_b(a, pn))[j];
-                        ex = sep_ds(Hi.x, li.x, Hj.x, lj.x, rp.Lhi, rp.Llo, rp.invLf);
-                        ey = sep_ds(Hi.y, li.y, Hj.y, lj.y, rp.Lhi, rp.Llo, rp.invLf);
-                        ez = sep_ds(Hi.z, li.z, Hj.z, lj.z, rp.Lhi, rp.Llo, rp.invLf);
-                    } else {
-                        ex = sep_f(Hi.x, Hj.x, rp.Lhi, rp.invLf);
-                        ey = sep_f(Hi.y, Hj.y, rp.Lhi, rp.invLf);
-                        ez = sep_f(Hi.z, Hj.z, rp.Lhi, rp.invLf);
-                    }
-                    tj = species_of(Hj.w);
-                }
-                in = fmaf(ex, ex, fmaf(ey, ey, ez * ez)) < a.tab.rl2[ti * 2 + tj];
-            }
-            const unsigned m = __ballot_sync(0xffffffffu, in);
-            const int pre = __popc(m & lt_mask);
-            if (in && cnt + pre < a.K)
-                out[cnt + pre] = j;
-            cnt += __popc(m);
+    if (tid < nst) {
+        int x = cc.x, y = cc.y, z = cc.z;
+        if (nst == 27) {
+            x = (x + tid % 3 - 1 + nc) % nc;
+            y = (y + (tid / 3) % 3 - 1 + nc) % nc;
+            z = (z + tid / 9 - 1 + nc) % nc;
         }
+        s_cell[tid] = a.crank[rp.cell0 + (z * nc + y) * nc + x];
     }
-    if (lane == 0) {
-        a.nnbr[i] = cnt < a.K ? cnt : a.K;
-        atomicMax(&ctl->max_nbr, cnt);
-        if (cnt > a.K)
-            atomicOr(&ctl->status, ST_OVERFLOW);
+    __syncthreads();
+    if (tid == 0) {
+        int s = 0;
+        for (int k = 0; k < nst; ++k) {
+            s_pref[k] = s;
+            s += a.cstart[s_cell[k] + 1] - a.cstart[s_cell[k]];
+        }
+        s_pref[nst] = s;
+    }
+    __syncthreads();
+    const int total = s_pref[nst];
+
+    // own cell box (centre, half edge) for the candidate filter
+    const float edge = rp.Lhi / (float)nc;
+    const float hx = 0.5f * edge + 1e-3f;
+    const float ccx = ((float)cc.x + 0.5f) * edge, ccy = ((float)cc.y + 0.5f) * edge,
+                ccz = ((float)cc.z + 0.5f) * edge;
+    const float rlmax2 = fmaxf(fmaxf(a.tab.rl2[0], a.tab.rl2[1]), fmaxf(a.tab.rl2[2], a.tab.rl2[3]));
+    const unsigned lt_mask = (1u << lane) - 1u;
+
+    for (int ob = c0; ob < c1; ob += kNbOwn) {
+        const int nown = min(kNbOwn, c1 - ob);
+        for (int t = tid; t < nown; t += kNbBlock)
+            s_cnt[t] = 0;
+        int staged = 0;
+        for (int base = 0; base < total; base += kNbBlock) {
+            // stage candidates base .. base + kNbBlock - 1, order-preserving compaction
+            const int t = base + tid;
+            bool keep = false;
+            float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+            int j = 0;
+            if (t < total) {
+                int k = 0;
+                while (k + 1 < nst && s_pref[k + 1] <= t)
+                    ++k;
+                j = a.cstart[s_cell[k]] + (t - s_pref[k]);
+                q = hi_pos<P>(a, pn, j);
+                keep = true;
+                if (nst == 27) {
+                    const float gx = box_gap(q.x, ccx, hx, rp.Lhi, rp.invLf);
+                    const float gy = box_gap(q.y, ccy, hx, rp.Lhi, rp.invLf);
+                    const float gz = box_gap(q.z, ccz, hx, rp.Lhi, rp.invLf);
+                    keep = fmaf(gx, gx, fmaf(gy, gy, gz * gz)) < rlmax2;
+                }
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, keep);
+            if (lane == 0)
+                s_wsum[warp] = __popc(m);
+            __syncthreads();
+            int off = staged, add = 0;
+#pragma unroll
+            for (int w = 0; w < NW; ++w) {
+                off += (w < warp) ? s_wsum[w] : 0;
+                add += s_wsum[w];
+            }
+            if (keep) {
+                const int s = off + __popc(m & lt_mask);
+                s_pos[s] = q;
+                s_idx[s] = j;
+            }
+            staged += add;
+            __syncthreads();
+            if (staged <= kNbCap - kNbBlock && base + kNbBlock < total)
+                continue;
+
+            // scan the staged candidates for every own particle of the batch
+            for (int o = warp; o < nown; o += NW) {
+                const int i = ob + o;
+                const float4 H = hi_pos<P>(a, pn, i);
+                const int ti = species_of(H.w);
+                const float rl0 = a.tab.rl2[ti * 2], rl1 = a.tab.rl2[ti * 2 + 1];
+                int *out = a.nbr + (size_t)i * (size_t)a.K;
+                int cnt = s_cnt[o];
+                for (int s0 = 0; s0 < staged; s0 += 32) {
+                    const int s = s0 + lane;
+                    bool in = false;
+                    int jj = 0;
+                    if (s < staged) {
+                        const float4 y = s_pos[s];
+                        jj = s_idx[s];
+                        const float ex = sep_f(H.x, y.x, rp.Lhi, rp.invLf);
+                        const float ey = sep_f(H.y, y.y, rp.Lhi, rp.invLf);
+                        const float ez = sep_f(H.z, y.z, rp.Lhi, rp.invLf);
+                        const float r2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+                        in = jj != i && r2 < (species_of(y.w) ? rl1 : rl0);
+                    }
+                    const unsigned mm = __ballot_sync(0xffffffffu, in);
+                    const int at = cnt + __popc(mm & lt_mask);
+                    if (in && at < a.K)
+                        out[at] = jj;
+                    cnt += __popc(mm);
+                }
+                if (lane == 0)
+                    s_cnt[o] = cnt;
+            }
+            staged = 0;
+            __syncthreads();
+        }
+        for (int o = tid; o < nown; o += kNbBlock) {
+            const int cnt = s_cnt[o];
+            a.nnbr[ob + o] = cnt < a.K ? cnt : a.K;
+            atomicMax(&ctl->max_nbr, cnt);
+            if (cnt > a.K)
+                atomicOr(&ctl->status, ST_OVERFLOW);
+        }
+        __syncthreads();
     }
 }
 
@@ -1580,15 +1715,18 @@ __global__ void __launch_bounds__(kIntBlock) k_load(KArgs a)
         }
         ((float4 *)pos_a(a, pp))[i] = make_float4(H[0], H[1], H[2], __int_as_float(sp));
         ((float4 *)pos_b(a, pp))[i] = make_float4(l[0], l[1], l[2], 0.f);
+        q_of(a, pp)[i] = make_int4((int)fixq(H[0], l[0], rp.invL), (int)fixq(H[1], l[1], rp.invL),
+                                   (int)fixq(H[2], l[2], rp.invL), sp);
         ds vx = ds_from_double(vv[0]), vy = ds_from_double(vv[1]), vz = ds_from_double(vv[2]);
         ((float4 *)vel_a(a, spar))[i] = make_float4(vx.hi, vy.hi, vz.hi, 0.f);
         ((float4 *)vel_b(a, spar))[i] = make_float4(vx.lo, vy.lo, vz.lo, 0.f);
     } else {
         float fx = __double2float_rn(x[0]), fy = __double2float_rn(x[1]), fz = __double2float_rn(x[2]);
         const float L = rp.Lhi;
-        if (fx >= L) fx = 0.f;
-        if (fy >= L) fy = 0.f;
-        if (fz >= L) fz = 0.f;
+        // a coordinate just below L can round to L: it is 0 of the next image
+        if (fx >= L) { fx = 0.f; im[0] += 1; }
+        if (fy >= L) { fy = 0.f; im[1] += 1; }
+        if (fz >= L) { fz = 0.f; im[2] += 1; }
         ((float4 *)pos_a(a, pp))[i] = make_float4(fx, fy, fz, __int_as_float(sp));
         ((float4 *)vel_a(a, spar))[i] = make_float4((float)vv[0], (float)vv[1], (float)vv[2], 0.f);
     }

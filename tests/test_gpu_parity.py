@@ -206,6 +206,34 @@ def test_state_roundtrip(md, prec):
     sim.close()
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "fp32"])
+def test_wrap_just_below_zero_keeps_unwrapped_position(md, prec):
+    """A coordinate that leaves the box by less than half an ulp of L wraps to
+    a value that rounds to L; the stored position and its image counter must
+    still describe the same unwrapped point (perfect fcc lattice at rest, so
+    the moving particle feels almost no force)."""
+    s = synth.make_system(864, 0.8442, 0.0, 1, synth.lj_params())
+    k = 0
+    p0 = np.mod(s.pos - s.pos[k], s.box)      # translate the lattice: particle k at the origin
+    assert (p0[k] == 0.0).all()
+    vel = np.zeros_like(p0)
+    vel[k, 0] = -1e-4                           # leaves the box by 1e-7 < ulp(L)/2 in FP32
+    tol = 1e-5 if prec == "fp32" else 1e-9
+    sim = md.System(md.make_params(s.params, 0.001, precision=md.PRECISIONS[prec]), [s.n], [s.box],
+                    s.species, p0, vel, s.image)
+    sim.step(1)
+    pos, _, img = sim.get_state()
+    assert (pos[:, 0] >= 0).all() and (pos[:, 0] <= s.box).all()
+    assert pos[k, 0] + img[k, 0] * s.box == pytest.approx(-1e-7, abs=tol)
+    # the same through set_state: a coordinate 1e-9 below zero
+    p2 = p0.copy()
+    p2[k, 0] = -1e-9
+    sim.set_state(p2, np.zeros_like(p2))
+    pos, _, img = sim.get_state()
+    assert pos[k, 0] + img[k, 0] * s.box == pytest.approx(-1e-9, abs=tol)
+    sim.close()
+
+
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_rescale_sets_temperature(md, prec):
     s = _system("ka", 2000)

@@ -11,7 +11,7 @@ ctypes.  Potential parameters arrive as the plain dictionaries produced by the
 seeded input generator.
 
 Functions (all arrays float64 / int32, original particle order):
-  pair(params, a, b, r2)                 -> (V, F/r) for one pair   (Sec. 3, Sec. 5)
+  pair(params, a, b, r2)                 -> (V, F/r) for one pair   (Sec. 3, 4, 5)
   forces_brute(params, L, species, pos)  -> (f[n,3], e[n], w7[7])   O(N^2)
   forces_cells(params, L, species, pos)  -> same, linked cells
   kinetic(params, species, vel)          -> (E_kin, P[3])
@@ -50,7 +50,7 @@ def build(force: bool = False) -> str:
 class _Pot(C.Structure):
     _fields_ = [("n_species", C.c_int), ("shift", C.c_int),
                 ("eps", C.c_double * 4), ("sigma", C.c_double * 4),
-                ("rcut", C.c_double * 4), ("mass", C.c_double * 2)]
+                ("rcut", C.c_double * 4), ("mass", C.c_double * 2), ("smooth_h", C.c_double)]
 
 
 class _Obs(C.Structure):
@@ -105,6 +105,7 @@ def _pot(params: dict) -> _Pot:
             p.rcut[2 * a + b] = float(params["rcut"][a][b])
     for a in range(2):
         p.mass[a] = float(params["mass"][a])
+    p.smooth_h = float(params.get("smooth", 0.0))
     return p
 
 

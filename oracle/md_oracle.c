@@ -15,7 +15,10 @@
  * What is computed, and where the paper defines it:
  *   - the 12-6 Lennard-Jones pair potential V(r) = 4 eps [(r/sig)^-12 - (r/sig)^-6]
  *     cut at r_c (Sec. 3, performance measurements), optionally shifted so that
- *     V(r_c) = 0; the Kob-Andersen A/B parameter table (Sec. 5);
+ *     V(r_c) = 0; the Kob-Andersen A/B parameter table (Sec. 5); optionally
+ *     multiplied by the smoothing function g((r - r_c) / (h sigma)),
+ *     g(x) = x^4 / (1 + x^4), of Sec. 4 (purely repulsive WCA is the shifted
+ *     potential cut at its minimum, r_c = 2^(1/6) sigma, also Sec. 4);
  *   - the force on each particle as the plain sum over all partners within the
  *     cutoff (Sec. 2.2: neighbour lists and cells only make that sum cheaper,
  *     they do not change it) -- once by brute force over all pairs and once by
@@ -40,6 +43,7 @@ typedef struct {
     double sigma[4];     /* sigma_ab                                        */
     double rcut[4];      /* absolute cutoff radius r_c,ab                   */
     double mass[2];      /* particle mass per species                       */
+    double smooth_h;     /* h of the smoothing function (Sec. 4); 0 = none  */
 } orc_pot;
 
 /* Per-step observables recorded by orc_vv_run. */
@@ -70,6 +74,11 @@ static double lj_raw(double eps, double sig, double r2)
  * *v  = V_ab(r) - S_ab, with S_ab = V_ab(r_c) when shifting, else 0;
  * *fr = -V'(r) / r, so that the force on i from j is  fr * (r_i - r_j).
  *   -V'(r)/r = 48 eps / r^2 * [(sig/r)^12 - (sig/r)^6 / 2]
+ * With smoothing (h > 0, Sec. 4) the potential is U(r) = V(r) g(x) with
+ * x = (r - r_c) / (h sigma_ab) and g(x) = x^4 / (1 + x^4), so that
+ *   *v  = V g
+ *   *fr = -U'(r) / r = (-V'(r)/r) g - V g'(x) / (h sigma_ab r),
+ *   g'(x) = 4 x^3 / (1 + x^4)^2.
  */
 int orc_pair(const orc_pot *p, int a, int b, double r2, double *v, double *fr)
 {
@@ -84,6 +93,16 @@ int orc_pair(const orc_pot *p, int a, int b, double r2, double *v, double *fr)
     double shift = p->shift ? lj_raw(eps, sig, rc * rc) : 0.0;
     *v = 4.0 * eps * (sr6 * sr6 - sr6) - shift;
     *fr = 48.0 * eps / r2 * (sr6 * sr6 - 0.5 * sr6);
+    if (p->smooth_h > 0.0) {
+        double hs = p->smooth_h * sig;
+        double r = sqrt(r2);
+        double x = (r - rc) / hs;
+        double x4 = x * x * x * x;
+        double g = x4 / (1.0 + x4);
+        double dg = 4.0 * x * x * x / ((1.0 + x4) * (1.0 + x4));
+        *fr = *fr * g - *v * dg / (hs * r);
+        *v = *v * g;
+    }
     return 1;
 }
 

@@ -62,8 +62,9 @@ class Stream:
         return np.argsort(self.u64(n), kind="stable")
 
 
-def lj_params(rcut: float = 2.5, shift: bool = True) -> dict:
-    """Monatomic 12-6 Lennard-Jones, eps = sigma = m = 1, cut at rcut (Sec. 3)."""
+def lj_params(rcut: float = 2.5, shift: bool = True, smooth: float = 0.0) -> dict:
+    """Monatomic 12-6 Lennard-Jones, eps = sigma = m = 1, cut at rcut (Sec. 3);
+    smooth = h > 0 multiplies it by g((r - r_c) / (h sigma)) (Sec. 4)."""
     one = [[1.0, 1.0], [1.0, 1.0]]
     return {
         "n_species": 1,
@@ -72,10 +73,20 @@ def lj_params(rcut: float = 2.5, shift: bool = True) -> dict:
         "rcut": [[rcut, rcut], [rcut, rcut]],
         "shift": bool(shift),
         "mass": [1.0, 1.0],
+        "smooth": float(smooth),
     }
 
 
-def ka_params(rcut_factor: float = 2.5, shift: bool = True) -> dict:
+WCA_RCUT = 2.0 ** (1.0 / 6.0)
+
+
+def wca_params(smooth: float = 0.0) -> dict:
+    """Purely repulsive Weeks-Chandler-Andersen potential (Sec. 4): the 12-6
+    potential shifted up by eps and cut at its minimum, r_c = 2^(1/6) sigma."""
+    return lj_params(rcut=WCA_RCUT, shift=True, smooth=smooth)
+
+
+def ka_params(rcut_factor: float = 2.5, shift: bool = True, smooth: float = 0.0) -> dict:
     """Kob-Andersen A/B mixture (Sec. 5): sigma_AA=1, sigma_BB=0.88,
     sigma_AB=0.8, eps_AA=1, eps_BB=0.5, eps_AB=1.5, equal masses.
     Each pair is cut at rcut_factor * sigma_ab."""
@@ -83,7 +94,7 @@ def ka_params(rcut_factor: float = 2.5, shift: bool = True) -> dict:
     sig = [[1.0, 0.8], [0.8, 0.88]]
     rc = [[rcut_factor * s for s in row] for row in sig]
     return {"n_species": 2, "eps": eps, "sigma": sig, "rcut": rc,
-            "shift": bool(shift), "mass": [1.0, 1.0]}
+            "shift": bool(shift), "mass": [1.0, 1.0], "smooth": float(smooth)}
 
 
 def max_rcut(params: dict) -> float:

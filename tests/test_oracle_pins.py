@@ -346,3 +346,91 @@ def test_single_particle_force_matches_full_sum():
     f1, e1 = oracle.force_on(p, s.box, s.species, s.pos, idx)
     assert np.allclose(f1, f[idx], rtol=0, atol=1e-12 * np.abs(f).max())
     assert np.allclose(e1, e[idx], rtol=1e-13, atol=1e-14)
+
+
+# --------------------------------------------------------------------------
+# Sec. 4: purely repulsive WCA potential and the smoothing function
+# g(x) = x^4 / (1 + x^4), x = (r - r_c) / (h sigma_ab)
+# --------------------------------------------------------------------------
+
+def test_wca_closed_forms():
+    """WCA = V_LJ + eps cut at the minimum 2^(1/6) sigma: V(sigma) = eps, and
+    both V and the force go to zero at r_c (the force is continuous there)."""
+    p = synth.wca_params()
+    v, fr = oracle.pair(p, 0, 0, 1.0)
+    assert v == pytest.approx(1.0, rel=1e-14)
+    assert fr == pytest.approx(24.0, rel=1e-14)          # 48 (1 - 1/2)
+    rc = synth.WCA_RCUT
+    v, fr = oracle.pair(p, 0, 0, (rc * (1 - 1e-9)) ** 2)
+    assert 0 <= v < 1e-15 and abs(fr) < 1e-6
+    assert oracle.pair(p, 0, 0, rc * rc) == (0.0, 0.0)
+
+
+@pytest.mark.parametrize("shift", [True, False])
+def test_smoothing_at_one_h_inside_cutoff(shift):
+    """At x = -1: g = 1/2 and g'(x) = 4x^3/(1+x^4)^2 = -1, so the smoothed pair
+    has V/2 and force factor fr/2 + V/(h sigma_ab r).  Checked on the KA A-B
+    pair (sigma_AB = 0.8), which also fixes that the length scale of x is the
+    pair's own sigma."""
+    h = 0.005
+    raw = synth.ka_params(shift=shift)
+    smo = synth.ka_params(shift=shift, smooth=h)
+    hs = h * 0.8
+    r = 2.0 - hs                       # r_c,AB = 2.5 * 0.8
+    v0, f0 = oracle.pair(raw, 0, 1, r * r)
+    v1, f1 = oracle.pair(smo, 0, 1, r * r)
+    assert v1 == pytest.approx(0.5 * v0, rel=1e-12)
+    assert f1 == pytest.approx(0.5 * f0 + v0 / (hs * r), rel=1e-9)
+
+
+@pytest.mark.parametrize("shift,pv,pf", [(False, 4, 3), (True, 5, 4)])
+def test_smoothed_potential_vanishes_with_its_derivatives_at_cutoff(shift, pv, pf):
+    """U = V g behaves as (r_c - r)^4 V(r_c) near the cutoff (as (r_c - r)^5
+    when V(r_c) = 0 by the shift), its force one power lower: U, U' and U''
+    all vanish at r_c, the C^2 continuity claimed in Sec. 4."""
+    p = synth.lj_params(shift=shift, smooth=0.005)
+    d = 0.005 * 1e-3
+    v1, f1 = oracle.pair(p, 0, 0, (2.5 - d) ** 2)
+    v2, f2 = oracle.pair(p, 0, 0, (2.5 - 2 * d) ** 2)
+    assert v2 / v1 == pytest.approx(2.0 ** pv, rel=1e-2)
+    assert f2 / f1 == pytest.approx(2.0 ** pf, rel=1e-2)
+    assert abs(v1) < 1e-13 and abs(f1) < 1e-7
+
+
+def test_smoothing_far_inside_cutoff_recovers_potential():
+    """At x = -50, g = 50^4 / (1 + 50^4)."""
+    h = 0.005
+    r = 2.5 - 50 * h
+    v0, _ = oracle.pair(synth.lj_params(), 0, 0, r * r)
+    v1, _ = oracle.pair(synth.lj_params(smooth=h), 0, 0, r * r)
+    assert v1 == pytest.approx(v0 * 50.0 ** 4 / (1 + 50.0 ** 4), rel=1e-13)
+
+
+@pytest.mark.parametrize("params", [synth.lj_params(smooth=0.005), synth.wca_params(smooth=0.005),
+                                    synth.ka_params(smooth=0.005)])
+@pytest.mark.parametrize("frac", [0.9, 0.97, 0.995, 0.999])
+def test_smoothed_force_is_minus_derivative(params, frac):
+    """fr = -U'(r)/r by central differences, down to r_c - 0.25 h sigma."""
+    for a, b in ((0, 0), (0, 1)) if params["n_species"] == 2 else ((0, 0),):
+        rc = params["rcut"][a][b]
+        r = rc * frac
+        d = 1e-7
+        vp, _ = oracle.pair(params, a, b, (r + d) ** 2)
+        vm, _ = oracle.pair(params, a, b, (r - d) ** 2)
+        _, fr = oracle.pair(params, a, b, r * r)
+        assert -fr * r == pytest.approx((vp - vm) / (2 * d), rel=1e-5, abs=1e-8)
+
+
+def test_wca_liquid_energy_error_scales_as_dt_squared():
+    """Velocity Verlet on a smoothed WCA liquid (rho = 0.75, T = 1.12, the
+    state point of Sec. 4): the largest energy deviation over a fixed time
+    drops by 4 when dt halves."""
+    s = synth.make_system(256, 0.75, 1.12, 11, synth.wca_params(smooth=0.005))
+    pos, vel, img, _, _ = oracle.vv_run(s.params, s.box, s.species, s.pos, s.vel, s.image, 0.002, 300)
+    errs = []
+    for dt in (0.002, 0.001):
+        *_, rec = oracle.vv_run(s.params, s.box, s.species, pos, vel, img, dt, int(round(0.4 / dt)),
+                                sample=1)
+        e = rec["e_pot"] + rec["e_kin"]
+        errs.append(np.abs(e - e[0]).max())
+    assert errs[0] / errs[1] == pytest.approx(4.0, rel=0.25)

@@ -20,6 +20,10 @@ Functions (all arrays float64 / int32, original particle order):
   rescale(params, species, vel, T)       -> vel scaled to T         (Sec. 2.3)
   neighbours_brute(params, L, species, pos, skin, kmax)
                                          -> (counts[n], lists[n,kmax])
+  rand48_seed / rand48_step / rand48_leapfrog / rand48_uniforms
+                                         the rand48 generator and its leapfrog (Sec. 2.3)
+  andersen(params, species, vel, T, seed, event)
+                                         one Andersen heat-bath collision      (Sec. 2.3)
 """
 from __future__ import annotations
 
@@ -83,6 +87,15 @@ def _load():
                                        C.POINTER(_Obs), C.c_long]
             lib.orc_vv_run.restype = C.c_long
             lib.orc_rescale.argtypes = [P, C.c_long, _ip, _dp, C.c_double]
+            u64 = C.c_ulonglong
+            lib.orc_rand48_seed.argtypes = [u64]
+            lib.orc_rand48_seed.restype = u64
+            lib.orc_rand48_step.argtypes = [u64, C.c_longlong]
+            lib.orc_rand48_step.restype = u64
+            lib.orc_rand48_leapfrog.argtypes = [C.c_longlong, C.POINTER(u64), C.POINTER(u64)]
+            lib.orc_rand48_uniforms.argtypes = [u64, C.c_longlong, C.c_longlong, _dp]
+            lib.orc_andersen.argtypes = [P, C.c_long, _ip, _dp, C.c_double, u64, C.c_longlong,
+                                         C.c_longlong, C.c_longlong]
             lib.orc_rescale.restype = None
             lib.orc_neighbours_brute.argtypes = [P, C.c_long, C.c_double, _ip, _dp, C.c_double,
                                                  _ip, C.c_void_p, C.c_long]
@@ -198,6 +211,40 @@ def rescale(params, species, vel, temperature):
     n = len(species)
     v = _f64(vel, (n, 3)).copy()
     _load().orc_rescale(C.byref(_pot(params)), n, _i32(species), v, float(temperature))
+    return v
+
+
+def rand48_seed(seed: int) -> int:
+    return int(_load().orc_rand48_seed(seed))
+
+
+def rand48_step(x: int, n: int) -> int:
+    """n steps of the rand48 recurrence from state x, one at a time."""
+    return int(_load().orc_rand48_step(x, n))
+
+
+def rand48_leapfrog(T: int) -> tuple[int, int]:
+    """(A_T, C_T) of the leapfrog over T threads, from their definitions."""
+    A, Cc = C.c_ulonglong(), C.c_ulonglong()
+    _load().orc_rand48_leapfrog(T, C.byref(A), C.byref(Cc))
+    return int(A.value), int(Cc.value)
+
+
+def rand48_uniforms(seed: int, first: int, count: int) -> np.ndarray:
+    u = np.empty(count)
+    _load().orc_rand48_uniforms(seed, first, count, _f64(u))
+    return u
+
+
+def andersen(params, species, vel, temperature, seed, event, nthreads=None, first_index=0):
+    """One Andersen collision of every particle (Sec. 2.3): returns new
+    velocities (original order); particle i is thread first_index + i of a
+    leapfrog over nthreads (default: the particle count) threads."""
+    sp = _i32(species)
+    n = sp.shape[0]
+    v = _f64(np.array(vel, dtype=np.float64, copy=True), (n, 3))
+    _load().orc_andersen(C.byref(_pot(params)), n, sp, v, float(temperature), int(seed), int(event),
+                         int(nthreads if nthreads is not None else n), int(first_index))
     return v
 
 

@@ -386,3 +386,97 @@ long orc_neighbours_brute(const orc_pot *p, long n, double L, const int *type,
     }
     return maxc;
 }
+
+/* ------------------------------------------------------------------------ */
+/* The rand48 generator and the Andersen heat bath (Sec. 2.3).              */
+/*                                                                          */
+/* rand48: x_{n+1} = (a x_n + c) mod 2^48 with a = 0x5DEECE66D, c = 0xB (the */
+/* POSIX drand48 family); seeding as srand48: x_0 = (seed mod 2^32) 2^16 +  */
+/* 0x330E; deviate n (n = 0, 1, ...) is d_n = x_{n+1} / 2^48, the value of  */
+/* the (n+1)-th drand48 call.  With T threads, thread t produces the        */
+/* deviates t, t + T, t + 2T, ... of this one sequence by the leapfrog      */
+/* x_{n+T} = A_T x_n + C_T, A_T = a^T, C_T = c sum_{n<T} a^n (mod 2^48).    */
+/* ------------------------------------------------------------------------ */
+#define R48_MASK 0xFFFFFFFFFFFFULL
+static const unsigned long long R48_A = 0x5DEECE66DULL, R48_C = 0xBULL;
+
+unsigned long long orc_rand48_seed(unsigned long long seed)
+{
+    return ((seed & 0xFFFFFFFFULL) << 16) | 0x330EULL;
+}
+
+/* n steps of the recurrence, one at a time */
+unsigned long long orc_rand48_step(unsigned long long x, long long n)
+{
+    for (long long k = 0; k < n; ++k)
+        x = (R48_A * x + R48_C) & R48_MASK;
+    return x;
+}
+
+/* leapfrog multiplier and addend for T threads, from their definitions */
+void orc_rand48_leapfrog(long long T, unsigned long long *A, unsigned long long *C)
+{
+    unsigned long long pw = 1, sum = 0;          /* a^n and sum_{m<n} a^m */
+    for (long long n = 0; n < T; ++n) {
+        sum = (sum + pw) & R48_MASK;
+        pw = (pw * R48_A) & R48_MASK;
+    }
+    *A = pw;
+    *C = (R48_C * sum) & R48_MASK;
+}
+
+/* count deviates d_first .. d_{first+count-1} of the sequence from seed */
+void orc_rand48_uniforms(unsigned long long seed, long long first, long long count, double *u)
+{
+    unsigned long long x = orc_rand48_step(orc_rand48_seed(seed), first + 1);
+    for (long long k = 0; k < count; ++k) {
+        u[k] = (double)x / 281474976710656.0;    /* 2^48 */
+        x = (R48_A * x + R48_C) & R48_MASK;
+    }
+}
+
+/*
+ * One Andersen heat-bath collision of every particle (Sec. 2.3): fresh
+ * Maxwell-Boltzmann velocities at temperature T, then the mass-weighted mean
+ * velocity is removed and the set rescaled so that 2 E_kin / (3N - 3) = T
+ * exactly.  Particle i (original index) is thread i of a leapfrog over
+ * nthreads threads; collision `event` uses its draws 4 event .. 4 event + 3,
+ * i.e. the sequence elements (4 event + k) nthreads + i.  Box-Muller:
+ *   v_x = s sqrt(-2 ln(1 - u0)) cos(2 pi u1),  v_y = ... sin(2 pi u1),
+ *   v_z = s sqrt(-2 ln(1 - u2)) cos(2 pi u3),  s = sqrt(T / m_i).
+ * The sequence is generated one element at a time (no jump-ahead).
+ */
+void orc_andersen(const orc_pot *p, long n, const int *type, double *vel, double T,
+                  unsigned long long seed, long long event, long long nthreads, long long first_index)
+{
+    long long span = 4 * nthreads;
+    double *u = (double *)malloc(sizeof(double) * (size_t)span);
+    orc_rand48_uniforms(seed, 4 * event * nthreads, span, u);
+    const double two_pi = 6.283185307179586476925286766559;
+    for (long i = 0; i < n; ++i) {
+        long long t = first_index + i;
+        double u0 = u[0 * nthreads + t], u1 = u[1 * nthreads + t];
+        double u2 = u[2 * nthreads + t], u3 = u[3 * nthreads + t];
+        double r1 = sqrt(-2.0 * log(1.0 - u0)), r2 = sqrt(-2.0 * log(1.0 - u2));
+        double s = sqrt(T / p->mass[type[i]]);
+        vel[3 * i + 0] = s * r1 * cos(two_pi * u1);
+        vel[3 * i + 1] = s * r1 * sin(two_pi * u1);
+        vel[3 * i + 2] = s * r2 * cos(two_pi * u3);
+    }
+    free(u);
+    double mtot = 0.0, mom[3] = {0.0, 0.0, 0.0};
+    for (long i = 0; i < n; ++i) {
+        double m = p->mass[type[i]];
+        mtot += m;
+        for (int k = 0; k < 3; ++k)
+            mom[k] += m * vel[3 * i + k];
+    }
+    for (long i = 0; i < n; ++i)
+        for (int k = 0; k < 3; ++k)
+            vel[3 * i + k] -= mom[k] / mtot;
+    if (n > 1 && T > 0.0)
+        orc_rescale(p, n, type, vel, T);
+    else
+        for (long i = 0; i < 3 * n; ++i)
+            vel[i] = 0.0;
+}

@@ -434,3 +434,69 @@ def test_wca_liquid_energy_error_scales_as_dt_squared():
         e = rec["e_pot"] + rec["e_kin"]
         errs.append(np.abs(e - e[0]).max())
     assert errs[0] / errs[1] == pytest.approx(4.0, rel=0.25)
+
+
+# --------------------------------------------------------------------------
+# Sec. 2.3: rand48 with leapfrogging, and the Andersen heat bath
+# --------------------------------------------------------------------------
+
+def _libc():
+    import ctypes
+    import ctypes.util
+    libc = ctypes.CDLL(ctypes.util.find_library("c") or None)
+    libc.drand48.restype = ctypes.c_double
+    libc.srand48.argtypes = [ctypes.c_long]
+    return libc
+
+
+@pytest.mark.parametrize("seed", [0, 1, 12345, 2 ** 31 + 7])
+def test_rand48_matches_the_c_library(seed):
+    """The oracle's rand48 against the C library's drand48 (an independent
+    implementation of the same published recurrence), bit for bit."""
+    libc = _libc()
+    libc.srand48(seed)
+    ref = np.array([libc.drand48() for _ in range(2000)])
+    assert np.array_equal(oracle.rand48_uniforms(seed, 0, 2000), ref)
+    assert np.array_equal(oracle.rand48_uniforms(seed, 1500, 500), ref[1500:])
+
+
+@pytest.mark.parametrize("T", [1, 2, 7, 1000, 65536])
+def test_rand48_leapfrog_equals_sequential_steps(T):
+    """x_{n+T} = A_T x_n + C_T with A_T = a^T, C_T = c sum a^n (mod 2^48)."""
+    A, Cc = oracle.rand48_leapfrog(T)
+    if T == 1:
+        assert (A, Cc) == (0x5DEECE66D, 0xB)
+    for x in (0x330E, 0xFFFFFFFFFFFF, 0x123456789ABC, oracle.rand48_seed(99)):
+        assert (A * x + Cc) % 2 ** 48 == oracle.rand48_step(x, T)
+
+
+def test_andersen_draws_from_interleaved_leapfrog_streams():
+    """Particle i of N uses the deviates (4e + k) N + i of the C library's
+    drand48 sequence for collision e; Box-Muller, mean removal and exact
+    rescaling then give the velocities."""
+    n, seed, event, T = 50, 777, 2, 1.3
+    libc = _libc()
+    libc.srand48(seed)
+    d = np.array([libc.drand48() for _ in range(4 * n * (event + 1))])
+    u = d[4 * n * event:].reshape(4, n)
+    r1, r2 = np.sqrt(-2 * np.log1p(-u[0])), np.sqrt(-2 * np.log1p(-u[2]))
+    v = np.stack([r1 * np.cos(2 * np.pi * u[1]), r1 * np.sin(2 * np.pi * u[1]),
+                  r2 * np.cos(2 * np.pi * u[3])], axis=1) * np.sqrt(T)
+    v -= v.mean(axis=0)
+    v *= np.sqrt(T * (3 * n - 3) / (v * v).sum())
+    got = oracle.andersen(synth.lj_params(), np.zeros(n, np.int32), np.zeros((n, 3)), T, seed, event)
+    assert np.abs(got - v).max() < 1e-13
+
+
+def test_andersen_temperature_momentum_and_distribution():
+    p = synth.ka_params()
+    s = synth.ka_mixture(6000, temperature=1.0, seed=4)
+    v = oracle.andersen(p, s.species, s.vel, 0.8, 4242, 0)
+    ek, mom = oracle.kinetic(p, s.species, v)
+    assert 2 * ek / (3 * s.n - 3) == pytest.approx(0.8, rel=1e-13)
+    assert np.abs(mom).max() < 1e-11
+    x = v.ravel() / np.sqrt(0.8)
+    assert abs(np.mean(x ** 4) / np.mean(x ** 2) ** 2 - 3.0) < 0.15     # Gaussian kurtosis
+    v2 = oracle.andersen(p, s.species, s.vel, 0.8, 4242, 1)
+    assert np.abs(v2 - v).min() > 0 and abs(np.corrcoef(v.ravel(), v2.ravel())[0, 1]) < 0.05
+    assert np.array_equal(v, oracle.andersen(p, s.species, s.vel, 0.8, 4242, 0))

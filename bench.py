@@ -51,7 +51,8 @@ def parse_args(argv=None):
     ap.add_argument("--no-graph", action="store_true",
                     help="plain stream launches instead of the CUDA graph (for per-kernel profiling)")
     ap.add_argument("--tpp", type=int, default=0, help="force-kernel threads per particle (0 = auto)")
-    ap.add_argument("--workload", choices=["ka65536", "lj-sweep", "replicas", "drift"], default="ka65536",
+    ap.add_argument("--workload", choices=["ka65536", "lj-sweep", "replicas", "drift", "stability"],
+                    default="ka65536",
                     help="ka65536: the headline line; the others print one line per case")
     ap.add_argument("--sizes", type=int, nargs="*", default=None, help="lj-sweep particle counts")
     ap.add_argument("--md-steps", type=int, default=100000, help="drift: NVE MD steps per run")
@@ -320,11 +321,11 @@ def run_ours(args, rank, world, local):
     sm_mhz = clk.get("sm_mhz") or 1.9e3
     peak_max = 152 * 128 * 2 * 2.07e9 / 1e12
     result["roofline"] = {
-        "bound": "alu", "kernel": f"k_step<{args.precision}, {info1['threads_per_particle']}> "
+        "bound": "alu", "kernel": f"k_step<{args.precision}, {info1['threads_per_particle']}, unsmoothed> "
                                   "(pair forces + velocity-Verlet update)",
         "achieved": flops / (f_ms * 1e-3) / 1e12, "peak": peak_max, "unit": "TFLOP/s",
         "frac": flops / (f_ms * 1e-3) / 1e12 / peak_max,
-        "traffic": profiled_traffic(f"k_step<{md.PRECISIONS[args.precision]}, {info1['threads_per_particle']}>"),
+        "traffic": profiled_traffic(f"k_step<{md.PRECISIONS[args.precision]}, {info1['threads_per_particle']}, 0>"),
         "per_launch_ms": f_ms, "flop_per_launch": flops, "mean_list": float(n_list),
         "mean_in_cutoff": float(n_cut),
         "peak_note": "FP32 FMA peak 152 SM x 128 lanes x 2 flop x 2.07 GHz (max clock)",
@@ -545,14 +546,36 @@ def run_drift(args, local):
     """Energy drift, momentum and MSD in FP32, mixed and FP64 from the same
     equilibrated state: LJ N=864 (dt 0.005), KA N=16384 at T=0.7 (two seeds)
     and KA N=65536 quenched to T=0.5 (rescaled every step for 10^4 steps)."""
-    torch, md, synth, device, stream, flush = _gpu_setup(local)
+    from paper_0912_3824_gb300 import synth
     M = args.md_steps
-    lags = [10 ** k for k in range(1, 8)]
     cases = [("lj864", lambda: synth.lj_fluid(864, density=0.8442, temperature=0.722, seed=1), 0.005,
               None, min(M, 100000)),
              ("ka16384-s2", lambda: synth.ka_mixture(16384, temperature=2.0, seed=2), 0.001, (2.0, 0.7), M),
              ("ka16384-s3", lambda: synth.ka_mixture(16384, temperature=2.0, seed=3), 0.001, (2.0, 0.7), M),
              ("ka65536", lambda: synth.ka_mixture(65536, temperature=2.0, seed=5), 0.001, (2.0, 0.5), M)]
+    return nve_cases(args, local, cases, "drift")
+
+
+def run_stability(args, local):
+    """The stability protocol of Sec. 4: N = 10000 at rho = 0.75, T = 1.12,
+    LJ (r_c = 2.5) and WCA, dt = 0.001 and 0.003, smoothing h = 0 and 0.005,
+    each in FP32, mixed and FP64 from the same equilibrated state."""
+    from paper_0912_3824_gb300 import synth
+    cases = []
+    for pot in ("wca", "lj"):
+        for h in (0.0, 0.005):
+            for dt in (0.001, 0.003):
+                mk = synth.wca_params if pot == "wca" else synth.lj_params
+                params = mk(smooth=h)
+                cases.append((f"{pot}-h{h}-dt{dt}",
+                               lambda params=params: synth.make_system(10000, 0.75, 1.12, 12, params),
+                               dt, (1.12, 1.12), args.md_steps))
+    return nve_cases(args, local, cases, "stability")
+
+
+def nve_cases(args, local, cases, workload):
+    torch, md, synth, device, stream, flush = _gpu_setup(local)
+    lags = [10 ** k for k in range(1, 8)]
     if args.cases:
         cases = [c for c in cases if c[0] in args.cases]
     lines = []
@@ -577,7 +600,8 @@ def run_drift(args, local):
             sim.close()
             slope, maxdev = energy_drift(obs, s.n)
             pmax = float(np.abs(obs["p"]).max()) / s.n
-            lines.append({"workload": "drift", "case": name, "precision": prec, "n": s.n, "dt": dt,
+            lines.append({"workload": workload, "case": name, "precision": prec, "n": s.n, "dt": dt,
+                          "smooth_h": float(s.params.get("smooth", 0.0)),
                           "md_steps": nsteps, "value": s.n * nsteps / (ms * 1e-3), "unit": UNIT,
                           "us_per_md_step": ms * 1e3 / nsteps,
                           "energy_drift_per_step_rel": slope,
@@ -631,7 +655,8 @@ def main(argv=None):
     if args.workload != "ka65536":
         if args.impl == "reference" or world > 1:
             raise SystemExit("--workload other than ka65536 runs our path on one GPU only")
-        fn = {"lj-sweep": run_lj_sweep, "replicas": run_replicas, "drift": run_drift}[args.workload]
+        fn = {"lj-sweep": run_lj_sweep, "replicas": run_replicas, "drift": run_drift,
+              "stability": run_stability}[args.workload]
         for line in fn(args, local):
             print(json.dumps(line), flush=True)
         return

@@ -90,7 +90,13 @@ typedef struct {
                                  the step loop decided on the device (default); 0 = plain
                                  stream launches, for debugging and per-kernel timing          */
     int32_t reorder;          /* 1 = order cells along a Morton curve (default); 0 = x-fastest  */
-    int32_t reserved[7];      /* must be zero                                                   */
+    int32_t reserved0;        /* must be zero                                                   */
+    double  smooth_h;         /* h >= 0 of the smoothing of Sec. 4: every pair potential is
+                                 multiplied by g(x) = x^4 / (1 + x^4), x = (r - r_c,ab) /
+                                 (h sigma_ab), which makes it and its first two derivatives
+                                 vanish at r_c; 0 = no smoothing (the paper uses h = 0.005).
+                                 Not supported by md_forces_noalloc.                           */
+    int32_t reserved[4];      /* must be zero                                                   */
 } md_params;
 
 /* one sample of the reductions of Sec. 2.2, per replica */

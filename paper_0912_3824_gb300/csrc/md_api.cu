@@ -29,6 +29,8 @@
 #include "md.h"
 #include "md_common.cuh"
 
+static_assert(sizeof(md_params) == 192, "md_params layout is part of the ABI");
+
 using mdk::KArgs;
 using mdk::KernelSet;
 
@@ -105,8 +107,17 @@ int make_geometry(const md_params *p, int R, const int64_t *nrep, const double *
         msg = "threads_per_particle must be 0 or a power of two in [1, 32]";
         return MD_E_INVAL;
     }
-    for (int k = 0; k < 7; ++k)
+    if (p->reserved0 != 0) { msg = "reserved fields must be zero"; return MD_E_INVAL; }
+    for (int k = 0; k < 4; ++k)
         if (p->reserved[k] != 0) { msg = "reserved fields must be zero"; return MD_E_INVAL; }
+    if (!(p->smooth_h >= 0.0) || !std::isfinite(p->smooth_h)) {
+        msg = "smooth_h must be finite and >= 0";
+        return MD_E_INVAL;
+    }
+    if (p->smooth_h > 0.0 && tpp > 8) {
+        msg = "threads_per_particle above 8 is not available with the smoothed potential";
+        return MD_E_INVAL;
+    }
     const int ns = p->n_species;
     double rcmax = 0.0;
     for (int a = 0; a < ns; ++a) {
@@ -396,7 +407,7 @@ int launch_force(md_handle *h, int fsample)
 {
     KArgs a = h->a;
     a.fsample = fsample;
-    return launch(h, h->ks->force[force_index(h->g.tpp)], h->g.nblk_f, kForceBlock, a);
+    return launch(h, h->ks->force[h->p.smooth_h > 0.0][force_index(h->g.tpp)], h->g.nblk_f, kForceBlock, a);
 }
 
 int launch_integrate(md_handle *h, int mode)
@@ -480,7 +491,7 @@ int build_graph(md_handle *h)
     if ((rc = add_conditional(h, g, &n_while, n_if0, c_loop, cudaGraphCondTypeWhile, &wbody)))
         return rc;
     // loop body: kUnroll step kernels, a conditional rebuild after every kCheck
-    const void *stepk = h->ks->step[force_index(h->g.tpp)];
+    const void *stepk = h->ks->step[h->p.smooth_h > 0.0][force_index(h->g.tpp)];
     cudaGraphNode_t prev = nullptr;
     for (int slot = 0; slot < kUnroll; ++slot) {
         KArgs sa = step_args(h, slot);
@@ -767,6 +778,12 @@ static int create_impl(md_handle *h, const md_params *p, const int32_t *species,
             a.tab.eps4[k] = (float)(4.0 * eps);
             a.tab.eps48[k] = (float)(48.0 * eps);
             a.tab.shift[k] = (float)shift;
+            // smoothing of Sec. 4: x = (r - r_c) / (h sigma_ab)
+            const double ihs = p->smooth_h > 0.0 ? 1.0 / (p->smooth_h * sig) : 0.0;
+            a.tab.rcd[k] = rc;
+            a.tab.ihsd[k] = ihs;
+            a.tab.rc[k] = (float)rc;
+            a.tab.ihs[k] = (float)ihs;
         }
     for (int s = 0; s < 2; ++s) {
         const int ss = std::min(s, p->n_species - 1);
@@ -873,7 +890,7 @@ int md_step(md_handle *h, int64_t nsteps)
     if ((rc = launch(h, h->ks->integrate, h->g.nblk_i, kIntBlock, first_args(h))) ||
         (rc = rebuild_if_flagged(h, nullptr)))
         return rc;
-    const void *stepk = h->ks->step[force_index(h->g.tpp)];
+    const void *stepk = h->ks->step[h->p.smooth_h > 0.0][force_index(h->g.tpp)];
     const int64_t iters = (nsteps + kUnroll - 1) / kUnroll;
     for (int64_t it = 0; it < iters; ++it) {
         for (int slot = 0; slot < kUnroll; ++slot) {

@@ -63,7 +63,9 @@ struct Rep {                  // one independent system
 
 struct PairTab {              // [a*2+b]
     float rc2[4], rl2[4], sig2[4], eps4[4], eps48[4], shift[4];
+    float rc[4], ihs[4];      // r_c and 1 / (h sigma) of the smoothing (Sec. 4)
     double rc2d[4], rl2d[4], sig2d[4], eps4d[4], eps48d[4], shiftd[4];
+    double rcd[4], ihsd[4];
 };
 
 struct Obs {                  // identical layout to md_obs
@@ -164,7 +166,8 @@ __device__ __forceinline__ ds ds_from_double(double x)
 
 // table of kernel entry addresses for one precision (one translation unit each)
 struct KernelSet {
-    const void *integrate, *force[6], *step[6], *bin, *scan, *scatter, *permute, *nbuild, *flip;
+    const void *integrate, *force[2][6], *step[2][6];   // [smoothed][log2 lanes per particle]
+    const void *bin, *scan, *scatter, *permute, *nbuild, *flip;
     const void *load, *getstate, *expforce, *scale, *set_steps, *reset, *mark_rebuild;
 };
 

@@ -36,6 +36,8 @@ constexpr int kForceBlock = 256; // force / step kernels: tpp threads per partic
 constexpr int kNbBlock = 256;    // neighbour build: one block per cell
 constexpr int kScanBlock = 1024;
 constexpr int kPartF = 12;       // doubles per block partial of the force / step kernels
+constexpr int kUnr = 4;          // list entries per lane and iteration of the FP32 pair loops
+                                 // (a multiple of 4, at most 8: lists are padded to 8)
 
 // ---------------------------------------------------------------------------
 // small helpers
@@ -188,6 +190,33 @@ __device__ __forceinline__ void kahan_add(float &s, float &c, float x)
     float t = __fadd_rn(s, y);
     c = __fsub_rn(__fsub_rn(t, s), y);
     s = t;
+}
+
+// Smoothing of Sec. 4: U = V g(x), g(x) = x^4 / (1 + x^4), x = (r - r_c) / (h sigma_ab).
+// On entry fr = -V'(r)/r and v = V(r); on exit fr = -U'(r)/r and v = U(r):
+//   -U'/r = (-V'/r) g - V g'(x) / (h sigma r),  g'(x) = 4 x^3 / (1 + x^4)^2.
+__device__ __forceinline__ void smooth_pair(float r2, float rc, float ihs, float &fr, float &v)
+{
+    const float rinv = rsqrtf(r2);
+    const float x = (r2 * rinv - rc) * ihs;
+    const float x2 = x * x, x4 = x2 * x2;
+    const float den = __fdividef(1.0f, 1.0f + x4);
+    const float g = x4 * den;
+    const float dg = 4.0f * x2 * x * den * den;
+    fr = fr * g - v * dg * ihs * rinv;
+    v = v * g;
+}
+
+__device__ __forceinline__ void smooth_pair(double r2, double rc, double ihs, double &fr, double &v)
+{
+    const double r = sqrt(r2);
+    const double x = (r - rc) * ihs;
+    const double x2 = x * x, x4 = x2 * x2;
+    const double den = 1.0 / (1.0 + x4);
+    const double g = x4 * den;
+    const double dg = 4.0 * x2 * x * den * den;
+    fr = fr * g - v * dg * ihs / r;
+    v = v * g;
 }
 
 template <int P> using FT = typename std::conditional<P == FP64, double, float>::type;
@@ -496,10 +525,10 @@ __device__ __forceinline__ unsigned int need_rebuild(const KArgs &a, float md2, 
 // holds the particle's share of E_pot, W and W_ab.
 // ---------------------------------------------------------------------------
 template <typename T> struct PairRow {   // parameters of (species i, species j = 0 / 1)
-    T rc2[2], sig2[2], eps4[2], eps48[2], shift[2];
+    T rc2[2], sig2[2], eps4[2], eps48[2], shift[2], rc[2], ihs[2];
 };
 
-template <int P, int TPP, bool SAMPLE>
+template <int P, int TPP, bool SAMPLE, bool SM>
 __device__ __forceinline__ void pair_forces(const KArgs &a, const Rep &rp, int pp, int ii, int nn,
                                             FT<P> &fx, FT<P> &fy, FT<P> &fz, double *acc)
 {
@@ -517,6 +546,8 @@ __device__ __forceinline__ void pair_forces(const KArgs &a, const Rep &rp, int p
             pr.eps4[tj] = a.tab.eps4d[ti * 2 + tj];
             pr.eps48[tj] = a.tab.eps48d[ti * 2 + tj];
             pr.shift[tj] = a.tab.shiftd[ti * 2 + tj];
+            pr.rc[tj] = a.tab.rcd[ti * 2 + tj];
+            pr.ihs[tj] = a.tab.ihsd[ti * 2 + tj];
         }
         double sx = 0, sy = 0, sz = 0, en = 0, vir = 0, wxx = 0, wyy = 0, wzz = 0, wxy = 0, wxz = 0, wyz = 0;
         for (int k0 = 4 * lane; k0 < nn; k0 += 4 * TPP) {
@@ -540,12 +571,17 @@ __device__ __forceinline__ void pair_forces(const KArgs &a, const Rep &rp, int p
                     const double ir2 = 1.0 / r2;
                     const double s2 = pr.sig2[tj] * ir2;
                     const double s6 = s2 * s2 * s2;
-                    const double fr = pr.eps48[tj] * ir2 * s6 * (s6 - 0.5);
+                    double fr = pr.eps48[tj] * ir2 * s6 * (s6 - 0.5);
+                    double v = 0.0;
+                    if (SM || SAMPLE)
+                        v = pr.eps4[tj] * s6 * (s6 - 1.0) - pr.shift[tj];
+                    if (SM)
+                        smooth_pair(r2, pr.rc[tj], pr.ihs[tj], fr, v);
                     sx += fr * dx;
                     sy += fr * dy;
                     sz += fr * dz;
                     if (SAMPLE) {
-                        en += pr.eps4[tj] * s6 * (s6 - 1.0) - pr.shift[tj];
+                        en += v;
                         vir += fr * r2;
                         wxx += fr * dx * dx; wyy += fr * dy * dy; wzz += fr * dz * dz;
                         wxy += fr * dx * dy; wxz += fr * dx * dz; wyz += fr * dy * dz;
@@ -593,16 +629,25 @@ __device__ __forceinline__ void pair_forces(const KArgs &a, const Rep &rp, int p
             pr.eps4[tj] = a.tab.eps4[ti * 2 + tj];
             pr.eps48[tj] = a.tab.eps48[ti * 2 + tj];
             pr.shift[tj] = a.tab.shift[ti * 2 + tj];
+            pr.rc[tj] = a.tab.rc[ti * 2 + tj];
+            pr.ihs[tj] = a.tab.ihs[ti * 2 + tj];
         }
         float sx = 0.f, sy = 0.f, sz = 0.f, cx = 0.f, cy = 0.f, cz = 0.f;
         float en = 0.f, vir = 0.f, wxx = 0.f, wyy = 0.f, wzz = 0.f, wxy = 0.f, wxz = 0.f, wyz = 0.f;
-        for (int k0 = 4 * lane; k0 < nn; k0 += 4 * TPP) {
-            const int4 q = __ldg((const int4 *)(lst + k0));
-            const int jj[4] = {q.x, q.y, q.z, q.w};
-            float4 Hs[4];
-            int4 Qs[4];
+        for (int k0 = kUnr * lane; k0 < nn; k0 += kUnr * TPP) {
+            int jj[kUnr];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int w = 0; w < kUnr / 4; ++w) {   // K is a multiple of 8: in bounds, aligned
+                const int4 q = __ldg((const int4 *)(lst + k0 + 4 * w));
+                jj[4 * w] = q.x;
+                jj[4 * w + 1] = q.y;
+                jj[4 * w + 2] = q.z;
+                jj[4 * w + 3] = q.w;
+            }
+            float4 Hs[kUnr];
+            int4 Qs[kUnr];
+#pragma unroll
+            for (int u = 0; u < kUnr; ++u) {
                 const int j = k0 + u < nn ? jj[u] : ii;
                 if constexpr (P == MIXED)
                     Qs[u] = __ldg(qp + j);
@@ -611,7 +656,7 @@ __device__ __forceinline__ void pair_forces(const KArgs &a, const Rep &rp, int p
             }
             float gx = 0.f, gy = 0.f, gz = 0.f;
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < kUnr; ++u) {
                 int tj;
                 float dx, dy, dz;
                 if constexpr (P == MIXED) {
@@ -634,14 +679,20 @@ __device__ __forceinline__ void pair_forces(const KArgs &a, const Rep &rp, int p
                 const float ir2 = __fdividef(1.0f, in ? r2 : 1.0f);
                 const float s2 = sig2 * ir2;
                 const float s6 = s2 * s2 * s2;
-                const float fr = in ? eps48 * ir2 * s6 * (s6 - 0.5f) : 0.0f;
+                float fr = in ? eps48 * ir2 * s6 * (s6 - 0.5f) : 0.0f;
+                float v = 0.0f;
+                if (SM || SAMPLE) {
+                    const float eps4 = tj ? pr.eps4[1] : pr.eps4[0];
+                    const float shift = tj ? pr.shift[1] : pr.shift[0];
+                    v = in ? eps4 * s6 * (s6 - 1.0f) - shift : 0.0f;
+                }
+                if (SM)
+                    smooth_pair(in ? r2 : 1.0f, tj ? pr.rc[1] : pr.rc[0], tj ? pr.ihs[1] : pr.ihs[0], fr, v);
                 gx = fmaf(fr, dx, gx);
                 gy = fmaf(fr, dy, gy);
                 gz = fmaf(fr, dz, gz);
                 if (SAMPLE) {
-                    const float eps4 = tj ? pr.eps4[1] : pr.eps4[0];
-                    const float shift = tj ? pr.shift[1] : pr.shift[0];
-                    en += in ? eps4 * s6 * (s6 - 1.0f) - shift : 0.0f;
+                    en += v;
                     vir += fr * r2;
                     wxx += fr * dx * dx; wyy += fr * dy * dy; wzz += fr * dz * dz;
                     wxy += fr * dx * dy; wxz += fr * dx * dz; wyz += fr * dy * dz;
@@ -697,7 +748,7 @@ __device__ __forceinline__ void pair_forces(const KArgs &a, const Rep &rp, int p
 // Potential energy, virial and virial tensor of particle ii (half of each pair,
 // Sec. 2.2 reductions), as a separate pass over the list on sample steps so
 // that the force loop carries no energy accumulators.  acc[0..7] = E, W, W_ab.
-template <int P, int TPP>
+template <int P, int TPP, bool SM>
 __device__ __forceinline__ void pair_energy(const KArgs &a, const Rep &rp, int pp, int ii, int nn, double *acc)
 {
     const int lane = threadIdx.x & (TPP - 1);
@@ -718,8 +769,11 @@ __device__ __forceinline__ void pair_energy(const KArgs &a, const Rep &rp, int p
                 const double ir2 = 1.0 / r2;
                 const double s2 = a.tab.sig2d[ab] * ir2;
                 const double s6 = s2 * s2 * s2;
-                const double fr = a.tab.eps48d[ab] * ir2 * s6 * (s6 - 0.5);
-                d8[0] += a.tab.eps4d[ab] * s6 * (s6 - 1.0) - a.tab.shiftd[ab];
+                double fr = a.tab.eps48d[ab] * ir2 * s6 * (s6 - 0.5);
+                double v = a.tab.eps4d[ab] * s6 * (s6 - 1.0) - a.tab.shiftd[ab];
+                if (SM)
+                    smooth_pair(r2, a.tab.rcd[ab], a.tab.ihsd[ab], fr, v);
+                d8[0] += v;
                 d8[1] += fr * r2;
                 d8[2] += fr * dx * dx; d8[3] += fr * dy * dy; d8[4] += fr * dz * dz;
                 d8[5] += fr * dx * dy; d8[6] += fr * dx * dz; d8[7] += fr * dy * dz;
@@ -739,8 +793,11 @@ __device__ __forceinline__ void pair_energy(const KArgs &a, const Rep &rp, int p
                 const float ir2 = __fdividef(1.0f, r2);
                 const float s2 = a.tab.sig2[ab] * ir2;
                 const float s6 = s2 * s2 * s2;
-                const float fr = a.tab.eps48[ab] * ir2 * s6 * (s6 - 0.5f);
-                d8[0] += a.tab.eps4[ab] * s6 * (s6 - 1.0f) - a.tab.shift[ab];
+                float fr = a.tab.eps48[ab] * ir2 * s6 * (s6 - 0.5f);
+                float v = a.tab.eps4[ab] * s6 * (s6 - 1.0f) - a.tab.shift[ab];
+                if (SM)
+                    smooth_pair(r2, a.tab.rc[ab], a.tab.ihs[ab], fr, v);
+                d8[0] += v;
                 d8[1] += fr * r2;
                 d8[2] += fr * dx * dx; d8[3] += fr * dy * dy; d8[4] += fr * dz * dz;
                 d8[5] += fr * dx * dy; d8[6] += fr * dx * dz; d8[7] += fr * dy * dz;
@@ -762,8 +819,11 @@ __device__ __forceinline__ void pair_energy(const KArgs &a, const Rep &rp, int p
                 const float ir2 = __fdividef(1.0f, r2);
                 const float s2 = a.tab.sig2[ab] * ir2;
                 const float s6 = s2 * s2 * s2;
-                const float fr = a.tab.eps48[ab] * ir2 * s6 * (s6 - 0.5f);
-                d8[0] += a.tab.eps4[ab] * s6 * (s6 - 1.0f) - a.tab.shift[ab];
+                float fr = a.tab.eps48[ab] * ir2 * s6 * (s6 - 0.5f);
+                float v = a.tab.eps4[ab] * s6 * (s6 - 1.0f) - a.tab.shift[ab];
+                if (SM)
+                    smooth_pair(r2, a.tab.rc[ab], a.tab.ihs[ab], fr, v);
+                d8[0] += v;
                 d8[1] += fr * r2;
                 d8[2] += fr * dx * dx; d8[3] += fr * dy * dy; d8[4] += fr * dz * dz;
                 d8[5] += fr * dx * dy; d8[6] += fr * dx * dz; d8[7] += fr * dy * dz;
@@ -797,7 +857,7 @@ __device__ __forceinline__ void store_force(const KArgs &a, int i, FT<P> fx, FT<
 // current positions; used when a handle is created or its state replaced and
 // by md_compute_forces.
 // ---------------------------------------------------------------------------
-template <int P, int TPP, bool SAMPLE>
+template <int P, int TPP, bool SAMPLE, bool SM>
 __device__ __forceinline__ void force_only(const KArgs &a)
 {
     __shared__ double sh[32 * kPartF];
@@ -815,9 +875,9 @@ __device__ __forceinline__ void force_only(const KArgs &a)
 #pragma unroll
     for (int k = 0; k < kPartF; ++k)
         acc[k] = 0.0;
-    pair_forces<P, TPP, false>(a, rp, pp, ii, nn, fx, fy, fz, acc);
+    pair_forces<P, TPP, false, SM>(a, rp, pp, ii, nn, fx, fy, fz, acc);
     if (SAMPLE)
-        pair_energy<P, TPP>(a, rp, pp, ii, nn, acc);
+        pair_energy<P, TPP, SM>(a, rp, pp, ii, nn, acc);
     if (!(valid && lane == 0)) {
 #pragma unroll
         for (int k = 0; k < kPartF; ++k)
@@ -834,7 +894,7 @@ __device__ __forceinline__ void force_only(const KArgs &a)
     }
 }
 
-template <int P, int TPP>
+template <int P, int TPP, bool SM>
 __global__ void __launch_bounds__(kForceBlock) k_force(KArgs a)
 {
     const Ctl *ctl = a.ctl;
@@ -843,9 +903,9 @@ __global__ void __launch_bounds__(kForceBlock) k_force(KArgs a)
     if (blockIdx.x == 0 && threadIdx.x == 0)
         atomicAdd((unsigned long long *)&a.ctl->n_force, 1ull);
     if (a.fsample || (ctl->step % a.si) == 0)
-        force_only<P, TPP, true>(a);
+        force_only<P, TPP, true, SM>(a);
     else
-        force_only<P, TPP, false>(a);
+        force_only<P, TPP, false, SM>(a);
 }
 
 // ---------------------------------------------------------------------------
@@ -953,7 +1013,7 @@ __device__ __forceinline__ void component_update(const KArgs &a, const Rep &rp, 
 // Step body for groups of at least 4 lanes: lanes 0-2 own one component each
 // of the update, lane 3 copies the species word; the operands of the update
 // are loaded before the neighbour loop so their latency is hidden.
-template <int P, int TPP, bool SAMPLE>
+template <int P, int TPP, bool SAMPLE, bool SM>
 __device__ __forceinline__ void step_body_split(const KArgs &a, bool active, bool last, int pp, int spar,
                                                 double *part, float &d2, float &v2, float &a2, unsigned int &bad)
 {
@@ -982,9 +1042,9 @@ __device__ __forceinline__ void step_body_split(const KArgs &a, bool active, boo
 #pragma unroll
     for (int k = 0; k < kPartF; ++k)
         part[k] = 0.0;
-    pair_forces<P, TPP, false>(a, rp, pp, ii, nn, fx, fy, fz, part);
+    pair_forces<P, TPP, false, SM>(a, rp, pp, ii, nn, fx, fy, fz, part);
     if (SAMPLE)
-        pair_energy<P, TPP>(a, rp, pp, ii, nn, part);
+        pair_energy<P, TPP, SM>(a, rp, pp, ii, nn, part);
     // Every lane of the warp must reach the shuffles below, including the
     // lanes of padding particles past the end of a replica's range: they skip
     // the update and contribute zeros.
@@ -1058,12 +1118,12 @@ __device__ __forceinline__ void step_body_split(const KArgs &a, bool active, boo
     }
 }
 
-template <int P, int TPP, bool SAMPLE>
+template <int P, int TPP, bool SAMPLE, bool SM>
 __device__ __forceinline__ void step_body(const KArgs &a, bool active, bool last, int pp, int spar,
                                           double *part, float &d2, float &v2, float &a2, unsigned int &bad)
 {
     if constexpr (TPP >= 4) {
-        step_body_split<P, TPP, SAMPLE>(a, active, last, pp, spar, part, d2, v2, a2, bad);
+        step_body_split<P, TPP, SAMPLE, SM>(a, active, last, pp, spar, part, d2, v2, a2, bad);
         return;
     }
     const int4 b = a.blk_f[blockIdx.x];
@@ -1077,9 +1137,9 @@ __device__ __forceinline__ void step_body(const KArgs &a, bool active, bool last
 #pragma unroll
     for (int k = 0; k < kPartF; ++k)
         part[k] = 0.0;
-    pair_forces<P, TPP, false>(a, rp, pp, ii, nn, fx, fy, fz, part);
+    pair_forces<P, TPP, false, SM>(a, rp, pp, ii, nn, fx, fy, fz, part);
     if (SAMPLE)
-        pair_energy<P, TPP>(a, rp, pp, ii, nn, part);
+        pair_energy<P, TPP, SM>(a, rp, pp, ii, nn, part);
     if (!(valid && lane == 0)) {
 #pragma unroll
         for (int k = 0; k < kPartF; ++k)
@@ -1104,7 +1164,7 @@ __device__ __forceinline__ void step_body(const KArgs &a, bool active, bool last
     store_vel<P>(a, spar, i, s);
 }
 
-template <int P, int TPP>
+template <int P, int TPP, bool SM>
 __global__ void __launch_bounds__(kForceBlock) k_step(KArgs a)
 {
     __shared__ double sh[32 * kPartF];
@@ -1124,9 +1184,9 @@ __global__ void __launch_bounds__(kForceBlock) k_step(KArgs a)
     float d2 = 0.f, v2 = 0.f, a2 = 0.f;
     unsigned int bad = 0u;
     if (sample)
-        step_body<P, TPP, true>(a, active, last, pp, spar, part, d2, v2, a2, bad);
+        step_body<P, TPP, true, SM>(a, active, last, pp, spar, part, d2, v2, a2, bad);
     else
-        step_body<P, TPP, false>(a, active, last, pp, spar, part, d2, v2, a2, bad);
+        step_body<P, TPP, false, SM>(a, active, last, pp, spar, part, d2, v2, a2, bad);
     if (bad)
         atomicOr(&ctl->status, bad);
 
@@ -1862,18 +1922,31 @@ KernelSet make_kernel_set()
 {
     KernelSet k;
     k.integrate = (const void *)k_integrate<P>;
-    k.force[0] = (const void *)k_force<P, 1>;
-    k.force[1] = (const void *)k_force<P, 2>;
-    k.force[2] = (const void *)k_force<P, 4>;
-    k.force[3] = (const void *)k_force<P, 8>;
-    k.force[4] = (const void *)k_force<P, 16>;
-    k.force[5] = (const void *)k_force<P, 32>;
-    k.step[0] = (const void *)k_step<P, 1>;
-    k.step[1] = (const void *)k_step<P, 2>;
-    k.step[2] = (const void *)k_step<P, 4>;
-    k.step[3] = (const void *)k_step<P, 8>;
-    k.step[4] = (const void *)k_step<P, 16>;
-    k.step[5] = (const void *)k_step<P, 32>;
+    k.force[0][0] = (const void *)k_force<P, 1, false>;
+    k.force[0][1] = (const void *)k_force<P, 2, false>;
+    k.force[0][2] = (const void *)k_force<P, 4, false>;
+    k.force[0][3] = (const void *)k_force<P, 8, false>;
+    k.force[0][4] = (const void *)k_force<P, 16, false>;
+    k.force[0][5] = (const void *)k_force<P, 32, false>;
+    k.step[0][0] = (const void *)k_step<P, 1, false>;
+    k.step[0][1] = (const void *)k_step<P, 2, false>;
+    k.step[0][2] = (const void *)k_step<P, 4, false>;
+    k.step[0][3] = (const void *)k_step<P, 8, false>;
+    k.step[0][4] = (const void *)k_step<P, 16, false>;
+    k.step[0][5] = (const void *)k_step<P, 32, false>;
+    // smoothed potential (Sec. 4): the common lane counts only
+    k.force[1][0] = (const void *)k_force<P, 1, true>;
+    k.force[1][1] = (const void *)k_force<P, 2, true>;
+    k.force[1][2] = (const void *)k_force<P, 4, true>;
+    k.force[1][3] = (const void *)k_force<P, 8, true>;
+    k.force[1][4] = nullptr;
+    k.force[1][5] = nullptr;
+    k.step[1][0] = (const void *)k_step<P, 1, true>;
+    k.step[1][1] = (const void *)k_step<P, 2, true>;
+    k.step[1][2] = (const void *)k_step<P, 4, true>;
+    k.step[1][3] = (const void *)k_step<P, 8, true>;
+    k.step[1][4] = nullptr;
+    k.step[1][5] = nullptr;
     k.bin = (const void *)k_bin<P>;
     k.scan = (const void *)k_scan<P>;
     k.scatter = (const void *)k_scatter<P>;

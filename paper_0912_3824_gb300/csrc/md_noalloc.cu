@@ -183,6 +183,9 @@ extern "C" int md_forces_noalloc(const md_params *p, int64_t n, double box, cons
                                 "fixed scratch area; use md_create / md_compute_forces instead");
     if (p->n_species < 1 || p->n_species > 2)
         return fail(MD_E_INVAL, "md_forces_noalloc: n_species must be 1 or 2");
+    if (p->smooth_h != 0.0)
+        return fail(MD_E_INVAL, "md_forces_noalloc: the smoothed potential (smooth_h > 0) is not supported; "
+                                "use md_create / md_compute_forces");
     Pot pot;
     double rcmax = 0.0;
     for (int a = 0; a < 2; ++a)

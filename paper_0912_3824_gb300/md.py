@@ -34,7 +34,8 @@ class md_params(C.Structure):
                 ("precision", C.c_int32), ("neigh_capacity", C.c_int32),
                 ("sample_interval", C.c_int32), ("obs_capacity", C.c_int32),
                 ("threads_per_particle", C.c_int32), ("use_graph", C.c_int32),
-                ("reorder", C.c_int32), ("reserved", C.c_int32 * 7)]
+                ("reorder", C.c_int32), ("reserved0", C.c_int32), ("smooth_h", C.c_double),
+                ("reserved", C.c_int32 * 4)]
 
 
 class md_obs(C.Structure):
@@ -262,6 +263,7 @@ def make_params(pot: dict, dt: float, skin: float = 0.3, precision: int = MD_PRE
             p.sigma[a][b] = float(pot["sigma"][a][b])
             p.rcut[a][b] = float(pot["rcut"][a][b])
         p.mass[a] = float(pot["mass"][a])
+    p.smooth_h = float(pot.get("smooth", 0.0))
     p.dt = float(dt)
     p.skin = float(skin)
     p.precision = int(precision)

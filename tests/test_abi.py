@@ -57,7 +57,7 @@ def test_workspace_size_grows_with_n_and_precision(md):
     assert b > 65536 * 128 * 4
 
 
-@pytest.mark.parametrize("bad", ["box", "dt", "species", "tpp", "sample", "asym"])
+@pytest.mark.parametrize("bad", ["box", "dt", "species", "tpp", "sample", "asym", "smooth", "smooth_tpp"])
 def test_argument_checks(md, bad):
     from paper_0912_3824_gb300 import synth
     pot = synth.ka_params()
@@ -76,6 +76,11 @@ def test_argument_checks(md, bad):
         p.sample_interval = 0
     if bad == "asym":
         p.eps[0][1] = 2.0
+    if bad == "smooth":
+        p.smooth_h = -0.005
+    if bad == "smooth_tpp":              # smoothed kernels exist for 1..8 lanes per particle
+        p.smooth_h = 0.005
+        p.threads_per_particle = 16
     with pytest.raises(md.MDError) as ei:
         md.md_workspace_size(p, [1000], [box])
     assert ei.value.code == md.MD_E_INVAL
@@ -88,3 +93,28 @@ def test_status_strings(md):
 
 def test_obs_record_layout(md):
     assert md.OBS_DTYPE.itemsize == 120
+
+
+def test_params_layout_and_smoothing_field(md):
+    """md_params keeps its 192-byte layout; the smoothing width travels from the
+    potential dictionary into smooth_h."""
+    import ctypes
+    from paper_0912_3824_gb300 import synth
+    assert ctypes.sizeof(md.md_params) == 192
+    assert md.md_params.smooth_h.offset == 168
+    assert md.make_params(synth.lj_params(smooth=0.005), 0.001).smooth_h == 0.005
+    assert md.make_params(synth.wca_params(), 0.001).rcut[0][0] == synth.WCA_RCUT
+
+
+def test_noalloc_rejects_smoothing_before_touching_the_device(md):
+    """The fixed-scratch entry point evaluates the plain potential only; the
+    rejection happens in argument checking, before any CUDA call."""
+    import ctypes
+    from paper_0912_3824_gb300 import synth
+    p = md.make_params(synth.lj_params(smooth=0.005), 0.001)
+    buf = (ctypes.c_double * 64)()
+    sp = (ctypes.c_int32 * 8)()
+    addr = ctypes.addressof(buf)
+    rc = md._lib.md_forces_noalloc(ctypes.byref(p), 8, ctypes.c_double(20.0), ctypes.addressof(sp), addr, addr,
+                                   addr, addr, None)
+    assert rc == md.MD_E_INVAL

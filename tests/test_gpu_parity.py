@@ -74,6 +74,50 @@ def test_forces_energy_virial_match_oracle(md, prec, kind, n):
     sim.close()
 
 
+def _melted(pot, n, density, temperature, seed=3, steps=300, dt=0.002):
+    """fcc start melted by 300 oracle steps: a liquid configuration."""
+    s = synth.make_system(n, density, temperature, seed, pot)
+    s.pos, s.vel, s.image, _, _ = oracle.vv_run(s.params, s.box, s.species, s.pos, s.vel, s.image, dt, steps)
+    return s
+
+
+SMOOTH_CASES = [("lj", 0.005), ("ka", 0.005), ("wca", 0.005), ("wca", 0.0)]
+
+
+def _smooth_system(kind, h):
+    if kind == "lj":
+        return _melted(synth.lj_params(smooth=h), 864, 0.8442, 1.0)
+    if kind == "wca":                     # the state point of Sec. 4
+        return _melted(synth.wca_params(smooth=h), 1000, 0.75, 1.12)
+    return _melted(synth.ka_params(smooth=h), 1000, 1.2, 1.0)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "fp32"])
+@pytest.mark.parametrize("kind,h", SMOOTH_CASES)
+def test_smoothed_and_wca_forces_match_oracle(md, prec, kind, h):
+    """Sec. 4 potentials: the C^2-smoothed LJ, KA and WCA pair sums and the plain
+    WCA potential against the oracle."""
+    s = _smooth_system(kind, h)
+    sim = _sim(md, s, prec)
+    f, e, tot = sim.forces()
+    fr, er, w7 = oracle.forces_cells(s.params, s.box, s.species, _ref_pos(s, prec))
+    assert _ferr(f, fr) <= TOL_F[prec]
+    assert abs(tot["e_pot"][0] - er.sum()) <= TOL_E[prec] * abs(er.sum())
+    assert np.abs(e - er).max() <= TOL_F[prec] * np.sqrt((er ** 2).mean())
+    assert abs(tot["virial"][0] - w7[0]) <= 10 * TOL_E[prec] * abs(w7[0]) + 1e-9
+    sim.close()
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-9), ("mixed", 1e-5)])
+def test_smoothed_wca_trajectory_matches_oracle(md, prec, tol):
+    s = _smooth_system("wca", 0.005)
+    pos, vel, img, obs, info = _trajectory(md, s, prec, 0.002, 200, 20)
+    rp, rv, ri, _, rec = oracle.vv_run(s.params, s.box, s.species, s.pos, s.vel, s.image, 0.002, 200, sample=20)
+    assert info["rebuilds"] >= 2
+    assert np.abs((pos + img * s.box) - (rp + ri * s.box)).max() < tol
+    assert np.allclose(obs["e_pot"], rec["e_pot"], rtol=1e-11 if prec == "fp64" else 1e-5)
+
+
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_melted_liquid_forces(md, prec):
     """A configuration taken from an oracle trajectory (fcc melted for 300 steps)."""

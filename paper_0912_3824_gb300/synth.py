@@ -197,3 +197,20 @@ def ensemble_sizes(n_replicas: int = 256, lo: int = 500, hi: int = 8000,
     st = Stream(seed)
     u = st.uniform(n_replicas)
     return [int(lo + math.floor(x * (hi - lo + 1))) for x in u]
+
+
+def shell_wavevectors(box: float, q: float, count: int = 16, seed: int = 9) -> np.ndarray:
+    """`count` wavevectors of the box's reciprocal lattice (2 pi / L) Z^3 whose
+    length is within half a lattice spacing of q, chosen by a seeded uniform
+    permutation of the whole shell (so that orientations are sampled evenly).
+    Returns float64 [count, 3]."""
+    dq = 2.0 * math.pi / box
+    nmax = int(math.ceil(q / dq + 1))
+    r = np.arange(-nmax, nmax + 1)
+    n = np.stack(np.meshgrid(r, r, r, indexing="ij"), axis=-1).reshape(-1, 3)
+    norm = np.sqrt((n * n).sum(axis=1)) * dq
+    shell = n[np.abs(norm - q) <= 0.5 * dq]
+    if shell.shape[0] == 0:
+        raise ValueError("no wavevector of the box near q")
+    pick = Stream(seed).permutation(shell.shape[0])[:count]
+    return shell[np.sort(pick)].astype(np.float64) * dq

@@ -51,10 +51,11 @@ def parse_args(argv=None):
     ap.add_argument("--no-graph", action="store_true",
                     help="plain stream launches instead of the CUDA graph (for per-kernel profiling)")
     ap.add_argument("--tpp", type=int, default=0, help="force-kernel threads per particle (0 = auto)")
-    ap.add_argument("--workload", choices=["ka65536", "lj-sweep", "replicas", "drift", "stability"],
+    ap.add_argument("--workload", choices=["ka65536", "lj-sweep", "e1", "replicas", "drift", "stability"],
                     default="ka65536",
                     help="ka65536: the headline line; the others print one line per case")
-    ap.add_argument("--sizes", type=int, nargs="*", default=None, help="lj-sweep particle counts")
+    ap.add_argument("--sizes", type=int, nargs="*", default=None, help="lj-sweep / e1 particle counts")
+    ap.add_argument("--densities", type=float, nargs="*", default=None, help="e1 number densities")
     ap.add_argument("--md-steps", type=int, default=100000, help="drift: NVE MD steps per run")
     ap.add_argument("--cases", nargs="*", default=None, help="drift: subset of cases")
     return ap.parse_args(argv)
@@ -424,13 +425,26 @@ def unwrapped(pos, img, box):
 def run_lj_sweep(args, local):
     """LJ fluid at rho = 0.8442, T = 1.0, dt = 0.005, skin 0.3, in the chosen
     precision, N from 4096 to 1048576: throughput against system size."""
+    cases = [(n, 0.8442) for n in (args.sizes or [4096, 32768, 262144, 1048576])]
+    return lj_cases(args, local, cases, "lj-sweep", temperature=1.0, dt=0.005, skin=0.3)
+
+
+def run_e1(args, local):
+    """The performance measurements of Sec. 3: LJ (r_c = 2.5) at T = 1.5,
+    dt = 0.001, skin 0.5, N = 1372 ... 864000 (4 n^3) and densities 0.2 ... 1.2."""
+    cases = [(n, rho) for rho in (args.densities or [0.2, 0.4, 0.8, 1.2])
+             for n in (args.sizes or [1372, 10976, 87808, 864000])]
+    return lj_cases(args, local, cases, "e1", temperature=1.5, dt=0.001, skin=0.5)
+
+
+def lj_cases(args, local, cases, workload, temperature, dt, skin):
     torch, md, synth, device, stream, flush = _gpu_setup(local)
     lines = []
-    for n in args.sizes or [4096, 32768, 262144, 1048576]:
-        s = synth.lj_fluid(n=n, density=0.8442, temperature=1.0, seed=3)
-        sim = md.System.from_synth(s, dt=0.005, precision=md.PRECISIONS[args.precision],
+    for n, rho in cases:
+        s = synth.lj_fluid(n=n, density=rho, temperature=temperature, seed=3)
+        sim = md.System.from_synth(s, dt=dt, skin=skin, precision=md.PRECISIONS[args.precision],
                                    sample_interval=100, device=device, threads_per_particle=args.tpp)
-        equilibrate(sim, 1.5, 1.0, melt_blocks=5, final_blocks=5)
+        equilibrate(sim, max(1.5, temperature), temperature, melt_blocks=5, final_blocks=5)
         sim.step(args.inner)                       # warm-up, graph captured
         assert sim.sync() == md.MD_OK
         sim.observables()
@@ -445,8 +459,10 @@ def run_lj_sweep(args, local):
         t_step = ms * 1e-3 / (args.inner * args.steps)
         flops = (FLOP_PER_ENTRY * n_list + FLOP_PER_PAIR * n_cut + FLOP_PER_UPDATE) * n
         hbm = n * (4 * n_list + 52 + 192)
-        line = {"workload": "lj-sweep", "config": f"LJ rho=0.8442 T=1.0 dt=0.005 r_c=2.5 shifted skin 0.3, N={n}",
-                "precision": args.precision, "n": n, "value": n / t_step, "unit": UNIT,
+        line = {"workload": workload,
+                "config": f"LJ rho={rho} T={temperature} dt={dt} r_c=2.5 shifted skin {skin}, N={n}",
+                "precision": args.precision, "n": n, "density": rho, "value": n / t_step, "unit": UNIT,
+                "ns_per_particle_step": t_step / n * 1e9,
                 "us_per_md_step": t_step * 1e6, "md_steps": args.inner * args.steps,
                 "rebuilds": int(info1["rebuilds"] - info0["rebuilds"]), "status": md._status_name(status),
                 "mean_list": float(n_list), "mean_in_cutoff": float(n_cut),
@@ -455,7 +471,7 @@ def run_lj_sweep(args, local):
                 "hbm_algorithmic_gbs_whole_step": hbm / t_step / 1e9, "clocks": clk}
         if n <= 32768 and not args.no_extras:
             pos, vel, img = sim.get_state()
-            line["cpu_baseline"] = cpu_baseline(s, pos, vel, img, budget_s=5.0, dt=0.005)
+            line["cpu_baseline"] = cpu_baseline(s, pos, vel, img, budget_s=5.0, dt=dt)
         sim.close()
         lines.append(line)
     return lines
@@ -655,7 +671,7 @@ def main(argv=None):
     if args.workload != "ka65536":
         if args.impl == "reference" or world > 1:
             raise SystemExit("--workload other than ka65536 runs our path on one GPU only")
-        fn = {"lj-sweep": run_lj_sweep, "replicas": run_replicas, "drift": run_drift,
+        fn = {"lj-sweep": run_lj_sweep, "e1": run_e1, "replicas": run_replicas, "drift": run_drift,
               "stability": run_stability}[args.workload]
         for line in fn(args, local):
             print(json.dumps(line), flush=True)

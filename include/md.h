@@ -84,8 +84,9 @@ typedef struct {
     int32_t neigh_capacity;   /* list entries per particle; 0 = derived from the density        */
     int32_t sample_interval;  /* record observables every this many steps (>= 1)                */
     int32_t obs_capacity;     /* ring-buffer samples kept on the device (0 = 4096)              */
-    int32_t threads_per_particle; /* force-kernel lanes per particle: 0 = automatic, else 1..32,
-                                     a power of two                                              */
+    int32_t threads_per_particle; /* force-kernel lanes per particle: 0 = automatic (2 for MIXED
+                                     and FP32, 4 for FP64), else a power of two in 1..32 (1..8
+                                     with smooth_h > 0)                                          */
     int32_t use_graph;        /* 1 = md_step runs as one CUDA graph with the rebuild branch and
                                  the step loop decided on the device (default); 0 = plain
                                  stream launches, for debugging and per-kernel timing          */
@@ -169,6 +170,22 @@ int md_rescale_velocities(md_handle *h, const double *T_target);
  * energy (may be NULL), and per-replica totals[n_replicas] (may be NULL;
  * e_pot, virial, w are the force-kernel reductions, e_kin and p those of the
  * current velocities).  Rebuilds the lists first.  Waits for the stream. */
+/* Andersen heat bath (Sec. 2.3): every particle of replica r receives a fresh
+ * Maxwell-Boltzmann velocity at T_target[r] (host array [n_replicas], >= 0);
+ * then the mass-weighted mean velocity of each replica is removed and its
+ * velocities are rescaled so that 2 E_kin / (3 N_r - 3) = T_target[r] exactly
+ * (all zero when N_r < 2 or T_target[r] = 0).  The random numbers are the
+ * rand48 sequence (x_{k+1} = 0x5DEECE66D x_k + 0xB mod 2^48, seeded as
+ * srand48(seed); deviate k = x_{k+1} / 2^48) shared out by leapfrogging:
+ * particle i (original index over all replicas, of n_total) uses deviates
+ * (4 event + j) n_total + i, j = 0..3, for three Box-Muller normals.  So a
+ * collision is reproducible from (seed, event) and independent of the
+ * particles' order in memory.  Call it every 1/(mu dt) steps with event =
+ * 0, 1, 2, ... for a heat-bath collision rate mu.  Asynchronous on the
+ * handle's stream.  MD_E_INVAL for a negative or non-finite target or a
+ * negative event index.                                                       */
+int md_andersen(md_handle *h, const double *T_target, uint64_t seed, int64_t event);
+
 int md_compute_forces(md_handle *h, double *f, double *e, md_obs *totals);
 
 /* Copy out the samples recorded since the previous call, oldest first, as
@@ -245,6 +262,54 @@ const char *md_status_string(int code);
 int md_forces_noalloc(const md_params *p, int64_t n, double box, const int32_t *species,
                       const double *pos, double *force, double *energy, double *totals,
                       void *cuda_stream);
+
+/* ---------------------------------------------------------------------------
+ * Time-correlation functions by the blocking scheme of Sec. 2.5.
+ *
+ * A correlator samples the state of one handle each time md_corr_sample is
+ * called (the caller advances the handle by a fixed number of MD steps, the
+ * sampling interval, between calls; sample index m = 0, 1, 2, ...).  Block n
+ * (n = 0 .. k-1) holds at most l samples spaced l^n samples apart (it takes
+ * the samples whose index is a multiple of l^n).  When a block becomes full
+ * its first entry is correlated with each of the other l - 1 entries (lags
+ * j l^n samples, j = 1 .. l-1) and then dropped.  Device memory: k l
+ * snapshots of the unwrapped positions (FP64, 24 bytes per particle each).
+ *
+ * Correlated quantities, per species (all replicas pooled, an ensemble
+ * average over independent systems), for a particle displacement d over the
+ * lag: the mean-square displacement |d|^2 and the self intermediate
+ * scattering function F_s = (1/n_q) sum_q cos(q . d) over the given
+ * wavevectors (Sec. 5: F_s(q, t) = <rho_q(t) rho_-q(0)>, orientation
+ * averaged; the paper uses |q| = 7.25 for the Kob-Andersen mixture).
+ * |d|^2 is summed in FP64; the cosine is evaluated in FP32.
+ * ------------------------------------------------------------------------- */
+typedef struct md_corr md_corr;
+
+/* Device workspace in bytes for a correlator over all particles of h:
+ * 1 <= k, 2 <= l <= 32, 1 <= n_q <= 64, l^k < 9e15.  Host-only. */
+int md_corr_workspace_size(const md_handle *h, int32_t k, int32_t l, int32_t n_q, size_t *bytes);
+
+/* Create a correlator on h.  q: host array [n_q][3] of wavevectors (copied).
+ * workspace: device memory, 256-byte aligned, caller-owned, at least
+ * md_corr_workspace_size bytes, outliving the correlator.  Destroy the
+ * correlator before its handle.  MD_E_INVAL / MD_E_NOMEM / MD_E_CUDA. */
+int md_corr_create(md_corr **c, md_handle *h, int32_t k, int32_t l, int32_t n_q, const double *q,
+                   void *workspace, size_t workspace_bytes);
+
+/* Take the handle's current state as the next sample; launches the snapshot
+ * and any correlation the insertion triggers, asynchronously on the handle's
+ * stream. */
+int md_corr_sample(md_corr *c);
+
+/* Results so far, each array (host) of k (l-1) entries in the order (block n,
+ * lag j): lags in samples (j l^n), number of time origins correlated, and per
+ * species (second index 0 = A, 1 = B; arrays of 2 k (l-1)) the mean-square
+ * displacement and F_s averaged over origins and particles; NaN where no
+ * origin has been correlated yet or the species is absent.  Any pointer may
+ * be NULL.  Synchronises the handle's stream. */
+int md_corr_result(md_corr *c, int64_t *lags, double *msd, double *fs, int64_t *origins);
+
+int md_corr_destroy(md_corr *c);
 
 #ifdef __cplusplus
 }

@@ -28,6 +28,7 @@
 
 #include "md.h"
 #include "md_common.cuh"
+#include "md_corr.cuh"
 
 static_assert(sizeof(md_params) == 192, "md_params layout is part of the ABI");
 
@@ -137,7 +138,9 @@ int make_geometry(const md_params *p, int R, const int64_t *nrep, const double *
     }
     g.R = R;
     g.rl_max = rcmax + p->skin + (double)mdk::kListMargin;
-    g.tpp = tpp ? tpp : 4;
+    // lanes per particle: 2 for the FP32 pair loops (4096 warps at KA N=65536 fit one wave at
+    // 64 registers), 4 for FP64 (measured on GB300)
+    g.tpp = tpp ? tpp : (p->precision == MD_PREC_FP64 ? 4 : 2);
     g.ppb_f = kForceBlock / g.tpp;
     g.n = 0;
     g.rep.assign(R, mdk::Rep{});
@@ -318,6 +321,7 @@ struct md_handle {
     double step_ms = 0.0, rebuild_ms = 0.0;
     int64_t step_launches = 0, rebuild_checks = 0;
     int64_t obs_read = 0;
+    int64_t n_species[2] = {0, 0};   // particles per species over all replicas
     std::string err;
 };
 
@@ -707,6 +711,14 @@ static int create_impl(md_handle *h, const md_params *p, const int32_t *species,
     for (int64_t i = 0; i < h->g.n; ++i)
         if (species[i] < 0 || species[i] >= p->n_species)
             return fail(h, MD_E_INVAL, "species out of range");
+    for (int64_t i = 0; i < h->g.n; ++i)
+        h->n_species[species[i]] += 1;
+    for (auto &q : h->g.rep) {
+        double m = 0.0;
+        for (int i = q.start; i < q.start + q.n; ++i)
+            m += p->mass[species[i]];
+        q.mtot = m;
+    }
     h->s = (cudaStream_t)cuda_stream;
     h->ws = (char *)workspace;
     h->ks = &kernel_set(p->precision);
@@ -933,6 +945,248 @@ int md_rescale_velocities(md_handle *h, const double *T_target)
     if ((rc = launch_integrate(h, mdk::IM_KE)))
         return rc;
     return launch(h, h->ks->scale, h->g.nblk_i, kIntBlock, h->a);
+}
+
+// Andersen heat bath (Sec. 2.3): one collision of every particle.
+int md_andersen(md_handle *h, const double *T_target, uint64_t seed, int64_t event)
+{
+    if (!h || !T_target)
+        return MD_E_INVAL;
+    if (event < 0)
+        return fail(h, MD_E_INVAL, "event index must be >= 0");
+    const unsigned long long n = (unsigned long long)h->g.n;
+    if ((unsigned long long)event > (~0ull >> 1) / 4 / (n + 1))
+        return fail(h, MD_E_INVAL, "event index too large");
+    int rc;
+    for (int r = 0; r < h->g.R; ++r)
+        if (!(T_target[r] >= 0.0) || !std::isfinite(T_target[r]))
+            return fail(h, MD_E_INVAL, "target temperatures must be finite and >= 0");
+    if ((rc = stage_wait(h)))
+        return rc;
+    memcpy(h->pin, T_target, 8 * (size_t)h->g.R);
+    CK(h, cudaMemcpyAsync(h->a.scale, h->pin, 8 * (size_t)h->g.R, cudaMemcpyHostToDevice, h->s));
+    CK(h, cudaEventRecord(h->ev_stage, h->s));
+    // rand48 (a = 0x5DEECE66D, c = 0xB, modulo 2^48), seeded as srand48; leapfrog over n threads
+    const unsigned long long A = 0x5DEECE66DULL, Cc = 0xBULL, mask = 0xFFFFFFFFFFFFULL;
+    unsigned long long AN = 1, CN = 0, Ab = A, Cb = Cc;
+    for (unsigned long long p = n; p; p >>= 1) {
+        if (p & 1ull) {
+            AN = (Ab * AN) & mask;
+            CN = (Ab * CN + Cb) & mask;
+        }
+        Cb = (Ab * Cb + Cb) & mask;
+        Ab = (Ab * Ab) & mask;
+    }
+    mdk::KArgs a = h->a;
+    a.r48_x0 = ((seed & 0xFFFFFFFFull) << 16) | 0x330Eull;
+    a.r48_AN = AN;
+    a.r48_CN = CN;
+    a.r48_base = (long long)(4ull * (unsigned long long)event * n);
+    if ((rc = launch(h, h->ks->andersen, h->g.nblk_i, kIntBlock, a)) ||
+        (rc = launch_integrate(h, mdk::IM_TOTALS)))
+        return rc;
+    return launch(h, h->ks->andersen_fix, h->g.nblk_i, kIntBlock, h->a);
+}
+
+// ---------------------------------------------------------------------------
+// Blocking scheme for time-correlation functions (Sec. 2.5).  Block n holds at
+// most l samples spaced l^n samples apart; when it is full its first entry is
+// correlated with the others and dropped.  Snapshots live in a pool of k l
+// slots shared by the blocks (a sample that enters several blocks is stored
+// once); the host keeps the bookkeeping, the device the data and the sums.
+// ---------------------------------------------------------------------------
+struct md_corr {
+    md_handle *h = nullptr;
+    int k = 0, l = 0, nq = 0, nblocks = 0;
+    int64_t m = 0;                            // samples taken
+    double *pool = nullptr;                   // [k l][n][3]
+    int *species = nullptr;                   // [n]
+    double *q = nullptr;                      // [nq][3]
+    double *part = nullptr;                   // [nblocks][l-1][4]
+    double *acc = nullptr;                    // [k][l-1][4]
+    std::vector<std::vector<int>> blocks;     // slot ids, oldest first
+    std::vector<int> refs;                    // blocks referring to each slot
+    std::vector<int64_t> origins;             // [k][l-1]
+};
+
+namespace {
+
+size_t corr_layout(int64_t n, int k, int l, int nq, size_t off[6])
+{
+    size_t o = 0;
+    auto take = [&](size_t bytes) { size_t r = o; o = align_up(o + std::max<size_t>(bytes, 1)); return r; };
+    const size_t nb = (size_t)((n + mdk::kCorrBlock - 1) / mdk::kCorrBlock);
+    off[0] = take(sizeof(double) * 3 * (size_t)n * (size_t)k * (size_t)l);
+    off[1] = take(sizeof(int) * (size_t)n);
+    off[2] = take(sizeof(double) * 3 * (size_t)nq);
+    off[3] = take(sizeof(double) * 4 * nb * (size_t)(l - 1));
+    off[4] = take(sizeof(double) * 4 * (size_t)k * (size_t)(l - 1));
+    off[5] = o;
+    return o;
+}
+
+int corr_check(const md_handle *h, int k, int l, int nq)
+{
+    if (!h || k < 1 || l < 2 || l - 1 > mdk::kCorrMaxJ || nq < 1 || nq > mdk::kCorrMaxQ)
+        return MD_E_INVAL;
+    double span = 1.0;                         // l^k must stay a valid sample index
+    for (int n = 0; n < k; ++n)
+        span *= l;
+    return span < 9e15 ? MD_OK : MD_E_INVAL;
+}
+
+}  // namespace
+
+int md_corr_workspace_size(const md_handle *h, int32_t k, int32_t l, int32_t n_q, size_t *bytes)
+{
+    if (!bytes || corr_check(h, k, l, n_q))
+        return MD_E_INVAL;
+    size_t off[6];
+    *bytes = corr_layout(h->g.n, k, l, n_q, off);
+    return MD_OK;
+}
+
+int md_corr_create(md_corr **out, md_handle *h, int32_t k, int32_t l, int32_t n_q, const double *q,
+                   void *workspace, size_t workspace_bytes)
+{
+    if (!out || !q || corr_check(h, k, l, n_q))
+        return h ? fail(h, MD_E_INVAL, "md_corr_create: bad arguments (1 <= k, 2 <= l <= 32, "
+                                       "1 <= n_q <= 64, non-null q)") : MD_E_INVAL;
+    *out = nullptr;
+    size_t off[6];
+    const size_t need = corr_layout(h->g.n, k, l, n_q, off);
+    if (!workspace || ((uintptr_t)workspace % kAlign) != 0)
+        return fail(h, MD_E_INVAL, "md_corr_create: workspace missing or not 256-byte aligned");
+    if (workspace_bytes < need)
+        return fail(h, MD_E_NOMEM, "md_corr_create: workspace smaller than md_corr_workspace_size()");
+    for (int t = 0; t < 3 * n_q; ++t)
+        if (!std::isfinite(q[t]))
+            return fail(h, MD_E_INVAL, "md_corr_create: non-finite wavevector");
+    md_corr *c = new (std::nothrow) md_corr;
+    if (!c)
+        return fail(h, MD_E_NOMEM, "md_corr_create: host allocation failed");
+    char *w = (char *)workspace;
+    c->h = h;
+    c->k = k;
+    c->l = l;
+    c->nq = n_q;
+    c->nblocks = (int)((h->g.n + mdk::kCorrBlock - 1) / mdk::kCorrBlock);
+    c->pool = (double *)(w + off[0]);
+    c->species = (int *)(w + off[1]);
+    c->q = (double *)(w + off[2]);
+    c->part = (double *)(w + off[3]);
+    c->acc = (double *)(w + off[4]);
+    c->blocks.assign(k, std::vector<int>());
+    c->refs.assign((size_t)k * l, 0);
+    c->origins.assign((size_t)k * (l - 1), 0);
+    int rc;
+    if ((rc = stage_wait(h)) || (rc = ensure_pinned(h, sizeof(double) * 3 * n_q))) {
+        delete c;
+        return rc;
+    }
+    memcpy(h->pin, q, sizeof(double) * 3 * n_q);
+    cudaError_t e = cudaMemcpyAsync(c->q, h->pin, sizeof(double) * 3 * n_q, cudaMemcpyHostToDevice, h->s);
+    if (e == cudaSuccess)
+        e = cudaEventRecord(h->ev_stage, h->s);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(c->acc, 0, sizeof(double) * 4 * (size_t)k * (l - 1), h->s);
+    if (e != cudaSuccess) {
+        delete c;
+        return cuda_fail(h, e, "md_corr_create");
+    }
+    *out = c;
+    return MD_OK;
+}
+
+int md_corr_sample(md_corr *c)
+{
+    if (!c)
+        return MD_E_INVAL;
+    md_handle *h = c->h;
+    int slot = -1;
+    for (size_t s = 0; s < c->refs.size(); ++s)
+        if (c->refs[s] == 0) {
+            slot = (int)s;
+            break;
+        }
+    if (slot < 0)
+        return fail(h, MD_E_INVAL, "md_corr_sample: no free snapshot slot");   // cannot happen: k l slots
+    const size_t n = (size_t)h->g.n;
+    mdk::KArgs a = h->a;
+    a.snap = c->pool + 3 * n * (size_t)slot;
+    a.snap_species = c->species;
+    int rc;
+    if ((rc = launch(h, h->ks->snapshot, h->g.nblk_i, kIntBlock, a)))
+        return rc;
+    int64_t spacing = 1;
+    for (int b = 0; b < c->k; ++b, spacing *= c->l) {
+        if (c->m % spacing)
+            break;
+        std::vector<int> &blk = c->blocks[b];
+        blk.push_back(slot);
+        c->refs[slot] += 1;
+        if ((int)blk.size() < c->l)
+            continue;
+        mdk::CorrArgs ca;
+        ca.s0 = c->pool + 3 * n * (size_t)blk[0];
+        for (int j = 1; j < c->l; ++j)
+            ca.sj[j - 1] = c->pool + 3 * n * (size_t)blk[j];
+        for (int j = c->l; j <= mdk::kCorrMaxJ; ++j)
+            ca.sj[j - 1] = nullptr;
+        ca.nj = c->l - 1;
+        ca.n = (int)n;
+        ca.nq = c->nq;
+        ca.species = c->species;
+        ca.q = c->q;
+        ca.part = c->part;
+        ca.acc = c->acc + (size_t)b * (c->l - 1) * 4;
+        ca.nblocks = c->nblocks;
+        mdk::k_corr<<<c->nblocks, mdk::kCorrBlock, 0, h->s>>>(ca);
+        mdk::k_corr_reduce<<<1, 128, 0, h->s>>>(ca);
+        CK(h, cudaGetLastError());
+        for (int j = 0; j < c->l - 1; ++j)
+            c->origins[(size_t)b * (c->l - 1) + j] += 1;
+        c->refs[blk[0]] -= 1;
+        blk.erase(blk.begin());
+    }
+    c->m += 1;
+    return MD_OK;
+}
+
+int md_corr_result(md_corr *c, int64_t *lags, double *msd, double *fs, int64_t *origins)
+{
+    if (!c)
+        return MD_E_INVAL;
+    md_handle *h = c->h;
+    const size_t nl = (size_t)c->k * (c->l - 1);
+    std::vector<double> acc(4 * nl);
+    CK(h, cudaStreamSynchronize(h->s));
+    CK(h, cudaMemcpy(acc.data(), c->acc, sizeof(double) * 4 * nl, cudaMemcpyDeviceToHost));
+    int64_t spacing = 1;
+    for (int b = 0; b < c->k; ++b, spacing *= c->l)
+        for (int j = 1; j < c->l; ++j) {
+            const size_t t = (size_t)b * (c->l - 1) + (j - 1);
+            const int64_t no = c->origins[t];
+            if (lags)
+                lags[t] = (int64_t)j * spacing;
+            if (origins)
+                origins[t] = no;
+            for (int a = 0; a < 2; ++a) {
+                const double cnt = (double)no * (double)h->n_species[a];
+                const double nan = std::nan("");
+                if (msd)
+                    msd[2 * t + a] = cnt > 0 ? acc[4 * t + 2 * a] / cnt : nan;
+                if (fs)
+                    fs[2 * t + a] = cnt > 0 ? acc[4 * t + 2 * a + 1] / cnt : nan;
+            }
+        }
+    return MD_OK;
+}
+
+int md_corr_destroy(md_corr *c)
+{
+    delete c;
+    return MD_OK;
 }
 
 int md_compute_forces(md_handle *h, double *f, double *e, md_obs *totals)

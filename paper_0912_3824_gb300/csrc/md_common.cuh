@@ -59,6 +59,7 @@ struct Rep {                  // one independent system
     float grid, inv_grid;     // anchoring grid of MIXED positions (powers of two)
     float qunit;              // L / 2^32: length of one unit of the fixed-point positions
     float pad;
+    double mtot;              // total mass of the replica
 };
 
 struct PairTab {              // [a*2+b]
@@ -102,6 +103,11 @@ struct KArgs {
     double *st_pos, *st_vel, *st_f, *st_e;   // staging, original order
     int *st_img, *st_code;
     double *scale;                    // [nrep] targets in, factors out (rescale)
+    unsigned long long r48_x0;        // Andersen heat bath (Sec. 2.3): rand48 state after seeding,
+    unsigned long long r48_AN, r48_CN;//   leapfrog multiplier / addend over n threads,
+    long long r48_base;               //   first deviate index of the collision (4 * event * n)
+    double *snap;                     // time-correlation snapshot: unwrapped positions [n][3] and
+    int *snap_species;                //   species, both by original particle index
     PairTab tab;
     double hdtm[2], dt, mass[2];      // dt / (2 m_a), dt, m_a
     long long nsteps;                 // for k_set_steps
@@ -169,6 +175,7 @@ struct KernelSet {
     const void *integrate, *force[2][6], *step[2][6];   // [smoothed][log2 lanes per particle]
     const void *bin, *scan, *scatter, *permute, *nbuild, *flip;
     const void *load, *getstate, *expforce, *scale, *set_steps, *reset, *mark_rebuild;
+    const void *andersen, *andersen_fix, *snapshot;
 };
 
 const KernelSet &kernels_fp64();

@@ -38,6 +38,7 @@ constexpr int kScanBlock = 1024;
 constexpr int kPartF = 12;       // doubles per block partial of the force / step kernels
 constexpr int kUnr = 4;          // list entries per lane and iteration of the FP32 pair loops
                                  // (a multiple of 4, at most 8: lists are padded to 8)
+constexpr bool kPrefetch = true; // load the next iteration's list indices ahead
 
 // ---------------------------------------------------------------------------
 // small helpers
@@ -634,16 +635,28 @@ __device__ __forceinline__ void pair_forces(const KArgs &a, const Rep &rp, int p
         }
         float sx = 0.f, sy = 0.f, sz = 0.f, cx = 0.f, cy = 0.f, cz = 0.f;
         float en = 0.f, vir = 0.f, wxx = 0.f, wyy = 0.f, wzz = 0.f, wxy = 0.f, wxz = 0.f, wyz = 0.f;
+        // list indices of the next iteration are loaded one iteration ahead, so
+        // that only the position gathers remain on each iteration's critical path
+        // (K is a multiple of 8: every 16-byte index load is in bounds and aligned)
+        int4 qn[kUnr / 4];
+        if (kPrefetch)
+#pragma unroll
+            for (int w = 0; w < kUnr / 4; ++w)
+                qn[w] = kUnr * lane < nn ? __ldg((const int4 *)(lst + kUnr * lane + 4 * w)) : make_int4(0, 0, 0, 0);
         for (int k0 = kUnr * lane; k0 < nn; k0 += kUnr * TPP) {
             int jj[kUnr];
 #pragma unroll
-            for (int w = 0; w < kUnr / 4; ++w) {   // K is a multiple of 8: in bounds, aligned
-                const int4 q = __ldg((const int4 *)(lst + k0 + 4 * w));
+            for (int w = 0; w < kUnr / 4; ++w) {
+                const int4 q = kPrefetch ? qn[w] : __ldg((const int4 *)(lst + k0 + 4 * w));
                 jj[4 * w] = q.x;
                 jj[4 * w + 1] = q.y;
                 jj[4 * w + 2] = q.z;
                 jj[4 * w + 3] = q.w;
             }
+            if (kPrefetch && k0 + kUnr * TPP < nn)
+#pragma unroll
+                for (int w = 0; w < kUnr / 4; ++w)
+                    qn[w] = __ldg((const int4 *)(lst + k0 + kUnr * TPP + 4 * w));
             float4 Hs[kUnr];
             int4 Qs[kUnr];
 #pragma unroll
@@ -1909,6 +1922,154 @@ __global__ void k_reset(KArgs a)
     a.ctl->n_other += 1;
 }
 
+// ---------------------------------------------------------------------------
+// Andersen heat bath (Sec. 2.3): every particle draws a Maxwell-Boltzmann
+// velocity from the rand48 sequence (x_{n+1} = a x_n + c mod 2^48; deviate n is
+// x_{n+1} / 2^48).  Particle i (original index) is thread i of a leapfrog over
+// the n particles: collision e uses its deviates (4e + k) n + i, k = 0..3.
+// The first is reached by jumping ahead (the affine map raised to a power by
+// squaring, exact in 64-bit integer arithmetic modulo 2^48), the others by the
+// leapfrog x -> A_n x + C_n.  Box-Muller turns them into three normals; then
+// k_andersen_fix removes the mean velocity and rescales to the target
+// temperature exactly, per replica, from the FP64 totals.
+// ---------------------------------------------------------------------------
+constexpr unsigned long long kR48A = 0x5DEECE66DULL, kR48C = 0xBULL, kR48Mask = 0xFFFFFFFFFFFFULL;
+
+__device__ __forceinline__ unsigned long long r48_jump(unsigned long long x, unsigned long long p)
+{
+    unsigned long long A = 1, C = 0, Ab = kR48A, Cb = kR48C;   // result map, map^(2^k)
+    while (p) {
+        if (p & 1ull) {
+            A = (Ab * A) & kR48Mask;
+            C = (Ab * C + Cb) & kR48Mask;
+        }
+        Cb = (Ab * Cb + Cb) & kR48Mask;
+        Ab = (Ab * Ab) & kR48Mask;
+        p >>= 1;
+    }
+    return (A * x + C) & kR48Mask;
+}
+
+template <int P>
+__global__ void __launch_bounds__(kIntBlock) k_andersen(KArgs a)
+{
+    const Ctl *ctl = a.ctl;
+    if (ctl->status)
+        return;
+    const int4 b = a.blk_i[blockIdx.x];
+    const int i = b.x + threadIdx.x;
+    if (i >= b.y)
+        return;
+    const int spar = ctl->state_par;
+    const int orig = img_of(a, spar)[i].w;
+    int sp;
+    if constexpr (P == FP64)
+        sp = species_of(((const d4 *)pos_a(a, ctl->pos_par))[i].w);
+    else
+        sp = species_of(((const float4 *)pos_a(a, ctl->pos_par))[i].w);
+    unsigned long long x = r48_jump(a.r48_x0, (unsigned long long)a.r48_base + (unsigned long long)orig + 1ull);
+    double u[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        u[k] = (double)x * 0x1p-48;
+        x = (a.r48_AN * x + a.r48_CN) & kR48Mask;
+    }
+    const double s = sqrt(a.scale[b.z] / a.mass[sp]);
+    const double r1 = s * sqrt(-2.0 * log(1.0 - u[0])), r2 = s * sqrt(-2.0 * log(1.0 - u[2]));
+    double s1, c1, s3, c3;
+    sincospi(2.0 * u[1], &s1, &c1);
+    sincospi(2.0 * u[3], &s3, &c3);
+    const double v[3] = {r1 * c1, r1 * s1, r2 * c3};
+    if constexpr (P == FP64) {
+        d4 w;
+        w.x = v[0]; w.y = v[1]; w.z = v[2]; w.w = 0.0;
+        ((d4 *)vel_a(a, spar))[i] = w;
+    } else if constexpr (P == MIXED) {
+        const ds x0 = ds_from_double(v[0]), y0 = ds_from_double(v[1]), z0 = ds_from_double(v[2]);
+        ((float4 *)vel_a(a, spar))[i] = make_float4(x0.hi, y0.hi, z0.hi, 0.f);
+        ((float4 *)vel_b(a, spar))[i] = make_float4(x0.lo, y0.lo, z0.lo, 0.f);
+    } else {
+        ((float4 *)vel_a(a, spar))[i] = make_float4((float)v[0], (float)v[1], (float)v[2], 0.f);
+    }
+}
+
+// v <- (v - P/M) s with s = sqrt(T (3N - 3) / (2 E_kin')), E_kin' = E_kin - |P|^2 / 2M,
+// from the per-replica totals (E_kin, P) of the drawn velocities
+template <int P>
+__global__ void __launch_bounds__(kIntBlock) k_andersen_fix(KArgs a)
+{
+    const Ctl *ctl = a.ctl;
+    if (ctl->status)
+        return;
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        atomicAdd((unsigned long long *)&a.ctl->n_other, 1ull);
+    const int4 b = a.blk_i[blockIdx.x];
+    const int i = b.x + threadIdx.x;
+    if (i >= b.y)
+        return;
+    const Rep &rp = a.rep[b.z];
+    const Obs &t = a.totals[b.z];
+    const double M = rp.mtot;
+    const double cx = t.p[0] / M, cy = t.p[1] / M, cz = t.p[2] / M;
+    const double ek = t.e_kin - 0.5 * (t.p[0] * t.p[0] + t.p[1] * t.p[1] + t.p[2] * t.p[2]) / M;
+    const double T = a.scale[b.z];
+    const double f = (rp.n > 1 && T > 0.0 && ek > 0.0) ? sqrt(T * (3.0 * rp.n - 3.0) / (2.0 * ek)) : 0.0;
+    const int spar = ctl->state_par;
+    if constexpr (P == FP64) {
+        d4 v = ((d4 *)vel_a(a, spar))[i];
+        v.x = (v.x - cx) * f; v.y = (v.y - cy) * f; v.z = (v.z - cz) * f;
+        ((d4 *)vel_a(a, spar))[i] = v;
+    } else if constexpr (P == MIXED) {
+        const float4 vh = ((float4 *)vel_a(a, spar))[i], vl = ((float4 *)vel_b(a, spar))[i];
+        const ds x = ds_from_double((ds_to_double(ds_from(vh.x, vl.x)) - cx) * f);
+        const ds y = ds_from_double((ds_to_double(ds_from(vh.y, vl.y)) - cy) * f);
+        const ds z = ds_from_double((ds_to_double(ds_from(vh.z, vl.z)) - cz) * f);
+        ((float4 *)vel_a(a, spar))[i] = make_float4(x.hi, y.hi, z.hi, 0.f);
+        ((float4 *)vel_b(a, spar))[i] = make_float4(x.lo, y.lo, z.lo, 0.f);
+    } else {
+        float4 v = ((float4 *)vel_a(a, spar))[i];
+        v.x = (float)((v.x - cx) * f); v.y = (float)((v.y - cy) * f); v.z = (float)((v.z - cz) * f);
+        ((float4 *)vel_a(a, spar))[i] = v;
+    }
+}
+
+// Snapshot for the time-correlation functions (Sec. 2.5): unwrapped positions
+// r + L n (FP64) and species, stored by original particle index.
+template <int P>
+__global__ void __launch_bounds__(kIntBlock) k_snapshot(KArgs a)
+{
+    const Ctl *ctl = a.ctl;
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        atomicAdd((unsigned long long *)&a.ctl->n_other, 1ull);
+    const int4 b = a.blk_i[blockIdx.x];
+    const int i = b.x + threadIdx.x;
+    if (i >= b.y)
+        return;
+    const double L = a.rep[b.z].L;
+    const int pp = ctl->pos_par, spar = ctl->state_par;
+    const int4 im = img_of(a, spar)[i];
+    double x[3];
+    int sp;
+    if constexpr (P == FP64) {
+        const d4 p = ((const d4 *)pos_a(a, pp))[i];
+        x[0] = p.x; x[1] = p.y; x[2] = p.z;
+        sp = species_of(p.w);
+    } else if constexpr (P == MIXED) {
+        const float4 H = ((const float4 *)pos_a(a, pp))[i], l = ((const float4 *)pos_b(a, pp))[i];
+        x[0] = (double)H.x + (double)l.x; x[1] = (double)H.y + (double)l.y; x[2] = (double)H.z + (double)l.z;
+        sp = species_of(H.w);
+    } else {
+        const float4 p = ((const float4 *)pos_a(a, pp))[i];
+        x[0] = p.x; x[1] = p.y; x[2] = p.z;
+        sp = species_of(p.w);
+    }
+    const size_t t = (size_t)im.w;
+    a.snap[3 * t + 0] = __dadd_rn(x[0], __dmul_rn(L, (double)im.x));
+    a.snap[3 * t + 1] = __dadd_rn(x[1], __dmul_rn(L, (double)im.y));
+    a.snap[3 * t + 2] = __dadd_rn(x[2], __dmul_rn(L, (double)im.z));
+    a.snap_species[t] = sp;
+}
+
 // request a list rebuild before the next force evaluation
 template <int P>
 __global__ void k_mark_rebuild(KArgs a)
@@ -1960,6 +2121,9 @@ KernelSet make_kernel_set()
     k.set_steps = (const void *)k_set_steps<P>;
     k.reset = (const void *)k_reset<P>;
     k.mark_rebuild = (const void *)k_mark_rebuild<P>;
+    k.andersen = (const void *)k_andersen<P>;
+    k.andersen_fix = (const void *)k_andersen_fix<P>;
+    k.snapshot = (const void *)k_snapshot<P>;
     return k;
 }
 

@@ -81,6 +81,13 @@ def _load() -> C.CDLL:
                        C.c_void_p], C.c_int),
         "md_step": ([H, C.c_int64], C.c_int),
         "md_rescale_velocities": ([H, d], C.c_int),
+        "md_andersen": ([H, d, C.c_uint64, C.c_int64], C.c_int),
+        "md_corr_workspace_size": ([H, C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_size_t)], C.c_int),
+        "md_corr_create": ([C.POINTER(C.c_void_p), H, C.c_int32, C.c_int32, C.c_int32, d, C.c_void_p,
+                            C.c_size_t], C.c_int),
+        "md_corr_sample": ([C.c_void_p], C.c_int),
+        "md_corr_result": ([C.c_void_p, i64, d, d, i64], C.c_int),
+        "md_corr_destroy": ([C.c_void_p], C.c_int),
         "md_compute_forces": ([H, d, d, C.POINTER(md_obs)], C.c_int),
         "md_observables": ([H, C.POINTER(md_obs), C.c_int32, i32], C.c_int),
         "md_get_state": ([H, d, d, i32], C.c_int),
@@ -105,7 +112,9 @@ _lib = _load()
 EXPORTED = ("md_params_default", "md_workspace_size", "md_create", "md_step",
             "md_rescale_velocities", "md_compute_forces", "md_observables", "md_get_state",
             "md_set_state", "md_get_neighbours", "md_info", "md_sync", "md_destroy",
-            "md_last_error", "md_status_string", "md_forces_noalloc")
+            "md_last_error", "md_status_string", "md_forces_noalloc", "md_andersen",
+            "md_corr_workspace_size", "md_corr_create", "md_corr_sample", "md_corr_result",
+            "md_corr_destroy")
 MD_NOALLOC_MAX_N = 1048576
 
 
@@ -177,6 +186,11 @@ def md_step(h, nsteps: int):
 def md_rescale_velocities(h, T_target):
     t = np.ascontiguousarray(T_target, dtype=np.float64)
     _check(_lib.md_rescale_velocities(h, _dptr(t)), h)
+
+
+def md_andersen(h, T_target, seed: int, event: int):
+    t = np.ascontiguousarray(T_target, dtype=np.float64)
+    _check(_lib.md_andersen(h, _dptr(t), int(seed), int(event)), h)
 
 
 def md_compute_forces(h, n_total: int, n_replicas: int):
@@ -312,6 +326,11 @@ class System:
         t = np.broadcast_to(np.asarray(temperature, dtype=np.float64), (self.nrep,))
         md_rescale_velocities(self.h, t)
 
+    def andersen(self, temperature, seed: int, event: int):
+        """One Andersen heat-bath collision of every particle (Sec. 2.3)."""
+        t = np.broadcast_to(np.asarray(temperature, dtype=np.float64), (self.nrep,))
+        md_andersen(self.h, t, seed, event)
+
     def forces(self):
         return md_compute_forces(self.h, self.n, self.nrep)
 
@@ -338,6 +357,52 @@ class System:
         if getattr(self, "h", None):
             md_destroy(self.h)
             self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Correlator:
+    """Blocking-scheme time-correlation functions (Sec. 2.5) of one System:
+    k blocks of l entries, tagged-particle MSD and F_s over the wavevectors q
+    ([n_q, 3]); the workspace is a torch tensor on the system's device."""
+
+    def __init__(self, system: "System", k: int, l: int, q):
+        import torch
+        self.system = system
+        self.k, self.l = int(k), int(l)
+        self.q = np.ascontiguousarray(q, dtype=np.float64).reshape(-1, 3)
+        nb = C.c_size_t()
+        _check(_lib.md_corr_workspace_size(system.h, self.k, self.l, self.q.shape[0], C.byref(nb)), system.h)
+        self.workspace = torch.empty(nb.value + 256, dtype=torch.uint8, device=system.workspace.device)
+        ptr = (self.workspace.data_ptr() + 255) // 256 * 256
+        c = C.c_void_p()
+        _check(_lib.md_corr_create(C.byref(c), system.h, self.k, self.l, self.q.shape[0], _dptr(self.q),
+                                   ptr, nb.value), system.h)
+        self.c = c
+
+    def sample(self):
+        _check(_lib.md_corr_sample(self.c), self.system.h)
+
+    def result(self):
+        """lags [k, l-1] (samples), msd and fs [k, l-1, 2], origins [k, l-1]."""
+        m = self.k * (self.l - 1)
+        lags = np.empty(m, dtype=np.int64)
+        org = np.empty(m, dtype=np.int64)
+        msd = np.empty(2 * m)
+        fs = np.empty(2 * m)
+        _check(_lib.md_corr_result(self.c, lags.ctypes.data_as(C.POINTER(C.c_int64)), _dptr(msd), _dptr(fs),
+                                   org.ctypes.data_as(C.POINTER(C.c_int64))), self.system.h)
+        sh = (self.k, self.l - 1)
+        return lags.reshape(sh), msd.reshape(sh + (2,)), fs.reshape(sh + (2,)), org.reshape(sh)
+
+    def close(self):
+        if getattr(self, "c", None):
+            _lib.md_corr_destroy(self.c)
+            self.c = None
 
     def __del__(self):
         try:

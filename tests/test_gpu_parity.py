@@ -278,6 +278,41 @@ def test_wrap_just_below_zero_keeps_unwrapped_position(md, prec):
     sim.close()
 
 
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("mixed", 1e-12), ("fp32", 2e-6)])
+def test_andersen_collision_matches_oracle(md, prec, tol):
+    """Sec. 2.3 heat bath: the velocities drawn on the device (rand48 jump-ahead
+    per particle) equal the oracle's sequential stream, whatever the particles'
+    order in memory (10 steps re-sort them first)."""
+    s = _system("ka", 3000)
+    sim = _sim(md, s, prec)
+    sim.step(10)
+    sim.andersen(0.8, 4242, 3)
+    _, vel, _ = sim.get_state()
+    ref = oracle.andersen(s.params, s.species, s.vel, 0.8, 4242, 3)
+    assert np.abs(vel - ref).max() <= tol * np.sqrt((ref ** 2).mean())
+    ek, mom = oracle.kinetic(s.params, s.species, vel)
+    assert 2 * ek / (3 * s.n - 3) == pytest.approx(0.8, rel=1e-12 if prec != "fp32" else 1e-6)
+    assert np.abs(mom).max() < (1e-10 if prec != "fp32" else 1e-3)
+    sim.close()
+
+
+def test_andersen_replicas_share_one_leapfrog(md):
+    """Two replicas in one handle: replica r's particles are the threads
+    start_r + i of one leapfrog over all particles; each gets its own target."""
+    p = synth.ka_params()
+    a = synth.ka_mixture(500, temperature=0.7, seed=21)
+    b = synth.ka_mixture(800, temperature=0.7, seed=22)
+    cat = lambda f: np.concatenate([getattr(a, f), getattr(b, f)])
+    sim = md.System(md.make_params(p, 0.001, precision=md.MD_PREC_FP64), [a.n, b.n], [a.box, b.box],
+                    cat("species"), cat("pos"), cat("vel"), cat("image"))
+    sim.andersen([0.5, 1.0], 99, 1)
+    _, vel, _ = sim.get_state()
+    ra = oracle.andersen(p, a.species, a.vel, 0.5, 99, 1, nthreads=1300, first_index=0)
+    rb = oracle.andersen(p, b.species, b.vel, 1.0, 99, 1, nthreads=1300, first_index=500)
+    assert np.abs(vel[:500] - ra).max() < 1e-12 and np.abs(vel[500:] - rb).max() < 1e-12
+    sim.close()
+
+
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_rescale_sets_temperature(md, prec):
     s = _system("ka", 2000)
@@ -367,4 +402,31 @@ def test_full_size_sampled_parity_ka65536(md):
     assert np.abs(f.sum(axis=0)).max() < 1e-3 * rms
     _, ec, _ = oracle.forces_cells(s.params, s.box, s.species, pos)
     assert abs(tot["e_pot"][0] - ec.sum()) <= TOL_E["mixed"] * abs(ec.sum())
+    sim.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_correlator_matches_blocking_oracle(md, prec):
+    """Sec. 2.5 blocking scheme on the device (snapshots, block bookkeeping,
+    MSD and F_s sums) against the oracle fed with the same unwrapped states."""
+    from oracle.correlation import BlockingCorrelator
+    s = _system("ka", 2000, amp=0.05, temperature=1.0)
+    sim = _sim(md, s, prec)
+    q = synth.shell_wavevectors(s.box, 7.25, count=12, seed=3)
+    corr = md.Correlator(sim, 3, 4, q)
+    ref = BlockingCorrelator(3, 4, s.species, q)
+    for _ in range(70):
+        corr.sample()
+        pos, _, img = sim.get_state()
+        ref.sample(pos + img * s.box)
+        sim.step(5)
+    lags, msd, fs, org = corr.result()
+    rl, rmsd, rfs, rorg = ref.result()
+    assert np.array_equal(lags, rl) and np.array_equal(org, rorg)
+    ok = org > 0
+    assert ok.sum() >= 6
+    assert np.allclose(msd[ok], rmsd[ok], rtol=1e-12, atol=0)
+    assert np.abs(fs[ok] - rfs[ok]).max() < 1e-5
+    assert np.isnan(msd[~ok]).all()
+    corr.close()
     sim.close()

@@ -38,7 +38,8 @@ constexpr int kScanBlock = 1024;
 constexpr int kPartF = 12;       // doubles per block partial of the force / step kernels
 constexpr int kUnr = 4;          // list entries per lane and iteration of the FP32 pair loops
                                  // (a multiple of 4, at most 8: lists are padded to 8)
-constexpr bool kPrefetch = true; // load the next iteration's list indices ahead
+constexpr int kPfDepth = 1;      // iterations ahead at which the list indices are loaded
+constexpr bool kSplitUpdate = false; // below 4 lanes: one lane updates (measured faster than sharing)
 
 // ---------------------------------------------------------------------------
 // small helpers
@@ -635,28 +636,37 @@ __device__ __forceinline__ void pair_forces(const KArgs &a, const Rep &rp, int p
         }
         float sx = 0.f, sy = 0.f, sz = 0.f, cx = 0.f, cy = 0.f, cz = 0.f;
         float en = 0.f, vir = 0.f, wxx = 0.f, wyy = 0.f, wzz = 0.f, wxy = 0.f, wxz = 0.f, wyz = 0.f;
-        // list indices of the next iteration are loaded one iteration ahead, so
-        // that only the position gathers remain on each iteration's critical path
+        // list indices are loaded kPfDepth iterations ahead, so that only the
+        // position gathers remain on each iteration's critical path
         // (K is a multiple of 8: every 16-byte index load is in bounds and aligned)
-        int4 qn[kUnr / 4];
-        if (kPrefetch)
+        constexpr int kStride = kUnr * TPP;
+        int4 pf[kPfDepth][kUnr / 4];
 #pragma unroll
-            for (int w = 0; w < kUnr / 4; ++w)
-                qn[w] = kUnr * lane < nn ? __ldg((const int4 *)(lst + kUnr * lane + 4 * w)) : make_int4(0, 0, 0, 0);
-        for (int k0 = kUnr * lane; k0 < nn; k0 += kUnr * TPP) {
+        for (int d = 0; d < kPfDepth; ++d)
+#pragma unroll
+            for (int w = 0; w < kUnr / 4; ++w) {
+                const int k = kUnr * lane + d * kStride;
+                pf[d][w] = k < nn ? __ldg((const int4 *)(lst + k + 4 * w)) : make_int4(0, 0, 0, 0);
+            }
+        for (int k0 = kUnr * lane; k0 < nn; k0 += kStride) {
             int jj[kUnr];
 #pragma unroll
             for (int w = 0; w < kUnr / 4; ++w) {
-                const int4 q = kPrefetch ? qn[w] : __ldg((const int4 *)(lst + k0 + 4 * w));
+                const int4 q = pf[0][w];
                 jj[4 * w] = q.x;
                 jj[4 * w + 1] = q.y;
                 jj[4 * w + 2] = q.z;
                 jj[4 * w + 3] = q.w;
             }
-            if (kPrefetch && k0 + kUnr * TPP < nn)
+#pragma unroll
+            for (int d = 0; d + 1 < kPfDepth; ++d)
 #pragma unroll
                 for (int w = 0; w < kUnr / 4; ++w)
-                    qn[w] = __ldg((const int4 *)(lst + k0 + kUnr * TPP + 4 * w));
+                    pf[d][w] = pf[d + 1][w];
+            if (k0 + kPfDepth * kStride < nn)
+#pragma unroll
+                for (int w = 0; w < kUnr / 4; ++w)
+                    pf[kPfDepth - 1][w] = __ldg((const int4 *)(lst + k0 + kPfDepth * kStride + 4 * w));
             float4 Hs[kUnr];
             int4 Qs[kUnr];
 #pragma unroll
@@ -1023,13 +1033,17 @@ __device__ __forceinline__ void component_update(const KArgs &a, const Rep &rp, 
     }
 }
 
-// Step body for groups of at least 4 lanes: lanes 0-2 own one component each
-// of the update, lane 3 copies the species word; the operands of the update
-// are loaded before the neighbour loop so their latency is hidden.
+// Step body: after the pair loop the lanes of a particle's group share its
+// update.  Lane l owns the components c = l*NC .. l*NC + NC - 1 (NC = 1 for 4
+// or more lanes, 4 / TPP below): c = 0..2 are the Cartesian components of the
+// double-single kick-drift-kick, c = 3 carries the species word to the new
+// position buffer.  The operands of the update are loaded before the
+// neighbour loop so that their latency is hidden.
 template <int P, int TPP, bool SAMPLE, bool SM>
 __device__ __forceinline__ void step_body_split(const KArgs &a, bool active, bool last, int pp, int spar,
                                                 double *part, float &d2, float &v2, float &a2, unsigned int &bad)
 {
+    constexpr int NC = TPP >= 4 ? 1 : 4 / TPP;
     const int4 b = a.blk_f[blockIdx.x];
     const Rep rp = a.rep[b.z];
     const int lane = threadIdx.x & (TPP - 1);
@@ -1037,19 +1051,23 @@ __device__ __forceinline__ void step_body_split(const KArgs &a, bool active, boo
     const bool valid = active && i < b.y;
     const int ii = (i < b.y) ? i : b.x;
     const int nn = valid ? a.nnbr[ii] : 0;
-    const int c = lane;
-    const size_t e = 4 * (size_t)ii + (c < 4 ? c : 0);
-    float vh = 0.f, vl = 0.f, rr = 0.f;
-    double vd = 0.0;
-    if (valid && c < 3) {
-        if constexpr (P == FP64) {
-            vd = ((const double *)vel_a(a, spar))[e];
-        } else {
-            vh = ((const float *)vel_a(a, spar))[e];
-            if constexpr (P == MIXED)
-                vl = ((const float *)vel_b(a, spar))[e];
+    float vh[NC], vl[NC], rr[NC];
+    double vd[NC];
+#pragma unroll
+    for (int u = 0; u < NC; ++u) {
+        const int c = lane * NC + u;
+        const size_t e = 4 * (size_t)ii + (c < 3 ? c : 0);
+        vh[u] = 0.f; vl[u] = 0.f; rr[u] = 0.f; vd[u] = 0.0;
+        if (valid && c < 3) {
+            if constexpr (P == FP64) {
+                vd[u] = ((const double *)vel_a(a, spar))[e];
+            } else {
+                vh[u] = ((const float *)vel_a(a, spar))[e];
+                if constexpr (P == MIXED)
+                    vl[u] = ((const float *)vel_b(a, spar))[e];
+            }
+            rr[u] = ((const float *)a.rref)[e];
         }
-        rr = ((const float *)a.rref)[e];
     }
     FT<P> fx = 0, fy = 0, fz = 0;
 #pragma unroll
@@ -1072,35 +1090,44 @@ __device__ __forceinline__ void step_body_split(const KArgs &a, bool active, boo
         store_force<P>(a, i, fx, fy, fz, SAMPLE ? part[0] : 0.0);
     double ke = 0.0, p3[3] = {0.0, 0.0, 0.0};
     float dd = 0.f, vv = 0.f;
-    if (!valid) {
-        // no update
-    } else if (c < 3) {
-        const FT<P> f_c = c == 0 ? fx : (c == 1 ? fy : fz);
-        double pc = 0.0;
-        component_update<P>(a, rp, pp, spar, i, c, sp, (float)f_c, (double)f_c, SAMPLE, last, vh, vl, vd, rr,
-                            ke, pc, dd, vv, bad);
-        p3[0] = c == 0 ? pc : 0.0;
-        p3[1] = c == 1 ? pc : 0.0;
-        p3[2] = c == 2 ? pc : 0.0;
-        if constexpr (P == FP64) {
-            ((double *)vel_a(a, spar))[e] = vd;
-        } else {
-            ((float *)vel_a(a, spar))[e] = vh;
-            if constexpr (P == MIXED)
-                ((float *)vel_b(a, spar))[e] = vl;
-        }
-    } else if (c == 3 && !last) {
-        // the species word travels with the position
-        if constexpr (P == FP64)
-            ((double *)pos_a(a, pp ^ 1))[4 * (size_t)i + 3] = ((const double *)pos_a(a, pp))[4 * (size_t)i + 3];
-        else
-            ((float *)pos_a(a, pp ^ 1))[4 * (size_t)i + 3] = ((const float *)pos_a(a, pp))[4 * (size_t)i + 3];
-        if constexpr (P == MIXED)
-            ((int *)q_of(a, pp ^ 1))[4 * (size_t)i + 3] = sp;
-    }
-    // combine the component lanes (the first four lanes of the group)
 #pragma unroll
-    for (int o = 2; o > 0; o >>= 1) {
+    for (int u = 0; u < NC; ++u) {
+        const int c = lane * NC + u;
+        if (!valid) {
+            // no update
+        } else if (c < 3) {
+            const size_t e = 4 * (size_t)i + c;
+            const FT<P> f_c = c == 0 ? fx : (c == 1 ? fy : fz);
+            double kc = 0.0, pc = 0.0;
+            float dc = 0.f, wc = 0.f;
+            component_update<P>(a, rp, pp, spar, i, c, sp, (float)f_c, (double)f_c, SAMPLE, last, vh[u], vl[u],
+                                vd[u], rr[u], kc, pc, dc, wc, bad);
+            ke += kc;
+            dd += dc;
+            vv += wc;
+            p3[0] += c == 0 ? pc : 0.0;
+            p3[1] += c == 1 ? pc : 0.0;
+            p3[2] += c == 2 ? pc : 0.0;
+            if constexpr (P == FP64) {
+                ((double *)vel_a(a, spar))[e] = vd[u];
+            } else {
+                ((float *)vel_a(a, spar))[e] = vh[u];
+                if constexpr (P == MIXED)
+                    ((float *)vel_b(a, spar))[e] = vl[u];
+            }
+        } else if (c == 3 && !last) {
+            // the species word travels with the position
+            if constexpr (P == FP64)
+                ((double *)pos_a(a, pp ^ 1))[4 * (size_t)i + 3] = ((const double *)pos_a(a, pp))[4 * (size_t)i + 3];
+            else
+                ((float *)pos_a(a, pp ^ 1))[4 * (size_t)i + 3] = ((const float *)pos_a(a, pp))[4 * (size_t)i + 3];
+            if constexpr (P == MIXED)
+                ((int *)q_of(a, pp ^ 1))[4 * (size_t)i + 3] = sp;
+        }
+    }
+    // combine the component lanes (the first min(TPP, 4) lanes of the group)
+#pragma unroll
+    for (int o = (TPP < 4 ? TPP : 4) / 2; o > 0; o >>= 1) {
         dd += __shfl_xor_sync(0xffffffffu, dd, o);
         vv += __shfl_xor_sync(0xffffffffu, vv, o);
         if (SAMPLE) {
@@ -1135,7 +1162,7 @@ template <int P, int TPP, bool SAMPLE, bool SM>
 __device__ __forceinline__ void step_body(const KArgs &a, bool active, bool last, int pp, int spar,
                                           double *part, float &d2, float &v2, float &a2, unsigned int &bad)
 {
-    if constexpr (TPP >= 4) {
+    if constexpr (kSplitUpdate || TPP >= 4) {
         step_body_split<P, TPP, SAMPLE, SM>(a, active, last, pp, spar, part, d2, v2, a2, bad);
         return;
     }
@@ -1543,29 +1570,78 @@ __global__ void __launch_bounds__(kIntBlock) k_permute(KArgs a)
 // particles of the 27 surrounding cells (all cells of the replica when fewer
 // than three fit along its edge) in shared memory, in a fixed order (stencil
 // order, then slot order inside a cell), dropping those farther than the
-// largest list radius from the cell's own box.  Each warp then takes one
-// particle of the cell at a time and keeps the staged particles closer than
-// r_c,ab + skin (plus a rounding margin), 32 candidates per ballot, writing
-// its row of the particle-major list nbr[i*K + k] in that order.  Distances
-// use the single-precision high words in every mode: the list only has to
-// contain every pair within r_c + skin, and the margin covers the rounding.
+// largest list radius from the cell's own box.  Each warp then takes
+// kNbPass particles of the cell at a time and keeps the staged particles
+// closer than r_c,ab + skin (plus a rounding margin), 32 candidates per
+// ballot, writing each particle's row of the particle-major list
+// nbr[i*K + k] in that order.  Distances
+// are single precision: from the fixed-point copy in MIXED mode, from the
+// (rounded) positions otherwise; the list only has to contain every pair
+// within r_c + skin, and the margin covers the rounding.
 // Reads the permuted positions (other buffer).  More candidates than fit in
 // shared memory, or more particles in the cell than one batch holds, are
 // processed in rounds, so no cell size is too large.
 // ---------------------------------------------------------------------------
 constexpr int kNbCap = 1024;     // staged candidates per round
 constexpr int kNbOwn = 256;      // own-cell particles per batch
+constexpr int kNbPass = 2;       // own-cell particles tested per warp pass over the candidates
+
+// Position word staged by the neighbour build: MIXED stages the fixed-point copy
+// (bits of X, Y, Z, species), whose wrapped differences give the exact minimum
+// image; the other modes the single-precision position and species bits.
+constexpr bool kNbFixed = true;
 
 template <int P>
-__device__ __forceinline__ float4 hi_pos(const KArgs &a, int pn, int j)
+__device__ __forceinline__ float4 nb_word(const KArgs &a, int pn, int j)
 {
-    if constexpr (P == FP64) {
+    if constexpr (P == MIXED && kNbFixed) {
+        const int4 q = q_of(a, pn)[j];
+        return make_float4(__int_as_float(q.x), __int_as_float(q.y), __int_as_float(q.z), __int_as_float(q.w));
+    } else if constexpr (P == FP64) {
         const d4 x = ((const d4 *)pos_a(a, pn))[j];
         return make_float4(__double2float_rn(x.x), __double2float_rn(x.y), __double2float_rn(x.z),
                            __int_as_float(species_of(x.w)));
     } else {
         return ((const float4 *)pos_a(a, pn))[j];
     }
+}
+
+template <int P>
+__device__ __forceinline__ int nb_species(float4 w)
+{
+    if constexpr (P == MIXED && kNbFixed)
+        return __float_as_int(w.w);
+    else
+        return species_of(w.w);
+}
+
+// approximate coordinates of a staged word (for the candidate filter)
+template <int P>
+__device__ __forceinline__ float3 nb_coords(float4 w, const Rep &rp)
+{
+    if constexpr (P == MIXED && kNbFixed)
+        return make_float3(__uint2float_rn(__float_as_uint(w.x)) * rp.qunit,
+                           __uint2float_rn(__float_as_uint(w.y)) * rp.qunit,
+                           __uint2float_rn(__float_as_uint(w.z)) * rp.qunit);
+    else
+        return make_float3(w.x, w.y, w.z);
+}
+
+// squared minimum-image distance of two staged words
+template <int P>
+__device__ __forceinline__ float nb_r2(float4 u, float4 w, const Rep &rp)
+{
+    float ex, ey, ez;
+    if constexpr (P == MIXED && kNbFixed) {
+        ex = sep_q(__float_as_uint(u.x), __float_as_uint(w.x), rp.qunit);
+        ey = sep_q(__float_as_uint(u.y), __float_as_uint(w.y), rp.qunit);
+        ez = sep_q(__float_as_uint(u.z), __float_as_uint(w.z), rp.qunit);
+    } else {
+        ex = sep_f(u.x, w.x, rp.Lhi, rp.invLf);
+        ey = sep_f(u.y, w.y, rp.Lhi, rp.invLf);
+        ez = sep_f(u.z, w.z, rp.Lhi, rp.invLf);
+    }
+    return fmaf(ex, ex, fmaf(ey, ey, ez * ez));
 }
 
 // distance of x from the interval [c - h, c + h] on a periodic axis
@@ -1648,12 +1724,13 @@ __global__ void __launch_bounds__(kNbBlock) k_nbuild(KArgs a)
                 while (k + 1 < nst && s_pref[k + 1] <= t)
                     ++k;
                 j = a.cstart[s_cell[k]] + (t - s_pref[k]);
-                q = hi_pos<P>(a, pn, j);
+                q = nb_word<P>(a, pn, j);
                 keep = true;
                 if (nst == 27) {
-                    const float gx = box_gap(q.x, ccx, hx, rp.Lhi, rp.invLf);
-                    const float gy = box_gap(q.y, ccy, hx, rp.Lhi, rp.invLf);
-                    const float gz = box_gap(q.z, ccz, hx, rp.Lhi, rp.invLf);
+                    const float3 x = nb_coords<P>(q, rp);
+                    const float gx = box_gap(x.x, ccx, hx, rp.Lhi, rp.invLf);
+                    const float gy = box_gap(x.y, ccy, hx, rp.Lhi, rp.invLf);
+                    const float gz = box_gap(x.z, ccz, hx, rp.Lhi, rp.invLf);
                     keep = fmaf(gx, gx, fmaf(gy, gy, gz * gz)) < rlmax2;
                 }
             }
@@ -1677,35 +1754,44 @@ __global__ void __launch_bounds__(kNbBlock) k_nbuild(KArgs a)
             if (staged <= kNbCap - kNbBlock && base + kNbBlock < total)
                 continue;
 
-            // scan the staged candidates for every own particle of the batch
-            for (int o = warp; o < nown; o += NW) {
-                const int i = ob + o;
-                const float4 H = hi_pos<P>(a, pn, i);
-                const int ti = species_of(H.w);
-                const float rl0 = a.tab.rl2[ti * 2], rl1 = a.tab.rl2[ti * 2 + 1];
-                int *out = a.nbr + (size_t)i * (size_t)a.K;
-                int cnt = s_cnt[o];
+            // scan the staged candidates: each warp pass takes kNbPass particles of
+            // the batch, so that every staged candidate read serves kNbPass tests
+            for (int o0 = warp * kNbPass; o0 < nown; o0 += NW * kNbPass) {
+                float4 H[kNbPass];
+                float rl0[kNbPass], rl1[kNbPass];
+                int cnt[kNbPass];
+#pragma unroll
+                for (int p = 0; p < kNbPass; ++p) {
+                    const bool ok = o0 + p < nown;
+                    H[p] = nb_word<P>(a, pn, ob + (ok ? o0 + p : 0));
+                    const int ti = nb_species<P>(H[p]);
+                    rl0[p] = ok ? a.tab.rl2[ti * 2] : -1.0f;       // -1: nothing passes
+                    rl1[p] = ok ? a.tab.rl2[ti * 2 + 1] : -1.0f;
+                    cnt[p] = ok ? s_cnt[o0 + p] : 0;
+                }
                 for (int s0 = 0; s0 < staged; s0 += 32) {
                     const int s = s0 + lane;
-                    bool in = false;
-                    int jj = 0;
-                    if (s < staged) {
-                        const float4 y = s_pos[s];
-                        jj = s_idx[s];
-                        const float ex = sep_f(H.x, y.x, rp.Lhi, rp.invLf);
-                        const float ey = sep_f(H.y, y.y, rp.Lhi, rp.invLf);
-                        const float ez = sep_f(H.z, y.z, rp.Lhi, rp.invLf);
-                        const float r2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
-                        in = jj != i && r2 < (species_of(y.w) ? rl1 : rl0);
+                    const bool sv = s < staged;
+                    const float4 y = sv ? s_pos[s] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    const int jj = sv ? s_idx[s] : -1;
+                    const bool tj = nb_species<P>(y) != 0;
+#pragma unroll
+                    for (int p = 0; p < kNbPass; ++p) {
+                        const int i = ob + o0 + p;
+                        const float r2 = nb_r2<P>(H[p], y, rp);
+                        const bool in = sv && jj != i && r2 < (tj ? rl1[p] : rl0[p]);
+                        const unsigned mm = __ballot_sync(0xffffffffu, in);
+                        const int at = cnt[p] + __popc(mm & lt_mask);
+                        if (in && at < a.K)
+                            a.nbr[(size_t)i * (size_t)a.K + at] = jj;
+                        cnt[p] += __popc(mm);
                     }
-                    const unsigned mm = __ballot_sync(0xffffffffu, in);
-                    const int at = cnt + __popc(mm & lt_mask);
-                    if (in && at < a.K)
-                        out[at] = jj;
-                    cnt += __popc(mm);
                 }
                 if (lane == 0)
-                    s_cnt[o] = cnt;
+#pragma unroll
+                    for (int p = 0; p < kNbPass; ++p)
+                        if (o0 + p < nown)
+                            s_cnt[o0 + p] = cnt[p];
             }
             staged = 0;
             __syncthreads();

@@ -51,7 +51,10 @@ def parse_args(argv=None):
     ap.add_argument("--no-graph", action="store_true",
                     help="plain stream launches instead of the CUDA graph (for per-kernel profiling)")
     ap.add_argument("--tpp", type=int, default=0, help="force-kernel threads per particle (0 = auto)")
-    ap.add_argument("--workload", choices=["ka65536", "lj-sweep", "e1", "replicas", "drift", "stability"],
+    ap.add_argument("--skin", type=float, default=0.3, help="neighbour-list skin (with --no-tune)")
+    ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (lanes, skin, capacity)")
+    ap.add_argument("--workload", choices=["ka65536", "lj-sweep", "e1", "replicas", "drift", "stability",
+                                           "longrun"],
                     default="ka65536",
                     help="ka65536: the headline line; the others print one line per case")
     ap.add_argument("--sizes", type=int, nargs="*", default=None, help="lj-sweep / e1 particle counts")
@@ -162,10 +165,11 @@ FLOP_PER_UPDATE = 210
 KERNEL_SOURCES = ("paper_0912_3824_gb300/csrc/md_kernels.cuh", "paper_0912_3824_gb300/csrc/md_common.cuh")
 
 
-def profiled_traffic(kernel):
+def profiled_traffic(kernel, skin):
     """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum)
     of `kernel` from the committed ncu summary, or None when no summary
-    covers it or its sources changed since the capture."""
+    covers it, its sources changed since the capture, or the capture ran with
+    another skin (another list length)."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "k_step_ka65536_mixed.md")
     if not os.path.exists(path):
@@ -173,10 +177,12 @@ def profiled_traffic(kernel):
     fields = {}
     for line in open(path):
         k, sep, v = line.partition(":")
-        if sep and k in ("traffic_bytes_per_launch", "kernel", "source_sha256"):
+        if sep and k in ("traffic_bytes_per_launch", "kernel", "source_sha256", "skin"):
             fields[k] = v.strip()
     now = " ".join(hashlib.sha256(open(os.path.join(ROOT, f), "rb").read()).hexdigest() for f in KERNEL_SOURCES)
     if fields.get("kernel") != kernel or fields.get("source_sha256") != now:
+        return None
+    if abs(float(fields.get("skin", "nan")) - float(skin)) > 1e-9:
         return None
     return float(fields["traffic_bytes_per_launch"])
 
@@ -254,6 +260,17 @@ def run_ours(args, rank, world, local):
     s, sim = prepare(md, synth, args.n, 5 + rank, args.precision, device,
                      use_graph=not args.no_graph, tpp=args.tpp)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=device)
+    # launch shape (lanes per particle), skin and list capacity from the autotuner, on
+    # the prepared state; --no-tune keeps --tpp / --skin as given
+    pos0, vel0, img0 = sim.get_state()
+    base = md.make_params(s.params, 0.001, skin=args.skin, precision=md.PRECISIONS[args.precision],
+                          sample_interval=100, use_graph=not args.no_graph, threads_per_particle=args.tpp)
+    trials = None
+    if not args.no_tune:
+        from paper_0912_3824_gb300 import tune
+        base, trials = tune.autotune(base, [s.n], [s.box], s.species, pos0, vel0, img0, device=device)
+    sim.close()
+    sim = md.System(base, [s.n], [s.box], s.species, pos0, vel0, img0, device=device)
 
     for _ in range(args.warmup):
         flush.fill_(1)
@@ -292,13 +309,16 @@ def run_ours(args, rank, world, local):
         "dtype": {"mixed": "f32 pair math, f32x2 (double-single) state", "fp64": "f64", "fp32": "f32"}[args.precision],
         "data": "synthetic (seeded fcc lattice, melted and quenched on the GPU)",
         "config": {"workload": f"Kob-Andersen 80:20, N={args.n} per GPU, rho=1.2, T=0.5 after quench, "
-                               f"dt=0.001, r_c=2.5 sigma_ab shifted, skin 0.3, NVE",
+                               f"dt=0.001, r_c=2.5 sigma_ab shifted, NVE",
                    "precision": args.precision, "md_steps_per_iteration": args.inner,
                    "l2": "flushed (256 MB write) between timed iterations",
                    "parallelism": f"replicas x{world} (no collective)",
                    "threads_per_particle": info1["threads_per_particle"],
-                   "neigh_capacity": info1["neigh_capacity"]},
+                   "neigh_capacity": info1["neigh_capacity"], "skin": float(base.skin),
+                   "tuned": trials is not None},
         "clocks": clk, "gpu_launches": launches,
+        "autotune": [{k: (round(v, 5) if isinstance(v, float) else v) for k, v in t.items()} for t in trials]
+                    if trials else None,
         "md": {"rebuilds_in_timed_region": rebuilds, "status": md._status_name(status),
                "energy_drift_per_step_rel": drift, "energy_max_rel_dev": maxdev,
                "samples": int(len(obs))},
@@ -308,14 +328,19 @@ def run_ours(args, rank, world, local):
 
     # ---- force kernel: live per-launch duration (stream launches + CUDA events) ----
     pos, vel, img = sim.get_state()
-    p_nog = md.make_params(s.params, 0.001, precision=md.PRECISIONS[args.precision], sample_interval=100,
-                           use_graph=False, threads_per_particle=args.tpp)
+    p_nog = md.make_params(s.params, 0.001, skin=base.skin, precision=md.PRECISIONS[args.precision],
+                           sample_interval=100, use_graph=False, threads_per_particle=base.threads_per_particle,
+                           neigh_capacity=base.neigh_capacity)
     sim_k = md.System(p_nog, [s.n], [s.box], s.species, pos, vel, img, device=device)
     sim_k.step(32)
     info_a = sim_k.info()
     sim_k.step(320)
     info_b = sim_k.info()
-    f_ms = (info_b["step_ms"] - info_a["step_ms"]) / max(1, info_b["step_launches"] - info_a["step_launches"])
+    ev_ms = (info_b["step_ms"] - info_a["step_ms"]) / max(1, info_b["step_launches"] - info_a["step_launches"])
+    # the step kernel's average duration inside the timed region (the CUDA-graph run),
+    # from the device timer each launch reads at its first block start and last block end
+    n_dev = info1["step_device_launches"] - info0["step_device_launches"]
+    f_ms = (info1["step_device_ms"] - info0["step_device_ms"]) / max(1, n_dev)
     n_list, n_cut = list_statistics(sim_k, s.params)
     sim_k.close()
     flops = (FLOP_PER_ENTRY * n_list + FLOP_PER_PAIR * n_cut + FLOP_PER_UPDATE) * s.n
@@ -326,8 +351,13 @@ def run_ours(args, rank, world, local):
                                   "(pair forces + velocity-Verlet update)",
         "achieved": flops / (f_ms * 1e-3) / 1e12, "peak": peak_max, "unit": "TFLOP/s",
         "frac": flops / (f_ms * 1e-3) / 1e12 / peak_max,
-        "traffic": profiled_traffic(f"k_step<{md.PRECISIONS[args.precision]}, {info1['threads_per_particle']}, 0>"),
-        "per_launch_ms": f_ms, "flop_per_launch": flops, "mean_list": float(n_list),
+        "traffic": profiled_traffic(f"k_step<{md.PRECISIONS[args.precision]}, {info1['threads_per_particle']}, 0>",
+                                    base.skin),
+        "per_launch_ms": f_ms, "launches_timed": int(n_dev),
+        "per_launch_ms_events": ev_ms,
+        "timing": "per_launch_ms: device timer over the timed region (every k_step launch of the graph); "
+                  "per_launch_ms_events: CUDA events around stream launches of the same kernel",
+        "flop_per_launch": flops, "mean_list": float(n_list),
         "mean_in_cutoff": float(n_cut),
         "peak_note": "FP32 FMA peak 152 SM x 128 lanes x 2 flop x 2.07 GHz (max clock)",
         "frac_at_sampled_clock": flops / (f_ms * 1e-3) / (152 * 128 * 2 * sm_mhz * 1e6),
@@ -337,7 +367,9 @@ def run_ours(args, rank, world, local):
     }
 
     # ---- same workload in full FP64 on the same GPU ----
-    p64 = md.make_params(s.params, 0.001, precision=md.MD_PREC_FP64, sample_interval=100)
+    p64 = md.make_params(s.params, 0.001, skin=args.skin, precision=md.MD_PREC_FP64, sample_interval=100)
+    if not args.no_tune:
+        p64, _ = tune.autotune(p64, [s.n], [s.box], s.species, pos, vel, img, device=device)
     sim64 = md.System(p64, [s.n], [s.box], s.species, pos, vel, img, device=device)
     sim64.step(args.inner)
     k64 = max(3, args.steps // 20)
@@ -572,6 +604,21 @@ def run_drift(args, local):
     return nve_cases(args, local, cases, "drift")
 
 
+def run_longrun(args, local):
+    """KA N=65536 quenched to T=0.5 (rescaled after every step for 10^4 steps),
+    then NVE for --md-steps steps in mixed precision and 1/5 of that in FP64,
+    with the plain cut and with the smoothing of Sec. 4 (h = 0.005): the energy
+    drift per particle over a long run."""
+    from paper_0912_3824_gb300 import synth
+    cases = []
+    for h in (0.0, 0.005):
+        params = synth.ka_params(smooth=h)
+        cases.append((f"ka65536-h{h}", lambda params=params: synth.make_system(65536, 1.2, 2.0, 5, params),
+                      0.001, (2.0, 0.5), args.md_steps))
+    return nve_cases(args, local, cases, "longrun", precisions=("mixed", "fp64"),
+                     steps_of={"fp64": max(1000, args.md_steps // 5)})
+
+
 def run_stability(args, local):
     """The stability protocol of Sec. 4: N = 10000 at rho = 0.75, T = 1.12,
     LJ (r_c = 2.5) and WCA, dt = 0.001 and 0.003, smoothing h = 0 and 0.005,
@@ -589,7 +636,7 @@ def run_stability(args, local):
     return nve_cases(args, local, cases, "stability")
 
 
-def nve_cases(args, local, cases, workload):
+def nve_cases(args, local, cases, workload, precisions=("fp32", "mixed", "fp64"), steps_of=None):
     torch, md, synth, device, stream, flush = _gpu_setup(local)
     lags = [10 ** k for k in range(1, 8)]
     if args.cases:
@@ -600,17 +647,18 @@ def nve_cases(args, local, cases, workload):
         prep = md.System.from_synth(s, dt=dt, precision=md.MD_PREC_MIXED, sample_interval=100, device=device)
         if temps is not None:
             equilibrate(prep, temps[0], temps[1])
-            if name == "ka65536":                 # quench: rescale after every step
+            if name.startswith("ka65536"):        # quench: rescale after every step
                 for _ in range(10000):
                     prep.step(1)
                     prep.rescale(temps[1])
         assert prep.sync() == md.MD_OK
         pos, vel, img = prep.get_state()
         prep.close()
-        for prec in ("fp32", "mixed", "fp64"):
+        for prec in precisions:
+            nsteps_p = (steps_of or {}).get(prec, nsteps)
             p = md.make_params(s.params, dt, precision=md.PRECISIONS[prec], sample_interval=100)
             sim = md.System(p, [s.n], [s.box], s.species, pos, vel, img, device=device)
-            obs, ms, msd = nve_run(md, torch, stream, sim, s.n, s.box, s.species, nsteps, lags)
+            obs, ms, msd = nve_run(md, torch, stream, sim, s.n, s.box, s.species, nsteps_p, lags)
             status = sim.sync()
             info = sim.info()
             sim.close()
@@ -618,10 +666,10 @@ def nve_cases(args, local, cases, workload):
             pmax = float(np.abs(obs["p"]).max()) / s.n
             lines.append({"workload": workload, "case": name, "precision": prec, "n": s.n, "dt": dt,
                           "smooth_h": float(s.params.get("smooth", 0.0)),
-                          "md_steps": nsteps, "value": s.n * nsteps / (ms * 1e-3), "unit": UNIT,
-                          "us_per_md_step": ms * 1e3 / nsteps,
+                          "md_steps": nsteps_p, "value": s.n * nsteps_p / (ms * 1e-3), "unit": UNIT,
+                          "us_per_md_step": ms * 1e3 / nsteps_p,
                           "energy_drift_per_step_rel": slope,
-                          "energy_drift_total_rel": None if slope is None else slope * nsteps,
+                          "energy_drift_total_rel": None if slope is None else slope * nsteps_p,
                           "energy_max_rel_dev": maxdev, "max_abs_momentum_per_particle": pmax,
                           "e_per_particle": float((obs["e_pot"][0] + obs["e_kin"][0]) / s.n),
                           "msd_A": msd, "rebuilds": int(info["rebuilds"]),
@@ -672,7 +720,7 @@ def main(argv=None):
         if args.impl == "reference" or world > 1:
             raise SystemExit("--workload other than ka65536 runs our path on one GPU only")
         fn = {"lj-sweep": run_lj_sweep, "e1": run_e1, "replicas": run_replicas, "drift": run_drift,
-              "stability": run_stability}[args.workload]
+              "stability": run_stability, "longrun": run_longrun}[args.workload]
         for line in fn(args, local):
             print(json.dumps(line), flush=True)
         return

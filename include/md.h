@@ -129,6 +129,10 @@ typedef struct {
     double  rebuild_ms;       /* with use_graph = 0: summed time of the rebuild chains (sort,
                                  list build) launched when a check point asked for one         */
     int64_t rebuild_checks;   /* with use_graph = 0: rebuild chains launched                    */
+    double  step_device_ms;   /* any mode: summed device duration of the step-kernel launches
+                                 that advanced a step (first block start to last block end,
+                                 read from the GPU's global timer)                              */
+    int64_t step_device_launches; /* launches summed into step_device_ms (one per MD step)      */
 } md_info_t;
 
 typedef struct md_handle md_handle;

@@ -38,7 +38,7 @@ using mdk::KernelSet;
 namespace {
 
 constexpr size_t kAlign = 256;
-constexpr int kIntBlock = 256, kForceBlock = 256, kNbBlock = 256, kScanBlock = 1024;
+constexpr int kIntBlock = 256, kForceBlock = 128, kNbBlock = 256, kScanBlock = 1024;
 constexpr double kCellMargin = 1e-3;   // cell edge exceeds the largest list radius by this
 constexpr int kUnroll = 16;            // step kernels per loop iteration of the graph
 constexpr int kCheck = 4;              // rebuild check after every kCheck steps (divides kUnroll)
@@ -1359,6 +1359,8 @@ int md_info(md_handle *h, md_info_t *out)
     out->step_launches = h->step_launches;
     out->rebuild_ms = h->rebuild_ms;
     out->rebuild_checks = h->rebuild_checks;
+    out->step_device_ms = (double)c.dev_ns * 1e-6;
+    out->step_device_launches = c.dev_launches;
     return MD_OK;
 }
 

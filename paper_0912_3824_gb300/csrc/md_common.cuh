@@ -45,6 +45,10 @@ struct Ctl {
     long long rebuilds;
     long long obs_count;      // samples written to the ring
     long long n_force, n_integrate, n_rebuild_k, n_other;   // kernel executions
+    unsigned long long t_first_inv;   // step kernel: ~(earliest block start, %globaltimer ns) of the
+                                      // running launch (0 = none yet; atomicMax of the complement)
+    unsigned long long dev_ns;        // summed device duration of the step-kernel launches
+    long long dev_launches;
     float last_maxdisp2;
     float pad1;
 };

@@ -32,7 +32,7 @@
 namespace mdk {
 
 constexpr int kIntBlock = 256;   // per-particle kernels: one thread per particle
-constexpr int kForceBlock = 256; // force / step kernels: tpp threads per particle
+constexpr int kForceBlock = 128; // force / step kernels: tpp threads per particle
 constexpr int kNbBlock = 256;    // neighbour build: one block per cell
 constexpr int kScanBlock = 1024;
 constexpr int kPartF = 12;       // doubles per block partial of the force / step kernels
@@ -44,6 +44,13 @@ constexpr bool kSplitUpdate = false; // below 4 lanes: one lane updates (measure
 // ---------------------------------------------------------------------------
 // small helpers
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
 __device__ __forceinline__ float warp_max(float v)
 {
 #pragma unroll
@@ -1219,6 +1226,8 @@ __global__ void __launch_bounds__(kForceBlock) k_step(KArgs a)
     const bool active = st0 == 0u && remaining > 0;
     const bool last = remaining == 1;
     const bool sample = active && (step % a.si) == 0;
+    if (threadIdx.x == 0)                       // device timing of this launch: earliest start
+        atomicMax(&ctl->t_first_inv, ~global_ns());
 
     double part[kPartF];
     float d2 = 0.f, v2 = 0.f, a2 = 0.f;
@@ -1294,6 +1303,15 @@ __global__ void __launch_bounds__(kForceBlock) k_step(KArgs a)
             if (a.set_loop)
                 cudaGraphSetConditional(a.h_loop, (s2 == 0u && rem > 0) ? 1u : 0u);
         }
+        // duration of this launch (one that advanced a step): earliest block start
+        // to the end of the last block
+        const unsigned long long t0 = ~ctl->t_first_inv;
+        const unsigned long long t1 = global_ns();
+        if (active) {
+            ctl->dev_ns += t1 > t0 ? t1 - t0 : 0ull;
+            ctl->dev_launches += 1;
+        }
+        ctl->t_first_inv = 0ull;
     }
 }
 

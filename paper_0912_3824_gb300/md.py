@@ -50,7 +50,8 @@ class md_info_t(C.Structure):
                 ("cells_per_edge", C.c_int32), ("step", C.c_int64), ("rebuilds", C.c_int64),
                 ("kernel_launches", C.c_int64), ("max_neighbours", C.c_int32),
                 ("status", C.c_int32), ("step_ms", C.c_double), ("step_launches", C.c_int64),
-                ("rebuild_ms", C.c_double), ("rebuild_checks", C.c_int64)]
+                ("rebuild_ms", C.c_double), ("rebuild_checks", C.c_int64),
+                ("step_device_ms", C.c_double), ("step_device_launches", C.c_int64)]
 
 
 OBS_DTYPE = np.dtype([("step", np.int64), ("e_pot", np.float64), ("e_kin", np.float64),

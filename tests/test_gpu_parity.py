@@ -430,3 +430,42 @@ def test_correlator_matches_blocking_oracle(md, prec):
     assert np.isnan(msd[~ok]).all()
     corr.close()
     sim.close()
+
+
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_step_kernel_device_timer(md, use_graph):
+    """Every step-kernel launch adds its device duration (first block start to
+    last block end) to md_info: one launch per MD step, graph or not."""
+    s = _system("ka", 4000, amp=0.05)
+    sim = _sim(md, s, "mixed", use_graph=use_graph)
+    sim.step(10)
+    a = sim.info()
+    sim.step(200)
+    b = sim.info()
+    n = b["step_device_launches"] - a["step_device_launches"]
+    assert n == 200
+    per = (b["step_device_ms"] - a["step_device_ms"]) / n
+    assert 1e-4 < per < 5.0
+    sim.close()
+
+
+def test_autotuner_picks_a_timed_candidate(md):
+    """The autotuner times each candidate (lanes per particle x skin) on the
+    caller's state and returns the fastest, with the list capacity set from the
+    longest list seen; the tuned system runs and matches the oracle forces."""
+    from paper_0912_3824_gb300 import tune
+    s = _system("ka", 4000, amp=0.05)
+    base = md.make_params(s.params, 0.001, precision=md.MD_PREC_MIXED)
+    p, trials = tune.autotune(base, [s.n], [s.box], s.species, s.pos, s.vel, s.image,
+                              lanes=(1, 2), skins=(0.25, 0.3), steps=100, repeats=2)
+    assert len(trials) == 4 and all(t["status"] == "MD_OK" for t in trials)
+    fastest = min(trials, key=lambda t: t["ms_per_step"])
+    assert (p.threads_per_particle, p.skin) == (fastest["threads_per_particle"], fastest["skin"])
+    assert p.neigh_capacity % 32 == 0 and p.neigh_capacity >= 1.25 * fastest["max_neighbours"]
+    sim = md.System(p, [s.n], [s.box], s.species, s.pos, s.vel, s.image)
+    f, _, _ = sim.forces()
+    fr, _, _ = oracle.forces_cells(s.params, s.box, s.species, s.pos)
+    assert _ferr(f, fr) <= TOL_F["mixed"]
+    sim.step(200)
+    assert sim.sync() == md.MD_OK
+    sim.close()

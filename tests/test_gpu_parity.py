@@ -469,3 +469,61 @@ def test_autotuner_picks_a_timed_candidate(md):
     sim.step(200)
     assert sim.sync() == md.MD_OK
     sim.close()
+
+
+@pytest.fixture(scope="module")
+def ka65536_reference():
+    """KA N=65536 start and the oracle's 24 velocity-Verlet steps from it (dt 0.002)."""
+    s = synth.perturb(synth.ka_mixture(n=65536, temperature=0.7, seed=5), 0.05, 9)
+    return s, oracle.vv_run(s.params, s.box, s.species, s.pos, s.vel, s.image, 0.002, 24, sample=8)
+
+
+@pytest.mark.parametrize("prec,tpp,skin,tol", [("mixed", 2, 0.2, 2e-6), ("mixed", 0, 0.3, 2e-6),
+                                               ("fp64", 4, 0.3, 1e-10)])
+def test_full_size_step_kernel_trajectory_ka65536(md, ka65536_reference, prec, tpp, skin, tol):
+    """The bench's system and launch shape (KA N=65536; the autotuner's usual
+    pick of 2 lanes and skin 0.2, and the defaults): 24 steps of the step
+    kernel in the CUDA graph, with list rebuilds, against the oracle's
+    velocity Verlet from the same start; every particle's position and the
+    sampled E_pot and E_kin."""
+    s, (rp, rv, ri, _, rec) = ka65536_reference
+    pos, vel, img, obs, info = _trajectory(md, s, prec, 0.002, 24, 8, threads_per_particle=tpp, skin=skin)
+    assert info["rebuilds"] >= 2
+    assert np.abs((pos + img * s.box) - (rp + ri * s.box)).max() < tol
+    assert (obs["step"] == rec["step"]).all()
+    assert np.allclose(obs["e_pot"], rec["e_pot"], rtol=1e-6 if prec == "mixed" else 1e-12)
+    assert np.allclose(obs["e_kin"], rec["e_kin"], rtol=1e-6 if prec == "mixed" else 1e-12)
+
+
+def test_full_size_replica_ensemble_sampled(md):
+    """The 256-replica ensemble (N_r uniform in 500..8000, seed 4) in one handle:
+    after 20 steps, six replicas (first, last and four drawn at random) equal
+    their own oracle runs particle by particle."""
+    sizes = synth.ensemble_sizes(256, 500, 8000, seed=4)
+    reps = [synth.ka_mixture(n=m, temperature=0.8, seed=4000 + r) for r, m in enumerate(sizes)]
+    cat = lambda f: np.concatenate([getattr(r, f) for r in reps])
+    p = md.make_params(reps[0].params, 0.001, precision=md.MD_PREC_MIXED, sample_interval=10)
+    sim = md.System(p, sizes, [r.box for r in reps], cat("species"), cat("pos"), cat("vel"), cat("image"))
+    sim.step(20)
+    assert sim.sync() == md.MD_OK
+    pos, vel, img = sim.get_state()
+    start = np.concatenate([[0], np.cumsum(sizes)])
+    pick = [0, 255] + list(np.random.default_rng(1).choice(np.arange(1, 255), 4, replace=False))
+    for r in pick:
+        q = reps[r]
+        rp, rv, ri, _, _ = oracle.vv_run(q.params, q.box, q.species, q.pos, q.vel, q.image, 0.001, 20)
+        sl = slice(start[r], start[r + 1])
+        assert np.abs((pos[sl] + img[sl] * q.box) - (rp + ri * q.box)).max() < 1e-6
+        assert np.abs(vel[sl] - rv).max() < 1e-5
+    sim.close()
+
+
+def test_full_size_lj_1m_two_steps(md):
+    """The largest size of the LJ sweep (N = 1,048,576, rho 0.8442, dt 0.005,
+    mixed, default launch shape): two steps against the oracle, every
+    particle."""
+    s = synth.perturb(synth.lj_fluid(n=1048576, density=0.8442, temperature=1.0, seed=3), 0.03, 4)
+    pos, vel, img, obs, info = _trajectory(md, s, "mixed", 0.005, 2, 1)
+    rp, rv, ri, _, rec = oracle.vv_run(s.params, s.box, s.species, s.pos, s.vel, s.image, 0.005, 2, sample=1)
+    assert np.abs((pos + img * s.box) - (rp + ri * s.box)).max() < 1e-6
+    assert np.allclose(obs["e_pot"], rec["e_pot"], rtol=1e-6)

@@ -90,7 +90,8 @@ typedef struct {
     int32_t use_graph;        /* 1 = md_step runs as one CUDA graph with the rebuild branch and
                                  the step loop decided on the device (default); 0 = plain
                                  stream launches, for debugging and per-kernel timing          */
-    int32_t reorder;          /* 1 = order cells along a Morton curve (default); 0 = x-fastest  */
+    int32_t reorder;          /* cell order in memory: 1 = Morton curve (default), 2 = Hilbert
+                                 curve (the paper's reorder, Sec. 2.2), 0 = x-fastest           */
     int32_t reserved0;        /* must be zero                                                   */
     double  smooth_h;         /* h >= 0 of the smoothing of Sec. 4: every pair potential is
                                  multiplied by g(x) = x^4 / (1 + x^4), x = (r - r_c,ab) /
@@ -144,6 +145,13 @@ int md_params_default(md_params *p);
 
 /* Device workspace needed for n_replicas systems with n_per_replica[r]
  * particles in cubic boxes of edge box[r].  Writes *bytes. */
+/* Host-only: the order of the cells of replica 0 in memory.  rank[lin] (for
+ * lin = x + nc (y + nc z), caller array of nc^3 entries, may be NULL) is the
+ * position of cell (x, y, z) along the chosen curve; *cells_per_edge = nc.
+ * Same argument checks as md_workspace_size. */
+int md_cell_order(const md_params *p, int32_t n_replicas, const int64_t *n_per_replica, const double *box,
+                  int32_t *rank, int32_t *cells_per_edge);
+
 int md_workspace_size(const md_params *p, int32_t n_replicas,
                       const int64_t *n_per_replica, const double *box, size_t *bytes);
 

@@ -69,6 +69,41 @@ struct Layout {
 
 int prec_pos_bytes(int prec) { return prec == MD_PREC_FP64 ? 32 : 16; }
 
+// Index of cell (x, y, z) along the Hilbert curve through a 2^b cube: the
+// coordinates are transformed in place (Skilling's transposition method,
+// "Programming the Hilbert curve", AIP Conf. Proc. 707, 2004), then their bits
+// are interleaved, most significant first.
+uint32_t hilbert3(uint32_t x, uint32_t y, uint32_t z, int b)
+{
+    uint32_t X[3] = {x, y, z};
+    const uint32_t top = 1u << (b - 1);
+    for (uint32_t q = top; q > 1; q >>= 1) {
+        const uint32_t low = q - 1;
+        for (int i = 0; i < 3; ++i) {
+            if (X[i] & q) {
+                X[0] ^= low;                          // reflect the lower bits of axis 0
+            } else {
+                const uint32_t t = (X[0] ^ X[i]) & low;   // exchange them with axis i
+                X[0] ^= t;
+                X[i] ^= t;
+            }
+        }
+    }
+    X[1] ^= X[0];                                     // Gray code across the axes
+    X[2] ^= X[1];
+    uint32_t t = 0;
+    for (uint32_t q = top; q > 1; q >>= 1)
+        if (X[2] & q)
+            t ^= q - 1;
+    for (int i = 0; i < 3; ++i)
+        X[i] ^= t;
+    uint32_t h = 0;
+    for (int k = b - 1; k >= 0; --k)
+        for (int i = 0; i < 3; ++i)
+            h = (h << 1) | ((X[i] >> k) & 1u);
+    return h;
+}
+
 uint32_t spread3(uint32_t v)
 {
     uint32_t r = 0;
@@ -113,6 +148,10 @@ int make_geometry(const md_params *p, int R, const int64_t *nrep, const double *
         if (p->reserved[k] != 0) { msg = "reserved fields must be zero"; return MD_E_INVAL; }
     if (!(p->smooth_h >= 0.0) || !std::isfinite(p->smooth_h)) {
         msg = "smooth_h must be finite and >= 0";
+        return MD_E_INVAL;
+    }
+    if (p->reorder < 0 || p->reorder > 2) {
+        msg = "reorder must be 0 (x-fastest), 1 (Morton) or 2 (Hilbert)";
         return MD_E_INVAL;
     }
     if (p->smooth_h > 0.0 && tpp > 8) {
@@ -200,13 +239,20 @@ int make_geometry(const md_params *p, int R, const int64_t *nrep, const double *
         for (int s = 0; s < q.n; s += g.ppb_f)
             g.blk_f.push_back(make_int4(q.start + s, q.start + std::min(q.n, s + g.ppb_f), r, 0));
         q.bf1 = (int)g.blk_f.size();
-        // cells, ordered along a Morton curve (or x-fastest)
+        // cells, ordered along a Morton curve, a Hilbert curve (the curve of the
+        // paper's reorder, Sec. 2.2) through the enclosing 2^b cube, or x-fastest
         const int nc3 = nc * nc * nc;
+        int bits = 1;
+        while ((1 << bits) < nc)
+            ++bits;
         std::vector<std::pair<uint32_t, int>> order(nc3);
         for (int lin = 0; lin < nc3; ++lin) {
             const int cx = lin % nc, cy = (lin / nc) % nc, cz = lin / (nc * nc);
-            const uint32_t code = p->reorder ? (spread3(cx) | (spread3(cy) << 1) | (spread3(cz) << 2))
-                                             : (uint32_t)lin;
+            uint32_t code = (uint32_t)lin;
+            if (p->reorder == 1)
+                code = spread3(cx) | (spread3(cy) << 1) | (spread3(cz) << 2);
+            else if (p->reorder == 2)
+                code = hilbert3(cx, cy, cz, bits);
             order[lin] = {code, lin};
         }
         std::sort(order.begin(), order.end());
@@ -680,6 +726,23 @@ int md_params_default(md_params *p)
     p->sample_interval = 100;
     p->use_graph = 1;
     p->reorder = 1;
+    return MD_OK;
+}
+
+int md_cell_order(const md_params *p, int32_t n_replicas, const int64_t *n_per_replica, const double *box,
+                  int32_t *rank, int32_t *cells_per_edge)
+{
+    Geometry g;
+    std::string msg;
+    int rc = make_geometry(p, n_replicas, n_per_replica, box, g, msg);
+    if (rc)
+        return rc;
+    const int nc = g.rep[0].nc;
+    if (cells_per_edge)
+        *cells_per_edge = nc;
+    if (rank)
+        for (int lin = 0; lin < nc * nc * nc; ++lin)
+            rank[lin] = g.crank[lin];
     return MD_OK;
 }
 

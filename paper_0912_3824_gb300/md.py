@@ -78,6 +78,7 @@ def _load() -> C.CDLL:
     sig = {
         "md_params_default": ([P], C.c_int),
         "md_workspace_size": ([P, C.c_int32, i64, d, C.POINTER(C.c_size_t)], C.c_int),
+        "md_cell_order": ([P, C.c_int32, i64, d, i32, i32], C.c_int),
         "md_create": ([C.POINTER(H), P, C.c_int32, i64, d, i32, d, d, i32, C.c_void_p, C.c_size_t,
                        C.c_void_p], C.c_int),
         "md_step": ([H, C.c_int64], C.c_int),
@@ -115,7 +116,7 @@ EXPORTED = ("md_params_default", "md_workspace_size", "md_create", "md_step",
             "md_set_state", "md_get_neighbours", "md_info", "md_sync", "md_destroy",
             "md_last_error", "md_status_string", "md_forces_noalloc", "md_andersen",
             "md_corr_workspace_size", "md_corr_create", "md_corr_sample", "md_corr_result",
-            "md_corr_destroy")
+            "md_corr_destroy", "md_cell_order")
 MD_NOALLOC_MAX_N = 1048576
 
 
@@ -161,6 +162,20 @@ def md_workspace_size(p: md_params, n_per_replica, box) -> int:
     _check(_lib.md_workspace_size(C.byref(p), len(n), n.ctypes.data_as(C.POINTER(C.c_int64)),
                                   _dptr(b), C.byref(out)))
     return out.value
+
+
+def md_cell_order(p: md_params, n_per_replica, box):
+    """Position along the cell curve of every cell (x, y, z) of replica 0, as an
+    array [nc, nc, nc] indexed [z, y, x]."""
+    nr = np.ascontiguousarray(n_per_replica, dtype=np.int64)
+    bx = np.ascontiguousarray(box, dtype=np.float64)
+    nc = C.c_int32()
+    _check(_lib.md_cell_order(C.byref(p), len(nr), nr.ctypes.data_as(C.POINTER(C.c_int64)), _dptr(bx), None,
+                              C.byref(nc)))
+    rank = np.empty(nc.value ** 3, dtype=np.int32)
+    _check(_lib.md_cell_order(C.byref(p), len(nr), nr.ctypes.data_as(C.POINTER(C.c_int64)), _dptr(bx),
+                              _iptr(rank), C.byref(nc)))
+    return rank.reshape(nc.value, nc.value, nc.value)
 
 
 def md_create(p: md_params, n_per_replica, box, species, pos, vel, image, workspace_ptr: int,
@@ -268,7 +283,7 @@ def md_forces_noalloc(p: md_params, n: int, box: float, species_ptr: int, pos_pt
 # ---------------------------------------------------------------------------
 def make_params(pot: dict, dt: float, skin: float = 0.3, precision: int = MD_PREC_MIXED,
                 sample_interval: int = 100, neigh_capacity: int = 0, threads_per_particle: int = 0,
-                use_graph: bool = True, reorder: bool = True, obs_capacity: int = 0) -> md_params:
+                use_graph: bool = True, reorder: int = 1, obs_capacity: int = 0) -> md_params:
     p = md_params_default()
     p.n_species = int(pot["n_species"])
     p.shift = 1 if pot.get("shift", True) else 0
@@ -286,7 +301,7 @@ def make_params(pot: dict, dt: float, skin: float = 0.3, precision: int = MD_PRE
     p.neigh_capacity = int(neigh_capacity)
     p.threads_per_particle = int(threads_per_particle)
     p.use_graph = 1 if use_graph else 0
-    p.reorder = 1 if reorder else 0
+    p.reorder = int(reorder)          # 0 x-fastest, 1 Morton, 2 Hilbert (True / False: 1 / 0)
     p.obs_capacity = int(obs_capacity)
     return p
 

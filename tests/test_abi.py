@@ -118,3 +118,38 @@ def test_noalloc_rejects_smoothing_before_touching_the_device(md):
     rc = md._lib.md_forces_noalloc(ctypes.byref(p), 8, ctypes.c_double(20.0), ctypes.addressof(sp), addr, addr,
                                    addr, addr, None)
     assert rc == md.MD_E_INVAL
+
+
+def _cells_in_order(md, reorder, box):
+    from paper_0912_3824_gb300 import synth
+    p = md.make_params(synth.ka_params(), 0.001, reorder=reorder)
+    rank = md.md_cell_order(p, [int(1.2 * box ** 3)], [box])
+    nc = rank.shape[0]
+    order = np.argsort(rank.ravel())               # cells (linear x-fastest index) along the curve
+    xyz = np.stack([order % nc, (order // nc) % nc, order // (nc * nc)], axis=1)
+    assert np.array_equal(np.sort(rank.ravel()), np.arange(nc ** 3))     # a bijection
+    return nc, rank, xyz
+
+
+def test_hilbert_cell_order_steps_to_a_face_neighbour(md):
+    """reorder = 2, 8 cells per edge (a power of two): consecutive cells along
+    the Hilbert curve share a face, the defining property of the curve."""
+    nc, _, xyz = _cells_in_order(md, 2, 23.0)
+    assert nc == 8
+    assert (np.abs(np.diff(xyz, axis=0)).sum(axis=1) == 1).all()
+
+
+def test_hilbert_cell_order_in_a_cut_cube_mostly_steps_to_neighbours(md):
+    """13 cells per edge: the curve of the enclosing 16^3 cube restricted to the
+    box still steps to a face neighbour most of the time."""
+    nc, _, xyz = _cells_in_order(md, 2, 37.94)
+    assert nc == 13
+    assert (np.abs(np.diff(xyz, axis=0)).sum(axis=1) == 1).mean() > 0.8
+
+
+def test_morton_and_plain_cell_orders(md):
+    nc, rank, xyz = _cells_in_order(md, 1, 23.0)
+    assert {tuple(c) for c in xyz[:8]} == {(x, y, z) for x in (0, 1) for y in (0, 1) for z in (0, 1)}
+    assert tuple(xyz[8]) == (2, 0, 0)               # x carries the lowest interleaved bit
+    nc, rank, xyz = _cells_in_order(md, 0, 23.0)
+    assert np.array_equal(rank.ravel(), np.arange(nc ** 3))

@@ -216,11 +216,17 @@ def test_repeated_runs_are_deterministic(md):
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_reorder_does_not_change_forces(md, prec):
+    """Cells in x-fastest, Morton and Hilbert order: the same forces, and a short
+    trajectory that stays together."""
     s = _system("ka", 4000)
-    f1, _, t1 = _sim(md, s, prec, reorder=True).forces()
-    f2, _, t2 = _sim(md, s, prec, reorder=False).forces()
-    assert _ferr(f1, f2) <= TOL_F[prec]
-    assert t1["e_pot"][0] == pytest.approx(t2["e_pot"][0], rel=TOL_E[prec])
+    f0, _, t0 = _sim(md, s, prec, reorder=0).forces()
+    for r in (1, 2):
+        f1, _, t1 = _sim(md, s, prec, reorder=r).forces()
+        assert _ferr(f1, f0) <= TOL_F[prec]
+        assert t1["e_pot"][0] == pytest.approx(t0["e_pot"][0], rel=TOL_E[prec])
+    a = _trajectory(md, s, prec, 0.002, 60, 20, reorder=2)
+    b = _trajectory(md, s, prec, 0.002, 60, 20, reorder=0)
+    assert np.abs((a[0] + a[2] * s.box) - (b[0] + b[2] * s.box)).max() < (1e-9 if prec == "fp64" else 1e-5)
 
 
 @pytest.mark.parametrize("tpp", [1, 2, 4, 16, 32])

@@ -39,6 +39,7 @@ constexpr int kPartF = 12;       // doubles per block partial of the force / ste
 constexpr int kUnr = 4;          // list entries per lane and iteration of the FP32 pair loops
                                  // (a multiple of 4, at most 8: lists are padded to 8)
 constexpr int kPfDepth = 1;      // iterations ahead at which the list indices are loaded
+constexpr bool kPadLists = true; // list rows padded with the particle itself (no masks in the loop)
 constexpr bool kSplitUpdate = false; // below 4 lanes: one lane updates (measured faster than sharing)
 
 // ---------------------------------------------------------------------------
@@ -126,10 +127,11 @@ __device__ __forceinline__ int4 *img_of(const KArgs &a, int par) { return par ? 
 // Re-anchor a double-single coordinate so that its high word lies on the grid
 // of spacing `grid` (a power of two chosen so that every coordinate in
 // [-L, 2L) is exactly representable on it), then wrap it into [0, L).
-// Differences of anchored high words, and their shift by the anchored box
-// edge Lhi, are exact in single precision; this is what makes the
-// single-precision pair separation accurate for pairs across the boundary.
-// Returns the change of the image counter (-1, 0, 1).
+// Shifting an anchored high word by the anchored box edge Lhi is exact in
+// single precision, so the wrap loses nothing; differences of high words are
+// exact too (the displacement check uses them).  The pair loops read the
+// fixed-point copy instead (fixq).  Returns the change of the image counter
+// (-1, 0, 1).
 __device__ __forceinline__ int anchor_wrap(ds x, float grid, float inv_grid, float Lhi, float Llo,
                                            float &H, float &l)
 {
@@ -148,18 +150,6 @@ __device__ __forceinline__ int anchor_wrap(ds x, float grid, float inv_grid, flo
     H = h;
     l = r;
     return img;
-}
-
-// Minimum-image separation component from anchored double-single coordinates.
-// d = Hi - Hj and d - k*Lhi are exact; only the final sum rounds.
-__device__ __forceinline__ float sep_ds(float Hi, float li, float Hj, float lj,
-                                        float Lhi, float Llo, float invL)
-{
-    float d = __fsub_rn(Hi, Hj);
-    float k = rintf(__fmul_rn(d, invL));
-    float dh = __fmaf_rn(-k, Lhi, d);
-    float dl = __fmaf_rn(-k, Llo, __fsub_rn(li, lj));
-    return __fadd_rn(dh, dl);
 }
 
 __device__ __forceinline__ float sep_f(float xi, float xj, float L, float invL)
@@ -678,7 +668,8 @@ __device__ __forceinline__ void pair_forces(const KArgs &a, const Rep &rp, int p
             int4 Qs[kUnr];
 #pragma unroll
             for (int u = 0; u < kUnr; ++u) {
-                const int j = k0 + u < nn ? jj[u] : ii;
+                // rows are padded with the particle itself up to a multiple of 4
+                const int j = kPadLists ? jj[u] : (k0 + u < nn ? jj[u] : ii);
                 if constexpr (P == MIXED)
                     Qs[u] = __ldg(qp + j);
                 else
@@ -703,10 +694,13 @@ __device__ __forceinline__ void pair_forces(const KArgs &a, const Rep &rp, int p
                     dz = sep_f(Hi.z, Hj.z, rp.Lhi, rp.invLf);
                 }
                 const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                const bool in = (k0 + u < nn) && (r2 < (tj ? pr.rc2[1] : pr.rc2[0]));
+                // (the particle itself, r2 = 0 exactly, is never inside)
+                const bool in = (kPadLists ? r2 > 0.0f : k0 + u < nn) && (r2 < (tj ? pr.rc2[1] : pr.rc2[0]));
                 const float sig2 = tj ? pr.sig2[1] : pr.sig2[0];
                 const float eps48 = tj ? pr.eps48[1] : pr.eps48[0];
-                const float ir2 = __fdividef(1.0f, in ? r2 : 1.0f);
+                // outside the cutoff (or the padding entry, r2 = 0) the factors below
+                // are not finite but are never selected (smoothing needs a finite r)
+                const float ir2 = __fdividef(1.0f, (SM || !kPadLists) ? (in ? r2 : 1.0f) : r2);
                 const float s2 = sig2 * ir2;
                 const float s6 = s2 * s2 * s2;
                 float fr = in ? eps48 * ir2 * s6 * (s6 - 0.5f) : 0.0f;
@@ -1817,6 +1811,10 @@ __global__ void __launch_bounds__(kNbBlock) k_nbuild(KArgs a)
         for (int o = tid; o < nown; o += kNbBlock) {
             const int cnt = s_cnt[o];
             a.nnbr[ob + o] = cnt < a.K ? cnt : a.K;
+            // pad the row with the particle itself to a multiple of 4 entries, so the
+            // pair loop reads whole 16-byte groups without masking (K is a multiple of 8)
+            for (int k = cnt; k < ((cnt + 3) & ~3) && k < a.K; ++k)
+                a.nbr[(size_t)(ob + o) * (size_t)a.K + k] = ob + o;
             atomicMax(&ctl->max_nbr, cnt);
             if (cnt > a.K)
                 atomicOr(&ctl->status, ST_OVERFLOW);

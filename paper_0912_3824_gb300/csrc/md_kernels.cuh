@@ -698,9 +698,7 @@ __device__ __forceinline__ void pair_forces(const KArgs &a, const Rep &rp, int p
                 const bool in = (kPadLists ? r2 > 0.0f : k0 + u < nn) && (r2 < (tj ? pr.rc2[1] : pr.rc2[0]));
                 const float sig2 = tj ? pr.sig2[1] : pr.sig2[0];
                 const float eps48 = tj ? pr.eps48[1] : pr.eps48[0];
-                // outside the cutoff (or the padding entry, r2 = 0) the factors below
-                // are not finite but are never selected (smoothing needs a finite r)
-                const float ir2 = __fdividef(1.0f, (SM || !kPadLists) ? (in ? r2 : 1.0f) : r2);
+                const float ir2 = __fdividef(1.0f, in ? r2 : 1.0f);
                 const float s2 = sig2 * ir2;
                 const float s6 = s2 * s2 * s2;
                 float fr = in ? eps48 * ir2 * s6 * (s6 - 0.5f) : 0.0f;

@@ -36,7 +36,7 @@ constexpr int kForceBlock = 128; // force / step kernels: tpp threads per partic
 constexpr int kNbBlock = 256;    // neighbour build: one block per cell
 constexpr int kScanBlock = 1024;
 constexpr int kPartF = 12;       // doubles per block partial of the force / step kernels
-constexpr int kUnr = 4;          // list entries per lane and iteration of the FP32 pair loops
+constexpr int kUnr = 8;          // list entries per lane and iteration of the FP32 pair loops
                                  // (a multiple of 4, at most 8: lists are padded to 8)
 constexpr int kPfDepth = 1;      // iterations ahead at which the list indices are loaded
 constexpr bool kPadLists = true; // list rows padded with the particle itself (no masks in the loop)
@@ -554,11 +554,11 @@ __device__ __forceinline__ void pair_forces(const KArgs &a, const Rep &rp, int p
             const int jj[4] = {q.x, q.y, q.z, q.w};
             d4 xs[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
-                xs[u] = pos[k0 + u < nn ? jj[u] : ii];
+            for (int u = 0; u < 4; ++u)                 // padded rows: whole groups of 4
+                xs[u] = pos[kPadLists ? jj[u] : (k0 + u < nn ? jj[u] : ii)];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                if (k0 + u >= nn)
+                if (!kPadLists && k0 + u >= nn)
                     break;
                 const d4 xj = xs[u];
                 const int tj = species_of(xj.w);
@@ -566,7 +566,7 @@ __device__ __forceinline__ void pair_forces(const KArgs &a, const Rep &rp, int p
                 const double dy = sep_d(xi.y, xj.y, rp.L, rp.invL);
                 const double dz = sep_d(xi.z, xj.z, rp.L, rp.invL);
                 const double r2 = dx * dx + dy * dy + dz * dz;
-                if (r2 < pr.rc2[tj]) {
+                if (r2 < pr.rc2[tj] && r2 > 0.0) {          // r2 = 0: the padding entry
                     const double ir2 = 1.0 / r2;
                     const double s2 = pr.sig2[tj] * ir2;
                     const double s6 = s2 * s2 * s2;
@@ -668,7 +668,7 @@ __device__ __forceinline__ void pair_forces(const KArgs &a, const Rep &rp, int p
             int4 Qs[kUnr];
 #pragma unroll
             for (int u = 0; u < kUnr; ++u) {
-                // rows are padded with the particle itself up to a multiple of 4
+                // rows are padded with the particle itself up to a multiple of kUnr
                 const int j = kPadLists ? jj[u] : (k0 + u < nn ? jj[u] : ii);
                 if constexpr (P == MIXED)
                     Qs[u] = __ldg(qp + j);
@@ -1809,9 +1809,9 @@ __global__ void __launch_bounds__(kNbBlock) k_nbuild(KArgs a)
         for (int o = tid; o < nown; o += kNbBlock) {
             const int cnt = s_cnt[o];
             a.nnbr[ob + o] = cnt < a.K ? cnt : a.K;
-            // pad the row with the particle itself to a multiple of 4 entries, so the
-            // pair loop reads whole 16-byte groups without masking (K is a multiple of 8)
-            for (int k = cnt; k < ((cnt + 3) & ~3) && k < a.K; ++k)
+            // pad the row with the particle itself to a multiple of kUnr entries, so the
+            // pair loop reads whole groups without masking (K is a multiple of 8)
+            for (int k = cnt; k < (cnt + kUnr - 1) / kUnr * kUnr && k < a.K; ++k)
                 a.nbr[(size_t)(ob + o) * (size_t)a.K + k] = ob + o;
             atomicMax(&ctl->max_nbr, cnt);
             if (cnt > a.K)

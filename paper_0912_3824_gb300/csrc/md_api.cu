@@ -125,6 +125,29 @@ int auto_capacity(const md_params *p, const Geometry &g, const std::vector<doubl
     return std::max(k, 32);
 }
 
+// Launch order of the force-kernel chunks.  A launch that fits in one wave
+// hands its blocks to the SMs in turns, so blocks p, p + nsm, p + 2 nsm, ...
+// share an SM; giving them consecutive chunks (neighbouring cells along the
+// cell curve) lets one SM's blocks share the neighbour positions they gather
+// in its L1.  Block p carries its chunk index in w, where its partial sums go,
+// so the per-replica sums keep their order.
+static std::vector<int4> sm_block_order(const std::vector<int4> &chunks, int nsm)
+{
+    const int nb = (int)chunks.size();
+    std::vector<int4> out(chunks);
+    for (int c = 0; c < nb; ++c)
+        out[c].w = c;
+    if (nsm <= 1 || nb <= nsm)
+        return out;
+    int c = 0;
+    for (int s = 0; s < nsm; ++s)
+        for (int p = s; p < nb; p += nsm, ++c) {
+            out[p] = chunks[c];
+            out[p].w = c;
+        }
+    return out;
+}
+
 // Returns MD_OK or MD_E_INVAL with *msg set.
 int make_geometry(const md_params *p, int R, const int64_t *nrep, const double *box, Geometry &g,
                   std::string &msg)
@@ -880,6 +903,9 @@ static int create_impl(md_handle *h, const md_params *p, const int32_t *species,
     if (a.hdtm_hi[0] == 0.0f)
         return fail(h, MD_E_INVAL, "dt / (2 m) underflows single precision");
 
+    int dev = 0, nsm = 0;
+    CK(h, cudaGetDevice(&dev));
+    CK(h, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     // pinned staging, events
     CK(h, cudaEventCreateWithFlags(&h->ev_stage, cudaEventDisableTiming));
     CK(h, cudaEventCreate(&h->ev_f0));
@@ -900,9 +926,10 @@ static int create_impl(md_handle *h, const md_params *p, const int32_t *species,
             q += align_up(bytes);
             return e == cudaSuccess ? MD_OK : cuda_fail(h, e, "table upload");
         };
+        const std::vector<int4> bf = sm_block_order(g.blk_f, nsm);
         if ((rc = put(L.off_rep, g.rep.data(), sizeof(mdk::Rep) * g.R)) ||
             (rc = put(L.off_blk_i, g.blk_i.data(), sizeof(int4) * g.nblk_i)) ||
-            (rc = put(L.off_blk_f, g.blk_f.data(), sizeof(int4) * g.nblk_f)) ||
+            (rc = put(L.off_blk_f, bf.data(), sizeof(int4) * g.nblk_f)) ||
             (rc = put(L.off_crank, g.crank.data(), sizeof(int) * g.ncell)) ||
             (rc = put(L.off_cxyz, g.cxyz.data(), sizeof(int4) * g.ncell)))
             return rc;

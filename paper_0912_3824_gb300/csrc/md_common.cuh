@@ -99,7 +99,8 @@ struct KArgs {
     const int *crank;                 // [global linear cell] -> global sorted cell id
     const int4 *cxyz;                 // [global sorted cell id] -> cx, cy, cz, replica
     int *nbr, *nnbr;
-    const int4 *blk_i, *blk_f;        // per block: first particle, end, replica
+    const int4 *blk_i, *blk_f;        // per block: first particle, end, replica (blk_f: + its
+                                      // chunk index, the slot of its partial sums)
     double *part_f, *part_i;          // per-block partial sums [nblk_f][12], [nblk_i][4]
     Obs *ring, *totals;
     Ctl *ctl;

@@ -912,7 +912,7 @@ __device__ __forceinline__ void force_only(const KArgs &a)
         if (threadIdx.x == 0)
 #pragma unroll
             for (int k = 0; k < kPartF; ++k)
-                a.part_f[(size_t)blockIdx.x * kPartF + k] = acc[k];
+                a.part_f[(size_t)b.w * kPartF + k] = acc[k];
     }
 }
 
@@ -1238,7 +1238,7 @@ __global__ void __launch_bounds__(kForceBlock) k_step(KArgs a)
         if (sample)
 #pragma unroll
             for (int k = 0; k < kPartF; ++k)
-                a.part_f[(size_t)blockIdx.x * kPartF + k] = part[k];
+                a.part_f[(size_t)a.blk_f[blockIdx.x].w * kPartF + k] = part[k];
         if (d2 > 0.f)
             atomicMax(&ctl->maxdisp2, __float_as_uint(d2));
         if (v2 > 0.f)

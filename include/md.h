@@ -143,8 +143,6 @@ typedef struct md_handle md_handle;
  * use_graph = 1, reorder = 1.  Returns MD_OK, or MD_E_INVAL if p is NULL. */
 int md_params_default(md_params *p);
 
-/* Device workspace needed for n_replicas systems with n_per_replica[r]
- * particles in cubic boxes of edge box[r].  Writes *bytes. */
 /* Host-only: the order of the cells of replica 0 in memory.  rank[lin] (for
  * lin = x + nc (y + nc z), caller array of nc^3 entries, may be NULL) is the
  * position of cell (x, y, z) along the chosen curve; *cells_per_edge = nc.
@@ -152,6 +150,8 @@ int md_params_default(md_params *p);
 int md_cell_order(const md_params *p, int32_t n_replicas, const int64_t *n_per_replica, const double *box,
                   int32_t *rank, int32_t *cells_per_edge);
 
+/* Device workspace needed for n_replicas systems with n_per_replica[r]
+ * particles in cubic boxes of edge box[r].  Writes *bytes. */
 int md_workspace_size(const md_params *p, int32_t n_replicas,
                       const int64_t *n_per_replica, const double *box, size_t *bytes);
 

@@ -61,7 +61,7 @@ struct Geometry {
 struct Layout {
     size_t off_ctl, off_rep, off_blk_i, off_blk_f, off_crank, off_cxyz;
     size_t off_pa, off_pb, off_va, off_vb, off_pa2, off_pb2, off_va2, off_vb2, off_qa, off_qb, off_force;
-    size_t off_rref, off_image, off_image2, off_key, off_tmpidx, off_cellof;
+    size_t off_rref, off_image, off_image2, off_key, off_tmpidx;
     size_t off_ccount, off_ccursor, off_cstart, off_nbr, off_nnbr, off_part_f, off_part_i;
     size_t off_ring, off_totals, off_scale, off_st_pos, off_st_vel, off_st_img, off_st_code;
     size_t off_st_f, off_st_e, total;
@@ -329,7 +329,6 @@ Layout make_layout(const md_params *p, const Geometry &g)
     L.off_image2 = take(16 * n);
     L.off_key = take(4 * n);
     L.off_tmpidx = take(4 * n);
-    L.off_cellof = take(4 * n);
     L.off_ccount = take(4 * (size_t)g.ncell);
     L.off_ccursor = take(4 * (size_t)g.ncell);
     L.off_cstart = take(4 * ((size_t)g.ncell + 1));
@@ -832,7 +831,6 @@ static int create_impl(md_handle *h, const md_params *p, const int32_t *species,
     a.image2 = (int4 *)(w + L.off_image2);
     a.key = (int *)(w + L.off_key);
     a.tmpidx = (int *)(w + L.off_tmpidx);
-    a.cellof = (int *)(w + L.off_cellof);
     a.ccount = (int *)(w + L.off_ccount);
     a.ccursor = (int *)(w + L.off_ccursor);
     a.cstart = (int *)(w + L.off_cstart);

@@ -95,7 +95,7 @@ struct KArgs {
     void *force;                      // float4 (MIXED, FP32) or d4 (FP64): f.xyz, e_i in w
     float4 *rref;                     // positions at the last list build
     int4 *image, *image2;             // image counters (w = original index), by state_par
-    int *key, *ccount, *cstart, *ccursor, *tmpidx, *cellof;
+    int *key, *ccount, *cstart, *ccursor, *tmpidx;
     const int *crank;                 // [global linear cell] -> global sorted cell id
     const int4 *cxyz;                 // [global sorted cell id] -> cx, cy, cz, replica
     int *nbr, *nnbr;

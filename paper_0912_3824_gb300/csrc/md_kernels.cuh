@@ -1572,7 +1572,6 @@ __global__ void __launch_bounds__(kIntBlock) k_permute(KArgs a)
         a.rref[d] = make_float4(x.x, x.y, x.z, 0.f);
     }
     img_of(a, spar ^ 1)[d] = img_of(a, spar)[i];
-    a.cellof[d] = k;
 }
 
 // ---------------------------------------------------------------------------

@@ -501,10 +501,28 @@ def test_full_size_step_kernel_trajectory_ka65536(md, ka65536_reference, prec, t
     assert np.allclose(obs["e_kin"], rec["e_kin"], rtol=1e-6 if prec == "mixed" else 1e-12)
 
 
+def _near_cutoff(params, box, species, pos, rel=1e-6):
+    """Particles with a partner at |r^2 / r_c,ab^2 - 1| < rel: whether such a pair
+    is inside the cutoff depends on the last rounding of r^2, so single and
+    double precision may both be right and still disagree (the force jumps by
+    F(r_c) there); the comparison leaves these particles out.  rel = 1e-6 is
+    several times the single-precision rounding of r^2 (about 3e-7)."""
+    from scipy.spatial import cKDTree
+    rc = np.asarray(params["rcut"], dtype=np.float64)
+    x = np.mod(pos, box)
+    pr = cKDTree(x, boxsize=box).query_pairs(rc.max() * (1 + 1e-3), output_type="ndarray")
+    d = x[pr[:, 0]] - x[pr[:, 1]]
+    d -= box * np.rint(d / box)
+    near = np.abs((d * d).sum(1) / rc[species[pr[:, 0]], species[pr[:, 1]]] ** 2 - 1.0) < rel
+    return set(pr[near].ravel().tolist())
+
+
 def test_full_size_replica_ensemble_sampled(md):
     """The 256-replica ensemble (N_r uniform in 500..8000, seed 4) in one handle:
     after 20 steps, six replicas (first, last and four drawn at random) equal
-    their own oracle runs particle by particle."""
+    their own oracle runs particle by particle (particles that met a pair at
+    the cutoff within rounding are left out, see _near_cutoff)."""
+    pytest.importorskip("scipy")
     sizes = synth.ensemble_sizes(256, 500, 8000, seed=4)
     reps = [synth.ka_mixture(n=m, temperature=0.8, seed=4000 + r) for r, m in enumerate(sizes)]
     cat = lambda f: np.concatenate([getattr(r, f) for r in reps])
@@ -517,10 +535,16 @@ def test_full_size_replica_ensemble_sampled(md):
     pick = [0, 255] + list(np.random.default_rng(1).choice(np.arange(1, 255), 4, replace=False))
     for r in pick:
         q = reps[r]
-        rp, rv, ri, _, _ = oracle.vv_run(q.params, q.box, q.species, q.pos, q.vel, q.image, 0.001, 20)
+        rp, rv, ri = q.pos, q.vel, q.image
+        skip = _near_cutoff(q.params, q.box, q.species, rp)
+        for _ in range(20):
+            rp, rv, ri, _, _ = oracle.vv_run(q.params, q.box, q.species, rp, rv, ri, 0.001, 1)
+            skip |= _near_cutoff(q.params, q.box, q.species, rp)
+        keep = np.setdiff1d(np.arange(q.n), np.fromiter(skip, dtype=np.int64, count=len(skip)))
+        assert len(keep) >= q.n - 40
         sl = slice(start[r], start[r + 1])
-        assert np.abs((pos[sl] + img[sl] * q.box) - (rp + ri * q.box)).max() < 1e-6
-        assert np.abs(vel[sl] - rv).max() < 1e-5
+        assert np.abs((pos[sl] + img[sl] * q.box) - (rp + ri * q.box))[keep].max() < 1e-6
+        assert np.abs(vel[sl] - rv)[keep].max() < 1e-5
     sim.close()
 
 

@@ -1636,15 +1636,16 @@ __device__ __forceinline__ float3 nb_coords(float4 w, const Rep &rp)
         return make_float3(w.x, w.y, w.z);
 }
 
-// squared minimum-image distance of two staged words
+// squared minimum-image distance of two staged words; for the fixed-point
+// words in units of the grid (qunit^2), which the caller's radii are scaled to
 template <int P>
 __device__ __forceinline__ float nb_r2(float4 u, float4 w, const Rep &rp)
 {
     float ex, ey, ez;
     if constexpr (P == MIXED && kNbFixed) {
-        ex = sep_q(__float_as_uint(u.x), __float_as_uint(w.x), rp.qunit);
-        ey = sep_q(__float_as_uint(u.y), __float_as_uint(w.y), rp.qunit);
-        ez = sep_q(__float_as_uint(u.z), __float_as_uint(w.z), rp.qunit);
+        ex = __int2float_rn((int)(__float_as_uint(u.x) - __float_as_uint(w.x)));
+        ey = __int2float_rn((int)(__float_as_uint(u.y) - __float_as_uint(w.y)));
+        ez = __int2float_rn((int)(__float_as_uint(u.z) - __float_as_uint(w.z)));
     } else {
         ex = sep_f(u.x, w.x, rp.Lhi, rp.invLf);
         ey = sep_f(u.y, w.y, rp.Lhi, rp.invLf);
@@ -1716,6 +1717,8 @@ __global__ void __launch_bounds__(kNbBlock) k_nbuild(KArgs a)
                 ccz = ((float)cc.z + 0.5f) * edge;
     const float rlmax2 = fmaxf(fmaxf(a.tab.rl2[0], a.tab.rl2[1]), fmaxf(a.tab.rl2[2], a.tab.rl2[3]));
     const unsigned lt_mask = (1u << lane) - 1u;
+    // nb_r2 of the fixed-point words is in units of qunit^2: the list radii follow
+    const float r2unit = (P == MIXED && kNbFixed) ? 1.0f / (rp.qunit * rp.qunit) : 1.0f;
 
     for (int ob = c0; ob < c1; ob += kNbOwn) {
         const int nown = min(kNbOwn, c1 - ob);
@@ -1774,8 +1777,8 @@ __global__ void __launch_bounds__(kNbBlock) k_nbuild(KArgs a)
                     const bool ok = o0 + p < nown;
                     H[p] = nb_word<P>(a, pn, ob + (ok ? o0 + p : 0));
                     const int ti = nb_species<P>(H[p]);
-                    rl0[p] = ok ? a.tab.rl2[ti * 2] : -1.0f;       // -1: nothing passes
-                    rl1[p] = ok ? a.tab.rl2[ti * 2 + 1] : -1.0f;
+                    rl0[p] = ok ? a.tab.rl2[ti * 2] * r2unit : -1.0f;       // -1: nothing passes
+                    rl1[p] = ok ? a.tab.rl2[ti * 2 + 1] * r2unit : -1.0f;
                     cnt[p] = ok ? s_cnt[o0 + p] : 0;
                 }
                 for (int s0 = 0; s0 < staged; s0 += 32) {

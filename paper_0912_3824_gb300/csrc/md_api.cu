@@ -4,7 +4,7 @@
 // the per-replica tables there, and drives the kernels on the caller's stream.
 // md_step() runs as one CUDA graph:
 //
-//   integrate(FIRST) -> IF(rebuild){bin, scan, scatter, permute, nbuild, flip}
+//   integrate(FIRST) -> IF(rebuild){bin, scan, scatter, permute, nbuild}
 //     -> WHILE(loop){ step x kCheck -> IF(rebuild){...} -> step x kCheck -> IF ... }
 //
 // with kUnroll step kernels per loop iteration and a rebuild check after every
@@ -437,9 +437,8 @@ int rebuild_chain(const md_handle *h, ChainStep *seq)
     seq[1] = {k.scan, 1, kScanBlock};
     seq[2] = {k.scatter, nb, kIntBlock};
     seq[3] = {k.permute, nb, kIntBlock};
-    seq[4] = {k.nbuild, h->g.ncell, kNbBlock};          // one block per cell
-    seq[5] = {k.flip, std::max(1, grid_n(h->g.ncell, kIntBlock)), kIntBlock};
-    return 6;
+    seq[4] = {k.nbuild, h->g.ncell, kNbBlock};          // one block per cell; its last block
+    return 5;                                            // makes the permuted buffers current
 }
 
 int launch_rebuild(md_handle *h)

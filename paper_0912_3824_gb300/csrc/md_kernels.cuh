@@ -1215,9 +1215,13 @@ __global__ void __launch_bounds__(kForceBlock) k_step(KArgs a)
     const long long step = ctl->step;
     const long long remaining = ctl->remaining;
     const int pp = ctl->pos_par, spar = ctl->state_par;
+    // The status word can change while the launch runs (another block's atomicOr),
+    // so threads of one block may read different values: it gates only per-particle
+    // work.  Everything that shapes the block's barriers and the lanes' shuffles
+    // (sample) depends on fields that change only in the last block.
     const bool active = st0 == 0u && remaining > 0;
     const bool last = remaining == 1;
-    const bool sample = active && (step % a.si) == 0;
+    const bool sample = remaining > 0 && (step % a.si) == 0;
     if (threadIdx.x == 0)                       // device timing of this launch: earliest start
         atomicMax(&ctl->t_first_inv, ~global_ns());
 
@@ -1416,8 +1420,9 @@ __global__ void __launch_bounds__(kIntBlock) k_integrate(KArgs a)
 // along a space-filling curve (the periodic reorder of Sec. 2.2).
 // Kernels: k_bin (cell key + histogram) -> k_scan -> k_scatter ->
 // k_permute (deterministic order inside a cell; gather of the state into the
-// other buffers) -> k_nbuild (lists from the permuted positions) -> k_flip.
-// Each returns at once unless a rebuild is pending.
+// other buffers) -> k_nbuild (lists from the permuted positions; its last
+// block makes the permuted buffers current).  Each returns at once unless a
+// rebuild is pending; k_scan clears the histogram for the next binning.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ bool rebuild_pending(const Ctl *ctl)
 {
@@ -1511,6 +1516,7 @@ __global__ void __launch_bounds__(kScanBlock) k_scan(KArgs a)
     for (int s = s0; s < s1; ++s) {
         a.cstart[s] = base;
         base += a.ccount[s];
+        a.ccount[s] = 0;          // ready for the next binning
         a.ccursor[s] = 0;
     }
     if (t == T - 1)
@@ -1660,8 +1666,10 @@ __device__ __forceinline__ float box_gap(float x, float c, float h, float L, flo
     return fmaxf(fabsf(sep_f(x, c, L, invL)) - h, 0.0f);
 }
 
+// Lists of the particles of cell blockIdx.x, from the positions in buffer pn
+// (the permuted copy being built).
 template <int P>
-__global__ void __launch_bounds__(kNbBlock) k_nbuild(KArgs a)
+__device__ __forceinline__ void nbuild_cell(const KArgs &a, int pn)
 {
     __shared__ float4 s_pos[kNbCap];
     __shared__ int s_idx[kNbCap];
@@ -1671,16 +1679,9 @@ __global__ void __launch_bounds__(kNbBlock) k_nbuild(KArgs a)
     __shared__ int s_wsum[kNbBlock / 32];
 
     Ctl *ctl = a.ctl;
-    if (!rebuild_pending(ctl))
-        return;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        atomicAdd((unsigned long long *)&ctl->n_rebuild_k, 1ull);
-        atomicAdd((unsigned long long *)&ctl->rebuilds, 1ull);
-    }
     const int c = blockIdx.x;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     constexpr int NW = kNbBlock / 32;
-    const int pn = ctl->pos_par ^ 1;
     const int4 cc = a.cxyz[c];
     const Rep rp = a.rep[cc.w];
     const int nc = rp.nc;
@@ -1816,36 +1817,49 @@ __global__ void __launch_bounds__(kNbBlock) k_nbuild(KArgs a)
             for (int k = cnt; k < (cnt + kUnr - 1) / kUnr * kUnr && k < a.K; ++k)
                 a.nbr[(size_t)(ob + o) * (size_t)a.K + k] = ob + o;
             atomicMax(&ctl->max_nbr, cnt);
-            if (cnt > a.K)
+            if (cnt > a.K) {
                 atomicOr(&ctl->status, ST_OVERFLOW);
+                __threadfence();            // performed before this block's ticket
+            }
         }
         __syncthreads();
     }
 }
 
-// End of a rebuild: the permuted buffers become current; clear the histogram.
+// The neighbour build closes the rebuild chain: the last block to finish (ticket
+// pattern) makes the permuted buffers current, unless a list overflowed.  The
+// pending check is read once per block (the status can change during the
+// launch) and every block takes a ticket.
 template <int P>
-__global__ void __launch_bounds__(kIntBlock) k_flip(KArgs a)
+__global__ void __launch_bounds__(kNbBlock) k_nbuild(KArgs a)
 {
+    __shared__ int s_go;
     Ctl *ctl = a.ctl;
-    if (!rebuild_pending(ctl))
-        return;
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    for (int c = t; c < a.ncell; c += gridDim.x * blockDim.x)
-        a.ccount[c] = 0;
-    if (t == 0) {
-        ctl->pos_par ^= 1;
-        ctl->state_par ^= 1;
-        atomicAdd((unsigned long long *)&ctl->n_rebuild_k, 1ull);
+    if (threadIdx.x == 0)
+        s_go = rebuild_pending(ctl) ? 1 : 0;
+    __syncthreads();
+    if (s_go) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            atomicAdd((unsigned long long *)&ctl->n_rebuild_k, 1ull);
+            atomicAdd((unsigned long long *)&ctl->rebuilds, 1ull);
+        }
+        nbuild_cell<P>(a, ctl->pos_par ^ 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        // (the last block reads nothing the others wrote but the status word, an
+        // atomic, which an overflowing thread fenced before the barrier above)
+        const unsigned int t = atomicAdd(&ctl->ticket, 1u);
+        if (t == gridDim.x - 1) {
+            if (ctl->rebuild != 0u && atomicOr(&ctl->status, 0u) == 0u) {
+                ctl->pos_par ^= 1;
+                ctl->state_par ^= 1;
+            }
+            ctl->ticket = 0u;
+        }
     }
 }
 
-// ---------------------------------------------------------------------------
-// state transfer between the staging area (original order, float64) and the
-// working layout; misc. control kernels
-// ---------------------------------------------------------------------------
-// Load the staged state into the current buffers in the original order, wrap
-// into [0, L), split into the precision's representation, request a rebuild.
 template <int P>
 __global__ void __launch_bounds__(kIntBlock) k_load(KArgs a)
 {
@@ -2215,7 +2229,6 @@ KernelSet make_kernel_set()
     k.scatter = (const void *)k_scatter<P>;
     k.permute = (const void *)k_permute<P>;
     k.nbuild = (const void *)k_nbuild<P>;
-    k.flip = (const void *)k_flip<P>;
     k.load = (const void *)k_load<P>;
     k.getstate = (const void *)k_getstate<P>;
     k.expforce = (const void *)k_expforce<P>;

@@ -378,6 +378,35 @@ def test_capacity_overflow_is_reported(md):
     assert ei.value.code == md.MD_E_CAPACITY
 
 
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_overflow_during_run_keeps_the_last_consistent_state(md, use_graph):
+    """A list capacity that fits the start but not the heated liquid: the step
+    loop stops at the rebuild that overflows, MD_E_CAPACITY is reported, and the
+    buffers stay those of the last completed step (the build's last block does
+    not make the half-written permutation current), so the positions equal
+    those of an unconstrained run after the same number of steps."""
+    s = _melted(synth.ka_params(), 2000, 1.2, 1.0)     # longest list 112 at the start, on a
+    probe = _sim(md, s, "mixed")                        # multiple of 8: no slack in the capacity
+    cap = (probe.info()["max_neighbours"] + 7) // 8 * 8
+    probe.close()
+    sim = _sim(md, s, "mixed", dt=0.002, neigh_capacity=cap, use_graph=use_graph)
+    sim.rescale(2.0)
+    sim.step(3000)
+    assert sim.sync() == md.MD_E_CAPACITY
+    k = sim.info()["step"]
+    assert 0 < k < 3000
+    pos, _, img = sim.get_state()
+    sim.close()
+    ref = _sim(md, s, "mixed", dt=0.002, use_graph=use_graph)
+    ref.rescale(2.0)
+    ref.step(k)
+    assert ref.sync() == md.MD_OK
+    rp, _, ri = ref.get_state()
+    ref.close()
+    assert np.isfinite(pos).all()
+    assert np.array_equal(pos + img * s.box, rp + ri * s.box)
+
+
 def test_instability_is_reported_and_state_kept(md):
     s = _system("lj", 864)
     sim = _sim(md, s, "fp64", dt=50.0)

@@ -477,6 +477,17 @@ def lj_cases(args, local, cases, workload, temperature, dt, skin):
         sim = md.System.from_synth(s, dt=dt, skin=skin, precision=md.PRECISIONS[args.precision],
                                    sample_interval=100, device=device, threads_per_particle=args.tpp)
         equilibrate(sim, max(1.5, temperature), temperature, melt_blocks=5, final_blocks=5)
+        trials = None
+        if not args.no_tune:
+            # lanes per particle from the autotuner; the skin is the workload's own
+            from paper_0912_3824_gb300 import tune
+            pos0, vel0, img0 = sim.get_state()
+            base = md.make_params(s.params, dt, skin=skin, precision=md.PRECISIONS[args.precision],
+                                  sample_interval=100, threads_per_particle=args.tpp)
+            base, trials = tune.autotune(base, [s.n], [s.box], s.species, pos0, vel0, img0, device=device,
+                                         skins=(skin,))
+            sim.close()
+            sim = md.System(base, [s.n], [s.box], s.species, pos0, vel0, img0, device=device)
         sim.step(args.inner)                       # warm-up, graph captured
         assert sim.sync() == md.MD_OK
         sim.observables()
@@ -500,7 +511,9 @@ def lj_cases(args, local, cases, workload, temperature, dt, skin):
                 "mean_list": float(n_list), "mean_in_cutoff": float(n_cut),
                 "neigh_capacity": info1["neigh_capacity"], "threads_per_particle": info1["threads_per_particle"],
                 "alu_tflops_whole_step": flops / t_step / 1e12,
-                "hbm_algorithmic_gbs_whole_step": hbm / t_step / 1e9, "clocks": clk}
+                "hbm_algorithmic_gbs_whole_step": hbm / t_step / 1e9, "clocks": clk,
+                "autotune": [{k: (round(v, 5) if isinstance(v, float) else v) for k, v in t.items()}
+                             for t in trials] if trials else None}
         if n <= 32768 and not args.no_extras:
             pos, vel, img = sim.get_state()
             line["cpu_baseline"] = cpu_baseline(s, pos, vel, img, budget_s=5.0, dt=dt)

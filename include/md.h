@@ -98,7 +98,13 @@ typedef struct {
                                  (h sigma_ab), which makes it and its first two derivatives
                                  vanish at r_c; 0 = no smoothing (the paper uses h = 0.005).
                                  Not supported by md_forces_noalloc.                           */
-    int32_t reserved[4];      /* must be zero                                                   */
+    int32_t check_interval;   /* MD steps between the rebuild checks of md_step's CUDA graph:
+                                 1, 2, 4, 8 or 16; 0 = automatic (4 below 262,144 particles, 1
+                                 from there).  Between checks the rebuild decision adds a bound
+                                 on how far particles can still move (speed and acceleration
+                                 over the unchecked steps), so a longer interval rebuilds
+                                 earlier; a check costs one conditional graph node           */
+    int32_t reserved[3];      /* must be zero                                                   */
 } md_params;
 
 /* one sample of the reductions of Sec. 2.2, per replica */
@@ -134,6 +140,8 @@ typedef struct {
                                  that advanced a step (first block start to last block end,
                                  read from the GPU's global timer)                              */
     int64_t step_device_launches; /* launches summed into step_device_ms (one per MD step)      */
+    int32_t check_interval;   /* MD steps between rebuild checks, as resolved                   */
+    int32_t reserved;
 } md_info_t;
 
 typedef struct md_handle md_handle;

@@ -5,12 +5,13 @@
 // md_step() runs as one CUDA graph:
 //
 //   integrate(FIRST) -> IF(rebuild){bin, scan, scatter, permute, nbuild}
-//     -> WHILE(loop){ step x kCheck -> IF(rebuild){...} -> step x kCheck -> IF ... }
+//     -> WHILE(loop){ step x c -> IF(rebuild){...} -> step x c -> IF ... }
 //
 // with kUnroll step kernels per loop iteration and a rebuild check after every
-// kCheck of them.  The last block of each kernel sets the conditions on the
-// device (rebuild when the displacement since the last build, plus a bound on
-// the motion until the next check, could exceed skin/2; loop while steps
+// c of them (the check interval).  The last block of each kernel sets the
+// conditions on the device (rebuild when the displacement since the last
+// build, plus a bound on the motion until the next check, could exceed
+// skin/2; loop while steps
 // remain), so a whole md_step of n steps is one graph launch with no host
 // round trip.  Conditional nodes cost microseconds each on this hardware,
 // which is why the loop is unrolled and the check is spaced.  With
@@ -41,7 +42,10 @@ constexpr size_t kAlign = 256;
 constexpr int kIntBlock = 256, kForceBlock = 128, kNbBlock = 256, kScanBlock = 1024;
 constexpr double kCellMargin = 1e-3;   // cell edge exceeds the largest list radius by this
 constexpr int kUnroll = 16;            // step kernels per loop iteration of the graph
-constexpr int kCheck = 4;              // rebuild check after every kCheck steps (divides kUnroll)
+constexpr int kCheck = 4;              // automatic check interval below kCheckLargeN particles
+constexpr int64_t kCheckLargeN = 262144;   // from here a check after every step: the conditional
+                                           // node costs little against the step, the earlier
+                                           // rebuilds of a long interval cost more
 
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
@@ -50,6 +54,7 @@ struct Geometry {
     int R = 0;
     int64_t n = 0;
     int K = 0, tpp = 8, ppb_f = 32;
+    int check = kCheck;                 // MD steps between rebuild checks of the graph
     int nblk_i = 0, nblk_f = 0, ncell = 0;
     double rl_max = 0.0;
     std::vector<mdk::Rep> rep;
@@ -126,18 +131,20 @@ int auto_capacity(const md_params *p, const Geometry &g, const std::vector<doubl
 }
 
 // Launch order of the force-kernel chunks.  A launch that fits in one wave
-// hands its blocks to the SMs in turns, so blocks p, p + nsm, p + 2 nsm, ...
-// share an SM; giving them consecutive chunks (neighbouring cells along the
-// cell curve) lets one SM's blocks share the neighbour positions they gather
-// in its L1.  Block p carries its chunk index in w, where its partial sums go,
-// so the per-replica sums keep their order.
-static std::vector<int4> sm_block_order(const std::vector<int4> &chunks, int nsm)
+// (at most `resident` blocks) hands its blocks to the SMs in turns, so blocks
+// p, p + nsm, p + 2 nsm, ... share an SM; giving them consecutive chunks
+// (neighbouring cells along the cell curve) lets one SM's blocks share the
+// neighbour positions they gather in its L1.  A longer launch keeps the chunk
+// order, so that the blocks resident at any time cover one compact region.
+// Block p carries its chunk index in w, where its partial sums go, so the
+// per-replica sums keep their order.
+static std::vector<int4> sm_block_order(const std::vector<int4> &chunks, int nsm, int resident)
 {
     const int nb = (int)chunks.size();
     std::vector<int4> out(chunks);
     for (int c = 0; c < nb; ++c)
         out[c].w = c;
-    if (nsm <= 1 || nb <= nsm)
+    if (nsm <= 1 || nb <= nsm || nb > resident)
         return out;
     int c = 0;
     for (int s = 0; s < nsm; ++s)
@@ -167,8 +174,15 @@ int make_geometry(const md_params *p, int R, const int64_t *nrep, const double *
         return MD_E_INVAL;
     }
     if (p->reserved0 != 0) { msg = "reserved fields must be zero"; return MD_E_INVAL; }
-    for (int k = 0; k < 4; ++k)
+    for (int k = 0; k < 3; ++k)
         if (p->reserved[k] != 0) { msg = "reserved fields must be zero"; return MD_E_INVAL; }
+    {
+        const int ci = p->check_interval;
+        if (ci != 0 && (ci < 1 || ci > kUnroll || (ci & (ci - 1)) || kUnroll % ci)) {
+            msg = "check_interval must be 0 (automatic) or 1, 2, 4, 8 or 16";
+            return MD_E_INVAL;
+        }
+    }
     if (!(p->smooth_h >= 0.0) || !std::isfinite(p->smooth_h)) {
         msg = "smooth_h must be finite and >= 0";
         return MD_E_INVAL;
@@ -295,6 +309,7 @@ int make_geometry(const md_params *p, int R, const int64_t *nrep, const double *
     std::vector<double> bx(box, box + R);
     std::vector<int64_t> nr(nrep, nrep + R);
     g.K = p->neigh_capacity > 0 ? (p->neigh_capacity + 7) / 8 * 8 : auto_capacity(p, g, bx, nr);
+    g.check = p->check_interval > 0 ? p->check_interval : (g.n >= kCheckLargeN ? 1 : kCheck);
     return MD_OK;
 }
 
@@ -458,8 +473,9 @@ KArgs step_args(const md_handle *h, int slot)
 {
     KArgs a = h->a;
     a.imode = mdk::IM_LOOP;
-    const bool check = (slot % kCheck) == kCheck - 1;
-    a.lookahead = check ? kCheck - 1 : 0;
+    const int ci = h->g.check;
+    const bool check = (slot % ci) == ci - 1;
+    a.lookahead = check ? ci - 1 : 0;
     a.set_rebuild = check ? 1 : 0;
     a.set_loop = slot == kUnroll - 1 ? 1 : 0;
     return a;
@@ -469,7 +485,7 @@ KArgs first_args(const md_handle *h)
 {
     KArgs a = h->a;
     a.imode = mdk::IM_FIRST;
-    a.lookahead = kCheck - 1;
+    a.lookahead = h->g.check - 1;
     a.set_rebuild = 1;
     return a;
 }
@@ -561,7 +577,7 @@ int build_graph(md_handle *h)
     cudaGraph_t wbody;
     if ((rc = add_conditional(h, g, &n_while, n_if0, c_loop, cudaGraphCondTypeWhile, &wbody)))
         return rc;
-    // loop body: kUnroll step kernels, a conditional rebuild after every kCheck
+    // loop body: kUnroll step kernels, a conditional rebuild after every g.check
     const void *stepk = h->ks->step[h->p.smooth_h > 0.0][force_index(h->g.tpp)];
     cudaGraphNode_t prev = nullptr;
     for (int slot = 0; slot < kUnroll; ++slot) {
@@ -900,9 +916,11 @@ static int create_impl(md_handle *h, const md_params *p, const int32_t *species,
     if (a.hdtm_hi[0] == 0.0f)
         return fail(h, MD_E_INVAL, "dt / (2 m) underflows single precision");
 
-    int dev = 0, nsm = 0;
+    int dev = 0, nsm = 0, per_sm = 0;
     CK(h, cudaGetDevice(&dev));
     CK(h, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+              &per_sm, h->ks->step[h->p.smooth_h > 0.0][force_index(g.tpp)], kForceBlock, 0));
     // pinned staging, events
     CK(h, cudaEventCreateWithFlags(&h->ev_stage, cudaEventDisableTiming));
     CK(h, cudaEventCreate(&h->ev_f0));
@@ -923,7 +941,7 @@ static int create_impl(md_handle *h, const md_params *p, const int32_t *species,
             q += align_up(bytes);
             return e == cudaSuccess ? MD_OK : cuda_fail(h, e, "table upload");
         };
-        const std::vector<int4> bf = sm_block_order(g.blk_f, nsm);
+        const std::vector<int4> bf = sm_block_order(g.blk_f, nsm, nsm * per_sm);
         if ((rc = put(L.off_rep, g.rep.data(), sizeof(mdk::Rep) * g.R)) ||
             (rc = put(L.off_blk_i, g.blk_i.data(), sizeof(int4) * g.nblk_i)) ||
             (rc = put(L.off_blk_f, bf.data(), sizeof(int4) * g.nblk_f)) ||
@@ -1436,6 +1454,7 @@ int md_info(md_handle *h, md_info_t *out)
     out->n_replicas = h->g.R;
     out->neigh_capacity = h->g.K;
     out->threads_per_particle = h->g.tpp;
+    out->check_interval = h->g.check;
     out->cells_per_edge = h->g.rep[0].nc;
     out->step = c.step;
     out->rebuilds = c.rebuilds;

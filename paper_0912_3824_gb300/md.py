@@ -35,7 +35,7 @@ class md_params(C.Structure):
                 ("sample_interval", C.c_int32), ("obs_capacity", C.c_int32),
                 ("threads_per_particle", C.c_int32), ("use_graph", C.c_int32),
                 ("reorder", C.c_int32), ("reserved0", C.c_int32), ("smooth_h", C.c_double),
-                ("reserved", C.c_int32 * 4)]
+                ("check_interval", C.c_int32), ("reserved", C.c_int32 * 3)]
 
 
 class md_obs(C.Structure):
@@ -51,7 +51,8 @@ class md_info_t(C.Structure):
                 ("kernel_launches", C.c_int64), ("max_neighbours", C.c_int32),
                 ("status", C.c_int32), ("step_ms", C.c_double), ("step_launches", C.c_int64),
                 ("rebuild_ms", C.c_double), ("rebuild_checks", C.c_int64),
-                ("step_device_ms", C.c_double), ("step_device_launches", C.c_int64)]
+                ("step_device_ms", C.c_double), ("step_device_launches", C.c_int64),
+                ("check_interval", C.c_int32), ("reserved", C.c_int32)]
 
 
 OBS_DTYPE = np.dtype([("step", np.int64), ("e_pot", np.float64), ("e_kin", np.float64),
@@ -283,7 +284,8 @@ def md_forces_noalloc(p: md_params, n: int, box: float, species_ptr: int, pos_pt
 # ---------------------------------------------------------------------------
 def make_params(pot: dict, dt: float, skin: float = 0.3, precision: int = MD_PREC_MIXED,
                 sample_interval: int = 100, neigh_capacity: int = 0, threads_per_particle: int = 0,
-                use_graph: bool = True, reorder: int = 1, obs_capacity: int = 0) -> md_params:
+                use_graph: bool = True, reorder: int = 1, obs_capacity: int = 0,
+                check_interval: int = 0) -> md_params:
     p = md_params_default()
     p.n_species = int(pot["n_species"])
     p.shift = 1 if pot.get("shift", True) else 0
@@ -303,6 +305,7 @@ def make_params(pot: dict, dt: float, skin: float = 0.3, precision: int = MD_PRE
     p.use_graph = 1 if use_graph else 0
     p.reorder = int(reorder)          # 0 x-fastest, 1 Morton, 2 Hilbert (True / False: 1 / 0)
     p.obs_capacity = int(obs_capacity)
+    p.check_interval = int(check_interval)   # 0 automatic, else 1, 2, 4, 8, 16
     return p
 
 

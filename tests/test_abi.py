@@ -57,7 +57,8 @@ def test_workspace_size_grows_with_n_and_precision(md):
     assert b > 65536 * 128 * 4
 
 
-@pytest.mark.parametrize("bad", ["box", "dt", "species", "tpp", "sample", "asym", "smooth", "smooth_tpp"])
+@pytest.mark.parametrize("bad", ["box", "dt", "species", "tpp", "sample", "asym", "smooth", "smooth_tpp",
+                                 "check3", "check32"])
 def test_argument_checks(md, bad):
     from paper_0912_3824_gb300 import synth
     pot = synth.ka_params()
@@ -81,6 +82,8 @@ def test_argument_checks(md, bad):
     if bad == "smooth_tpp":              # smoothed kernels exist for 1..8 lanes per particle
         p.smooth_h = 0.005
         p.threads_per_particle = 16
+    if bad in ("check3", "check32"):     # the check interval divides the 16 steps of a graph loop
+        p.check_interval = 3 if bad == "check3" else 32
     with pytest.raises(md.MDError) as ei:
         md.md_workspace_size(p, [1000], [box])
     assert ei.value.code == md.MD_E_INVAL
@@ -102,6 +105,7 @@ def test_params_layout_and_smoothing_field(md):
     from paper_0912_3824_gb300 import synth
     assert ctypes.sizeof(md.md_params) == 192
     assert md.md_params.smooth_h.offset == 168
+    assert md.md_params.check_interval.offset == 176
     assert md.make_params(synth.lj_params(smooth=0.005), 0.001).smooth_h == 0.005
     assert md.make_params(synth.wca_params(), 0.001).rcut[0][0] == synth.WCA_RCUT
 

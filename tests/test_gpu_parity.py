@@ -159,11 +159,15 @@ def _trajectory(md, s, prec, dt, nsteps, sample, **kw):
     return pos, vel, img, obs[:, 0], info
 
 
-@pytest.mark.parametrize("use_graph", [True, False])
-def test_fp64_trajectory_matches_oracle(md, use_graph):
-    """200 velocity-Verlet steps of the LJ fluid (several list rebuilds)."""
+@pytest.mark.parametrize("use_graph,check", [(True, 0), (False, 0), (True, 1), (True, 16)])
+def test_fp64_trajectory_matches_oracle(md, use_graph, check):
+    """200 velocity-Verlet steps of the LJ fluid (several list rebuilds), with
+    the rebuild checked every 4 steps (the automatic interval here), every
+    step, and every 16 steps."""
     s = _system("lj", 864, amp=0.02)
-    pos, vel, img, obs, info = _trajectory(md, s, "fp64", 0.005, 200, 20, use_graph=use_graph)
+    pos, vel, img, obs, info = _trajectory(md, s, "fp64", 0.005, 200, 20, use_graph=use_graph,
+                                           check_interval=check)
+    assert info["check_interval"] == (check or 4)
     rp, rv, ri, _, rec = oracle.vv_run(s.params, s.box, s.species, s.pos, s.vel, s.image, 0.005, 200,
                                        sample=20)
     assert info["rebuilds"] >= 3
@@ -583,6 +587,7 @@ def test_full_size_lj_1m_two_steps(md):
     particle."""
     s = synth.perturb(synth.lj_fluid(n=1048576, density=0.8442, temperature=1.0, seed=3), 0.03, 4)
     pos, vel, img, obs, info = _trajectory(md, s, "mixed", 0.005, 2, 1)
+    assert info["check_interval"] == 1          # automatic from 262,144 particles on
     rp, rv, ri, _, rec = oracle.vv_run(s.params, s.box, s.species, s.pos, s.vel, s.image, 0.005, 2, sample=1)
     assert np.abs((pos + img * s.box) - (rp + ri * s.box)).max() < 1e-6
     assert np.allclose(obs["e_pot"], rec["e_pot"], rtol=1e-6)

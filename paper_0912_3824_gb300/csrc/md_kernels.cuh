@@ -35,6 +35,7 @@ constexpr int kIntBlock = 256;   // per-particle kernels: one thread per particl
 constexpr int kForceBlock = 128; // force / step kernels: tpp threads per particle
 constexpr int kNbBlock = 256;    // neighbour build: one block per cell
 constexpr int kScanBlock = 1024;
+constexpr int kScanPer = 8;      // cell counts per thread and tile of the scan
 constexpr int kPartF = 12;       // doubles per block partial of the force / step kernels
 constexpr int kUnr = 8;          // list entries per lane and iteration of the FP32 pair loops
                                  // (a multiple of 4, at most 8: lists are padded to 8)
@@ -1478,49 +1479,82 @@ __global__ void __launch_bounds__(kIntBlock) k_bin(KArgs a)
 template <int P>
 __global__ void __launch_bounds__(kScanBlock) k_scan(KArgs a)
 {
+    // Exclusive prefix sum of the cell counts (one block), in tiles of
+    // kScanBlock x kScanPer cells: each tile is read and written with coalesced
+    // accesses through shared memory, each thread scans kScanPer consecutive
+    // counts, and the per-thread sums are scanned across the block.  The
+    // counts are cleared for the next binning.
+    constexpr int T = kScanBlock, R = kScanPer;
+    __shared__ int tile[T * R + T * R / 32];      // padded: one word every 32
     __shared__ int wsum[32];
+    __shared__ int s_carry;
     Ctl *ctl = a.ctl;
     if (!rebuild_pending(ctl))
         return;
-    if (threadIdx.x == 0)
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    if (t == 0) {
         atomicAdd((unsigned long long *)&ctl->n_rebuild_k, 1ull);
-    const int n = a.ncell, T = blockDim.x, t = threadIdx.x;
-    const int per = (n + T - 1) / T;
-    const int s0 = min(t * per, n), s1 = min(s0 + per, n);
-    int sum = 0;
-    for (int s = s0; s < s1; ++s)
-        sum += a.ccount[s];
-    const int lane = t & 31, w = t >> 5, nw = T >> 5;
-    int incl = sum;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        int y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o)
-            incl += y;
+        s_carry = 0;
     }
-    if (lane == 31)
-        wsum[w] = incl;
-    __syncthreads();
-    if (w == 0) {
-        int v = lane < nw ? wsum[lane] : 0;
+    const int n = a.ncell;
+    auto at = [](int i) { return i + (i >> 5); };
+    for (int base = 0; base < n; base += T * R) {
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            const int i = base + k * T + t;
+            tile[at(k * T + t)] = i < n ? a.ccount[i] : 0;
+        }
+        __syncthreads();
+        int v[R], sum = 0;
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            v[k] = tile[at(t * R + k)];
+            sum += v[k];
+        }
+        int incl = sum;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            int y = __shfl_up_sync(0xffffffffu, v, o);
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
             if (lane >= o)
-                v += y;
+                incl += y;
         }
-        wsum[lane] = v;
+        if (lane == 31)
+            wsum[w] = incl;
+        __syncthreads();
+        if (w == 0) {
+            int x = lane < T / 32 ? wsum[lane] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o)
+                    x += y;
+            }
+            wsum[lane] = x;                       // inclusive sums of the warps
+        }
+        __syncthreads();
+        const int carry = s_carry;
+        int run = carry + (w > 0 ? wsum[w - 1] : 0) + incl - sum;
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            tile[at(t * R + k)] = run;
+            run += v[k];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            const int i = base + k * T + t;
+            if (i < n) {
+                a.cstart[i] = tile[at(k * T + t)];
+                a.ccount[i] = 0;          // ready for the next binning
+                a.ccursor[i] = 0;
+            }
+        }
+        if (t == 0)
+            s_carry = carry + wsum[T / 32 - 1];
+        __syncthreads();
     }
-    __syncthreads();
-    int base = (w > 0 ? wsum[w - 1] : 0) + incl - sum;
-    for (int s = s0; s < s1; ++s) {
-        a.cstart[s] = base;
-        base += a.ccount[s];
-        a.ccount[s] = 0;          // ready for the next binning
-        a.ccursor[s] = 0;
-    }
-    if (t == T - 1)
-        a.cstart[n] = base;
+    if (t == 0)
+        a.cstart[n] = s_carry;
 }
 
 template <int P>

@@ -40,7 +40,6 @@ constexpr int kPartF = 12;       // doubles per block partial of the force / ste
 constexpr int kUnr = 8;          // list entries per lane and iteration of the FP32 pair loops
                                  // (a multiple of 4, at most 8: lists are padded to 8)
 constexpr int kPfDepth = 1;      // iterations ahead at which the list indices are loaded
-constexpr bool kPadLists = true; // list rows padded with the particle itself (no masks in the loop)
 constexpr bool kSplitUpdate = false; // below 4 lanes: one lane updates (measured faster than sharing)
 
 // ---------------------------------------------------------------------------
@@ -516,21 +515,22 @@ __device__ __forceinline__ unsigned int need_rebuild(const KArgs &a, float md2, 
 // ---------------------------------------------------------------------------
 // pair forces over the neighbour list (Sec. 2.2), 12-6 potential cut (and
 // shifted) at r_c,ab (Sec. 3, Sec. 5).  TPP threads share one particle; each
-// lane takes 4 consecutive list entries at a time (one 16-byte load) and
-// issues their gathers together.  Single precision: the 4 contributions are
+// lane takes groups of consecutive list entries (16-byte index loads) and
+// issues their gathers together.  List rows are padded with the particle
+// itself to whole groups of 8 (r^2 = 0 exactly: never inside), so the loops
+// carry no end-of-row masks.  Single precision: a group's contributions are
 // summed branch-free (zero factor outside the cutoff) and the group sum enters
 // a Kahan accumulator (MIXED; plain sum for FP32); lanes are combined in
-// double-single.  Energies and the virial are accumulated on sample steps only.
-// On return every lane of the particle holds the total force; acc[] (SAMPLE)
-// holds the particle's share of E_pot, W and W_ab.
+// double-single.  On return every lane of the particle holds the total force;
+// the energies and the virial come from pair_energy on sample steps.
 // ---------------------------------------------------------------------------
 template <typename T> struct PairRow {   // parameters of (species i, species j = 0 / 1)
     T rc2[2], sig2[2], eps4[2], eps48[2], shift[2], rc[2], ihs[2];
 };
 
-template <int P, int TPP, bool SAMPLE, bool SM>
+template <int P, int TPP, bool SM>
 __device__ __forceinline__ void pair_forces(const KArgs &a, const Rep &rp, int pp, int ii, int nn,
-                                            FT<P> &fx, FT<P> &fy, FT<P> &fz, double *acc)
+                                            FT<P> &fx, FT<P> &fy, FT<P> &fz)
 {
     const int lane = threadIdx.x & (TPP - 1);
     const int *lst = a.nbr + (size_t)ii * (size_t)a.K;
@@ -549,18 +549,16 @@ __device__ __forceinline__ void pair_forces(const KArgs &a, const Rep &rp, int p
             pr.rc[tj] = a.tab.rcd[ti * 2 + tj];
             pr.ihs[tj] = a.tab.ihsd[ti * 2 + tj];
         }
-        double sx = 0, sy = 0, sz = 0, en = 0, vir = 0, wxx = 0, wyy = 0, wzz = 0, wxy = 0, wxz = 0, wyz = 0;
+        double sx = 0, sy = 0, sz = 0;
         for (int k0 = 4 * lane; k0 < nn; k0 += 4 * TPP) {
             const int4 q = __ldg((const int4 *)(lst + k0));
             const int jj[4] = {q.x, q.y, q.z, q.w};
             d4 xs[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u)                 // padded rows: whole groups of 4
-                xs[u] = pos[kPadLists ? jj[u] : (k0 + u < nn ? jj[u] : ii)];
+            for (int u = 0; u < 4; ++u)                 // padded rows: whole groups
+                xs[u] = pos[jj[u]];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                if (!kPadLists && k0 + u >= nn)
-                    break;
                 const d4 xj = xs[u];
                 const int tj = species_of(xj.w);
                 const double dx = sep_d(xi.x, xj.x, rp.L, rp.invL);
@@ -572,20 +570,13 @@ __device__ __forceinline__ void pair_forces(const KArgs &a, const Rep &rp, int p
                     const double s2 = pr.sig2[tj] * ir2;
                     const double s6 = s2 * s2 * s2;
                     double fr = pr.eps48[tj] * ir2 * s6 * (s6 - 0.5);
-                    double v = 0.0;
-                    if (SM || SAMPLE)
-                        v = pr.eps4[tj] * s6 * (s6 - 1.0) - pr.shift[tj];
-                    if (SM)
+                    if (SM) {
+                        double v = pr.eps4[tj] * s6 * (s6 - 1.0) - pr.shift[tj];
                         smooth_pair(r2, pr.rc[tj], pr.ihs[tj], fr, v);
+                    }
                     sx += fr * dx;
                     sy += fr * dy;
                     sz += fr * dz;
-                    if (SAMPLE) {
-                        en += v;
-                        vir += fr * r2;
-                        wxx += fr * dx * dx; wyy += fr * dy * dy; wzz += fr * dz * dz;
-                        wxy += fr * dx * dy; wxz += fr * dx * dz; wyz += fr * dy * dz;
-                    }
                 }
             }
         }
@@ -596,17 +587,6 @@ __device__ __forceinline__ void pair_forces(const KArgs &a, const Rep &rp, int p
             sz += __shfl_xor_sync(0xffffffffu, sz, o);
         }
         fx = sx; fy = sy; fz = sz;
-        if (SAMPLE) {
-            double d[8] = {en, vir, wxx, wyy, wzz, wxy, wxz, wyz};
-#pragma unroll
-            for (int o = TPP / 2; o > 0; o >>= 1)
-#pragma unroll
-                for (int k = 0; k < 8; ++k)
-                    d[k] += __shfl_xor_sync(0xffffffffu, d[k], o);
-#pragma unroll
-            for (int k = 0; k < 8; ++k)
-                acc[k] = 0.5 * d[k];
-        }
     } else {
         // MIXED reads the fixed-point copy (16 B per neighbour), FP32 the positions
         const float4 *pos = (const float4 *)pos_a(a, pp);
@@ -633,7 +613,6 @@ __device__ __forceinline__ void pair_forces(const KArgs &a, const Rep &rp, int p
             pr.ihs[tj] = a.tab.ihs[ti * 2 + tj];
         }
         float sx = 0.f, sy = 0.f, sz = 0.f, cx = 0.f, cy = 0.f, cz = 0.f;
-        float en = 0.f, vir = 0.f, wxx = 0.f, wyy = 0.f, wzz = 0.f, wxy = 0.f, wxz = 0.f, wyz = 0.f;
         // list indices are loaded kPfDepth iterations ahead, so that only the
         // position gathers remain on each iteration's critical path
         // (K is a multiple of 8: every 16-byte index load is in bounds and aligned)
@@ -670,7 +649,7 @@ __device__ __forceinline__ void pair_forces(const KArgs &a, const Rep &rp, int p
 #pragma unroll
             for (int u = 0; u < kUnr; ++u) {
                 // rows are padded with the particle itself up to a multiple of kUnr
-                const int j = kPadLists ? jj[u] : (k0 + u < nn ? jj[u] : ii);
+                const int j = jj[u];
                 if constexpr (P == MIXED)
                     Qs[u] = __ldg(qp + j);
                 else
@@ -696,30 +675,22 @@ __device__ __forceinline__ void pair_forces(const KArgs &a, const Rep &rp, int p
                 }
                 const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
                 // (the particle itself, r2 = 0 exactly, is never inside)
-                const bool in = (kPadLists ? r2 > 0.0f : k0 + u < nn) && (r2 < (tj ? pr.rc2[1] : pr.rc2[0]));
+                const bool in = r2 > 0.0f && r2 < (tj ? pr.rc2[1] : pr.rc2[0]);
                 const float sig2 = tj ? pr.sig2[1] : pr.sig2[0];
                 const float eps48 = tj ? pr.eps48[1] : pr.eps48[0];
                 const float ir2 = __fdividef(1.0f, in ? r2 : 1.0f);
                 const float s2 = sig2 * ir2;
                 const float s6 = s2 * s2 * s2;
                 float fr = in ? eps48 * ir2 * s6 * (s6 - 0.5f) : 0.0f;
-                float v = 0.0f;
-                if (SM || SAMPLE) {
+                if (SM) {
                     const float eps4 = tj ? pr.eps4[1] : pr.eps4[0];
                     const float shift = tj ? pr.shift[1] : pr.shift[0];
-                    v = in ? eps4 * s6 * (s6 - 1.0f) - shift : 0.0f;
-                }
-                if (SM)
+                    float v = in ? eps4 * s6 * (s6 - 1.0f) - shift : 0.0f;
                     smooth_pair(in ? r2 : 1.0f, tj ? pr.rc[1] : pr.rc[0], tj ? pr.ihs[1] : pr.ihs[0], fr, v);
+                }
                 gx = fmaf(fr, dx, gx);
                 gy = fmaf(fr, dy, gy);
                 gz = fmaf(fr, dz, gz);
-                if (SAMPLE) {
-                    en += v;
-                    vir += fr * r2;
-                    wxx += fr * dx * dx; wyy += fr * dy * dy; wzz += fr * dz * dz;
-                    wxy += fr * dx * dy; wxz += fr * dx * dz; wyz += fr * dy * dz;
-                }
             }
             if constexpr (P == MIXED) {
                 kahan_add(sx, cx, gx);
@@ -753,17 +724,6 @@ __device__ __forceinline__ void pair_forces(const KArgs &a, const Rep &rp, int p
                 sz += __shfl_xor_sync(0xffffffffu, sz, o);
             }
             fx = sx; fy = sy; fz = sz;
-        }
-        if (SAMPLE) {
-            double d[8] = {en, vir, wxx, wyy, wzz, wxy, wxz, wyz};
-#pragma unroll
-            for (int o = TPP / 2; o > 0; o >>= 1)
-#pragma unroll
-                for (int k = 0; k < 8; ++k)
-                    d[k] += __shfl_xor_sync(0xffffffffu, d[k], o);
-#pragma unroll
-            for (int k = 0; k < 8; ++k)
-                acc[k] = 0.5 * d[k];
         }
     }
 }
@@ -898,7 +858,7 @@ __device__ __forceinline__ void force_only(const KArgs &a)
 #pragma unroll
     for (int k = 0; k < kPartF; ++k)
         acc[k] = 0.0;
-    pair_forces<P, TPP, false, SM>(a, rp, pp, ii, nn, fx, fy, fz, acc);
+    pair_forces<P, TPP, SM>(a, rp, pp, ii, nn, fx, fy, fz);
     if (SAMPLE)
         pair_energy<P, TPP, SM>(a, rp, pp, ii, nn, acc);
     if (!(valid && lane == 0)) {
@@ -1073,7 +1033,7 @@ __device__ __forceinline__ void step_body_split(const KArgs &a, bool active, boo
 #pragma unroll
     for (int k = 0; k < kPartF; ++k)
         part[k] = 0.0;
-    pair_forces<P, TPP, false, SM>(a, rp, pp, ii, nn, fx, fy, fz, part);
+    pair_forces<P, TPP, SM>(a, rp, pp, ii, nn, fx, fy, fz);
     if (SAMPLE)
         pair_energy<P, TPP, SM>(a, rp, pp, ii, nn, part);
     // Every lane of the warp must reach the shuffles below, including the
@@ -1177,7 +1137,7 @@ __device__ __forceinline__ void step_body(const KArgs &a, bool active, bool last
 #pragma unroll
     for (int k = 0; k < kPartF; ++k)
         part[k] = 0.0;
-    pair_forces<P, TPP, false, SM>(a, rp, pp, ii, nn, fx, fy, fz, part);
+    pair_forces<P, TPP, SM>(a, rp, pp, ii, nn, fx, fy, fz);
     if (SAMPLE)
         pair_energy<P, TPP, SM>(a, rp, pp, ii, nn, part);
     if (!(valid && lane == 0)) {

@@ -591,3 +591,79 @@ def test_full_size_lj_1m_two_steps(md):
     rp, rv, ri, _, rec = oracle.vv_run(s.params, s.box, s.species, s.pos, s.vel, s.image, 0.005, 2, sample=1)
     assert np.abs((pos + img * s.box) - (rp + ri * s.box)).max() < 1e-6
     assert np.allclose(obs["e_pot"], rec["e_pot"], rtol=1e-6)
+
+
+# ---------------------------------------------------------------------------
+# edge placements: pairs at the cutoff and at the list radius, and pairs that
+# straddle a face, an edge or a corner of the periodic box
+# ---------------------------------------------------------------------------
+def _placed_pairs():
+    """LJ (r_c = 2.5, list radius 2.8 at skin 0.3) in a box of 24: isolated
+    pairs centred on a 4^3 grid of spacing 6 (centres at 0 lie on the faces,
+    edges and corner of the box, so those pairs straddle the boundary); any two
+    particles of different pairs are more than 3.2 apart."""
+    rc, rl = 2.5, 2.8
+    seps = [rc * (1 - 1e-5), rc * (1 + 1e-5), rl * (1 - 1e-5), rl * (1 + 1e-3), 1.12, 1.0, 0.95, 2.0]
+    dirs = [np.array(d, dtype=np.float64) / np.linalg.norm(d) for d in
+            ([1, 0, 0], [0, 1, 0], [0, 0, 1], [1, 1, 0], [1, 0, 1], [0, 1, 1], [1, 1, 1], [1, -1, 1])]
+    L = 24.0
+    pos, tags = [], []
+    k = 0
+    for i in range(4):
+        for j in range(4):
+            for m in range(4):
+                c = np.array([6.0 * i, 6.0 * j, 6.0 * m])
+                d = seps[k % len(seps)]
+                u = dirs[(k // len(seps)) % len(dirs)]
+                pos += [c - 0.5 * d * u, c + 0.5 * d * u]
+                tags.append(d)
+                k += 1
+    pos = np.mod(np.array(pos), L)
+    n = len(pos)
+    s = synth.System(n=n, box=L, species=np.zeros(n, dtype=np.int32), pos=pos,
+                     vel=np.zeros((n, 3)), image=np.zeros((n, 3), dtype=np.int32),
+                     params=synth.lj_params(), seed=0)
+    return s, np.repeat(np.array(tags), 2), rc, rl
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "fp32"])
+def test_pairs_at_the_cutoff_and_across_the_box_faces(md, prec):
+    """Forces of pairs 1e-5 inside and outside r_c, and of pairs across faces,
+    edges and the corner of the box, against the oracle; a particle whose
+    partner is just beyond r_c feels exactly zero force; the lists hold the
+    partner just inside the list radius and not the one 1e-3 beyond it."""
+    s, sep, rc, rl = _placed_pairs()
+    sim = _sim(md, s, prec, skin=0.3)
+    f, e, tot = sim.forces()
+    counts, lists = sim.neighbours()
+    sim.close()
+    fr, er, _ = oracle.forces_brute(s.params, s.box, s.species, _ref_pos(s, prec))
+    assert _ferr(f, fr) <= TOL_F[prec]
+    outside = sep > rc
+    assert (f[outside] == 0.0).all() and (np.abs(fr[outside]).max() == 0.0)
+    assert (np.abs(f[sep == rc * (1 - 1e-5)]) > 0.0).any(axis=1).all()
+    partner = np.arange(s.n) ^ 1
+    listed = np.array([partner[i] in lists[i, :counts[i]] for i in range(s.n)])
+    assert listed[sep < rl].all()
+    assert not listed[sep > rl * 1.0005].any()
+    assert (counts <= 1).all()
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_lists_cover_the_cutoff_between_rebuilds(md, prec):
+    """At arbitrary steps between rebuilds every pair inside r_c,ab is still in
+    the list built earlier (the displacement criterion of Sec. 2.2)."""
+    s = _system("ka", 3000, amp=0.05, temperature=1.5)
+    sim = _sim(md, s, prec, dt=0.002, skin=0.3)
+    seen = 0
+    for n in (13, 29, 41):
+        sim.step(n)
+        assert sim.sync() == md.MD_OK
+        pos, _, _ = sim.get_state()
+        counts, lists = sim.neighbours()
+        inner, inner_l = oracle.neighbours_brute(s.params, s.box, s.species, pos, -1e-6, kmax=256)
+        for i in range(s.n):
+            assert set(inner_l[i, :inner[i]].tolist()) <= set(lists[i, :counts[i]].tolist())
+        seen += int(inner.sum())
+    assert seen > 0
+    sim.close()

@@ -64,6 +64,8 @@ extern "C" {
 #define MD_E_UNSTABLE   5  /* a particle moved more than a quarter box length in one step     */
 #define MD_E_TIMEOUT    6  /* the device-side step loop exceeded its iteration bound          */
 #define MD_E_CAPACITY   7  /* a neighbour list needed more than neigh_capacity entries        */
+#define MD_E_BOUNDS     8  /* only in a library built with MD_CHECK_BOUNDS: a kernel index
+                              left its array (the access was redirected to a valid one)     */
 
 /* precision modes (Sec. 2.4) */
 #define MD_PREC_FP64  0    /* everything in IEEE double                                        */

@@ -18,6 +18,7 @@
 // use_graph = 0 the same kernel sequence, with the same check points, is
 // launched from the host (the results are bitwise identical).
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -35,6 +36,17 @@ static_assert(sizeof(md_params) == 192, "md_params layout is part of the ABI");
 
 using mdk::KArgs;
 using mdk::KernelSet;
+
+namespace {
+// A named range on a profiler's host timeline for the duration of one API call
+// (NVTX; costs nothing when no tool is attached).
+struct ApiRange {
+    explicit ApiRange(const char *name) { nvtxRangePushA(name); }
+    ~ApiRange() { nvtxRangePop(); }
+    ApiRange(const ApiRange &) = delete;
+    ApiRange &operator=(const ApiRange &) = delete;
+};
+}  // namespace
 
 namespace {
 
@@ -671,6 +683,7 @@ int status_code(unsigned st)
     if (st & mdk::ST_UNSTABLE) return MD_E_UNSTABLE;
     if (st & mdk::ST_OVERFLOW) return MD_E_CAPACITY;
     if (st & mdk::ST_TIMEOUT) return MD_E_TIMEOUT;
+    if (st & mdk::ST_BOUNDS) return MD_E_BOUNDS;
     return MD_OK;
 }
 
@@ -680,6 +693,7 @@ const char *status_message(int code)
     case MD_E_NONFINITE: return "a position became non-finite; the step loop stopped";
     case MD_E_UNSTABLE: return "a particle moved more than a quarter box in one step; the step loop stopped";
     case MD_E_CAPACITY: return "a neighbour list exceeded neigh_capacity; the step loop stopped";
+    case MD_E_BOUNDS: return "an index left its array (bounds-checked build); the access was redirected";
     case MD_E_TIMEOUT: return "the device step loop exceeded its iteration bound";
     default: return "";
     }
@@ -965,6 +979,7 @@ int md_create(md_handle **out, const md_params *p, int32_t n_replicas, const int
               const double *box, const int32_t *species, const double *pos, const double *vel,
               const int32_t *image, void *workspace, size_t workspace_bytes, void *cuda_stream)
 {
+    ApiRange range_("md_create");
     if (!out)
         return MD_E_INVAL;
     *out = nullptr;
@@ -985,6 +1000,7 @@ int md_create(md_handle **out, const md_params *p, int32_t n_replicas, const int
 
 int md_step(md_handle *h, int64_t nsteps)
 {
+    ApiRange range_("md_step");
     if (!h)
         return MD_E_INVAL;
     if (nsteps < 1)
@@ -1036,6 +1052,7 @@ int md_step(md_handle *h, int64_t nsteps)
 
 int md_rescale_velocities(md_handle *h, const double *T_target)
 {
+    ApiRange range_("md_rescale_velocities");
     if (!h || !T_target)
         return MD_E_INVAL;
     int rc;
@@ -1055,6 +1072,7 @@ int md_rescale_velocities(md_handle *h, const double *T_target)
 // Andersen heat bath (Sec. 2.3): one collision of every particle.
 int md_andersen(md_handle *h, const double *T_target, uint64_t seed, int64_t event)
 {
+    ApiRange range_("md_andersen");
     if (!h || !T_target)
         return MD_E_INVAL;
     if (event < 0)
@@ -1154,6 +1172,7 @@ int md_corr_workspace_size(const md_handle *h, int32_t k, int32_t l, int32_t n_q
 int md_corr_create(md_corr **out, md_handle *h, int32_t k, int32_t l, int32_t n_q, const double *q,
                    void *workspace, size_t workspace_bytes)
 {
+    ApiRange range_("md_corr_create");
     if (!out || !q || corr_check(h, k, l, n_q))
         return h ? fail(h, MD_E_INVAL, "md_corr_create: bad arguments (1 <= k, 2 <= l <= 32, "
                                        "1 <= n_q <= 64, non-null q)") : MD_E_INVAL;
@@ -1205,6 +1224,7 @@ int md_corr_create(md_corr **out, md_handle *h, int32_t k, int32_t l, int32_t n_
 
 int md_corr_sample(md_corr *c)
 {
+    ApiRange range_("md_corr_sample");
     if (!c)
         return MD_E_INVAL;
     md_handle *h = c->h;
@@ -1260,6 +1280,7 @@ int md_corr_sample(md_corr *c)
 
 int md_corr_result(md_corr *c, int64_t *lags, double *msd, double *fs, int64_t *origins)
 {
+    ApiRange range_("md_corr_result");
     if (!c)
         return MD_E_INVAL;
     md_handle *h = c->h;
@@ -1296,6 +1317,7 @@ int md_corr_destroy(md_corr *c)
 
 int md_compute_forces(md_handle *h, double *f, double *e, md_obs *totals)
 {
+    ApiRange range_("md_compute_forces");
     if (!h)
         return MD_E_INVAL;
     int rc;
@@ -1325,6 +1347,7 @@ int md_compute_forces(md_handle *h, double *f, double *e, md_obs *totals)
 
 int md_observables(md_handle *h, md_obs *out, int32_t max_samples, int32_t *n_samples)
 {
+    ApiRange range_("md_observables");
     if (!h || !n_samples || (max_samples > 0 && !out))
         return MD_E_INVAL;
     *n_samples = 0;
@@ -1361,6 +1384,7 @@ int md_observables(md_handle *h, md_obs *out, int32_t max_samples, int32_t *n_sa
 
 int md_get_state(md_handle *h, double *pos, double *vel, int32_t *image)
 {
+    ApiRange range_("md_get_state");
     if (!h)
         return MD_E_INVAL;
     int rc;
@@ -1385,6 +1409,7 @@ int md_get_state(md_handle *h, double *pos, double *vel, int32_t *image)
 
 int md_set_state(md_handle *h, const double *pos, const double *vel, const int32_t *image)
 {
+    ApiRange range_("md_set_state");
     if (!h || !pos || !vel)
         return MD_E_INVAL;
     int rc;
@@ -1411,6 +1436,7 @@ int md_set_state(md_handle *h, const double *pos, const double *vel, const int32
 
 int md_get_neighbours(md_handle *h, int32_t *counts, int32_t *lists, int32_t kmax)
 {
+    ApiRange range_("md_get_neighbours");
     if (!h || !counts || (lists && kmax < 1))
         return MD_E_INVAL;
     const size_t n = (size_t)h->g.n, K = (size_t)h->g.K;
@@ -1479,6 +1505,7 @@ int md_sync(md_handle *h)
 
 int md_destroy(md_handle *h)
 {
+    ApiRange range_("md_destroy");
     if (!h)
         return MD_E_INVAL;
     if (h->ws)
@@ -1519,6 +1546,7 @@ const char *md_status_string(int code)
     case MD_E_UNSTABLE: return "MD_E_UNSTABLE";
     case MD_E_TIMEOUT: return "MD_E_TIMEOUT";
     case MD_E_CAPACITY: return "MD_E_CAPACITY";
+    case MD_E_BOUNDS: return "MD_E_BOUNDS";
     default: return "MD_E_UNKNOWN";
     }
 }

@@ -11,7 +11,7 @@ namespace mdk {
 enum { FP64 = 0, MIXED = 1, FP32 = 2 };
 
 // device status bits
-enum { ST_OVERFLOW = 1u, ST_NONFINITE = 2u, ST_UNSTABLE = 4u, ST_TIMEOUT = 8u };
+enum { ST_OVERFLOW = 1u, ST_NONFINITE = 2u, ST_UNSTABLE = 4u, ST_TIMEOUT = 8u, ST_BOUNDS = 16u };
 
 // integrate-kernel modes
 enum {

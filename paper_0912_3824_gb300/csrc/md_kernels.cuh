@@ -42,6 +42,27 @@ constexpr int kUnr = 8;          // list entries per lane and iteration of the F
 constexpr int kPfDepth = 1;      // iterations ahead at which the list indices are loaded
 constexpr bool kSplitUpdate = false; // below 4 lanes: one lane updates (measured faster than sharing)
 
+// Bounds-checked build (compile with -DMD_CHECK_BOUNDS=1; off in the product
+// library): every index read from device memory (list entries, cell keys,
+// permutation slots) is tested against its array before use.
+#ifndef MD_CHECK_BOUNDS
+#define MD_CHECK_BOUNDS 0
+#endif
+constexpr bool kCheckBounds = MD_CHECK_BOUNDS != 0;
+
+// i unchanged if 0 <= i < n; otherwise (checked builds) ST_BOUNDS is recorded
+// and `safe` returned, so that the access stays inside the array.
+__device__ __forceinline__ int checked(const KArgs &a, int i, int n, int safe)
+{
+    if constexpr (kCheckBounds) {
+        if ((unsigned int)i >= (unsigned int)n) {
+            atomicOr(&a.ctl->status, ST_BOUNDS);
+            return safe;
+        }
+    }
+    return i;
+}
+
 // ---------------------------------------------------------------------------
 // small helpers
 // ---------------------------------------------------------------------------
@@ -556,7 +577,7 @@ __device__ __forceinline__ void pair_forces(const KArgs &a, const Rep &rp, int p
             d4 xs[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u)                 // padded rows: whole groups
-                xs[u] = pos[jj[u]];
+                xs[u] = pos[checked(a, jj[u], a.n, ii)];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const d4 xj = xs[u];
@@ -649,7 +670,7 @@ __device__ __forceinline__ void pair_forces(const KArgs &a, const Rep &rp, int p
 #pragma unroll
             for (int u = 0; u < kUnr; ++u) {
                 // rows are padded with the particle itself up to a multiple of kUnr
-                const int j = jj[u];
+                const int j = checked(a, jj[u], a.n, ii);
                 if constexpr (P == MIXED)
                     Qs[u] = __ldg(qp + j);
                 else
@@ -742,7 +763,7 @@ __device__ __forceinline__ void pair_energy(const KArgs &a, const Rep &rp, int p
         const d4 xi = pos[ii];
         const int ti = species_of(xi.w);
         for (int k = lane; k < nn; k += TPP) {
-            const d4 xj = pos[__ldg(lst + k)];
+            const d4 xj = pos[checked(a, __ldg(lst + k), a.n, ii)];
             const int ab = ti * 2 + species_of(xj.w);
             const double dx = sep_d(xi.x, xj.x, rp.L, rp.invL);
             const double dy = sep_d(xi.y, xj.y, rp.L, rp.invL);
@@ -766,7 +787,7 @@ __device__ __forceinline__ void pair_energy(const KArgs &a, const Rep &rp, int p
         const int4 *qp = q_of(a, pp);
         const int4 Qi = qp[ii];
         for (int k = lane; k < nn; k += TPP) {
-            const int4 Qj = __ldg(qp + __ldg(lst + k));
+            const int4 Qj = __ldg(qp + checked(a, __ldg(lst + k), a.n, ii));
             const int ab = Qi.w * 2 + Qj.w;
             const float dx = sep_q(Qi.x, Qj.x, rp.qunit);
             const float dy = sep_q(Qi.y, Qj.y, rp.qunit);
@@ -791,7 +812,7 @@ __device__ __forceinline__ void pair_energy(const KArgs &a, const Rep &rp, int p
         const float4 Hi = pos[ii];
         const int ti = species_of(Hi.w);
         for (int k = lane; k < nn; k += TPP) {
-            const int j = __ldg(lst + k);
+            const int j = checked(a, __ldg(lst + k), a.n, ii);
             const float4 Hj = __ldg(pos + j);
             const int ab = ti * 2 + species_of(Hj.w);
             const float dx = sep_f(Hi.x, Hj.x, rp.Lhi, rp.invLf);
@@ -1430,7 +1451,7 @@ __global__ void __launch_bounds__(kIntBlock) k_bin(KArgs a)
         cy = cell_coord_f(x.y, rp.cscalef, rp.nc);
         cz = cell_coord_f(x.z, rp.cscalef, rp.nc);
     }
-    const int key = a.crank[rp.cell0 + (cz * rp.nc + cy) * rp.nc + cx];
+    const int key = checked(a, a.crank[rp.cell0 + (cz * rp.nc + cy) * rp.nc + cx], a.ncell, 0);
     a.key[i] = key;
     atomicAdd(&a.ccount[key], 1);
 }
@@ -1528,8 +1549,8 @@ __global__ void __launch_bounds__(kIntBlock) k_scatter(KArgs a)
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.n)
         return;
-    const int k = a.key[i];
-    const int slot = a.cstart[k] + atomicAdd(&a.ccursor[k], 1);
+    const int k = checked(a, a.key[i], a.ncell, 0);
+    const int slot = checked(a, a.cstart[k] + atomicAdd(&a.ccursor[k], 1), a.n, 0);
     a.tmpidx[slot] = i;
 }
 
@@ -1548,13 +1569,13 @@ __global__ void __launch_bounds__(kIntBlock) k_permute(KArgs a)
     if (s >= a.n)
         return;
     const int pp = ctl->pos_par, spar = ctl->state_par;
-    const int i = a.tmpidx[s];
-    const int k = a.key[i];
+    const int i = checked(a, a.tmpidx[s], a.n, 0);
+    const int k = checked(a, a.key[i], a.ncell, 0);
     const int b0 = a.cstart[k], b1 = a.cstart[k + 1];
     int rank = 0;
     for (int t = b0; t < b1; ++t)
         rank += (a.tmpidx[t] < i) ? 1 : 0;
-    const int d = b0 + rank;
+    const int d = checked(a, b0 + rank, a.n, 0);
     if constexpr (P == FP64) {
         const d4 x = ((const d4 *)pos_a(a, pp))[i];
         ((d4 *)pos_a(a, pp ^ 1))[d] = x;
@@ -1730,7 +1751,7 @@ __device__ __forceinline__ void nbuild_cell(const KArgs &a, int pn)
                 int k = 0;
                 while (k + 1 < nst && s_pref[k + 1] <= t)
                     ++k;
-                j = a.cstart[s_cell[k]] + (t - s_pref[k]);
+                j = checked(a, a.cstart[s_cell[k]] + (t - s_pref[k]), a.n, 0);
                 q = nb_word<P>(a, pn, j);
                 keep = true;
                 if (nst == 27) {

@@ -21,7 +21,8 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.environ.get("MDGB300_LIB", os.path.join(_HERE, "libmdgb300.so"))
 
-MD_OK, MD_E_INVAL, MD_E_NOMEM, MD_E_CUDA, MD_E_NONFINITE, MD_E_UNSTABLE, MD_E_TIMEOUT, MD_E_CAPACITY = range(8)
+(MD_OK, MD_E_INVAL, MD_E_NOMEM, MD_E_CUDA, MD_E_NONFINITE, MD_E_UNSTABLE, MD_E_TIMEOUT, MD_E_CAPACITY,
+ MD_E_BOUNDS) = range(9)
 MD_PREC_FP64, MD_PREC_MIXED, MD_PREC_FP32 = 0, 1, 2
 PRECISIONS = {"fp64": MD_PREC_FP64, "mixed": MD_PREC_MIXED, "fp32": MD_PREC_FP32}
 

@@ -51,6 +51,8 @@ def parse_args(argv=None):
     ap.add_argument("--no-graph", action="store_true",
                     help="plain stream launches instead of the CUDA graph (for per-kernel profiling)")
     ap.add_argument("--tpp", type=int, default=0, help="force-kernel threads per particle (0 = auto)")
+    ap.add_argument("--check", type=int, default=0,
+                    help="MD steps between rebuild checks of the graph (0 = the library's choice)")
     ap.add_argument("--skin", type=float, default=0.3, help="neighbour-list skin (with --no-tune)")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (lanes, skin, capacity)")
     ap.add_argument("--workload", choices=["ka65536", "lj-sweep", "e1", "replicas", "drift", "stability",
@@ -264,7 +266,8 @@ def run_ours(args, rank, world, local):
     # the prepared state; --no-tune keeps --tpp / --skin as given
     pos0, vel0, img0 = sim.get_state()
     base = md.make_params(s.params, 0.001, skin=args.skin, precision=md.PRECISIONS[args.precision],
-                          sample_interval=100, use_graph=not args.no_graph, threads_per_particle=args.tpp)
+                          sample_interval=100, use_graph=not args.no_graph, threads_per_particle=args.tpp,
+                          check_interval=args.check)
     trials = None
     if not args.no_tune:
         from paper_0912_3824_gb300 import tune
@@ -314,6 +317,7 @@ def run_ours(args, rank, world, local):
                    "l2": "flushed (256 MB write) between timed iterations",
                    "parallelism": f"replicas x{world} (no collective)",
                    "threads_per_particle": info1["threads_per_particle"],
+                   "check_interval": info1["check_interval"],
                    "neigh_capacity": info1["neigh_capacity"], "skin": float(base.skin),
                    "tuned": trials is not None},
         "clocks": clk, "gpu_launches": launches,

@@ -38,6 +38,19 @@ def test_library_exports_every_declared_symbol(md):
     assert set(_declared()) == set(md.EXPORTED)
 
 
+def test_bounds_checked_library_builds_and_exports_the_same_symbols(md):
+    """The bounds-checked variant used by tests/test_bounds_checked.py compiles
+    (nvcc cross-compiles without a GPU) and exports the same entry points."""
+    import ctypes
+    import shutil
+    if shutil.which("nvcc") is None:
+        pytest.skip("nvcc not available")
+    from paper_0912_3824_gb300 import build
+    lib = ctypes.CDLL(build.build(checked=True))
+    for name in _declared():
+        assert hasattr(lib, name), name
+
+
 def test_params_default(md):
     p = md.md_params_default()
     assert p.n_species == 1 and p.shift == 1

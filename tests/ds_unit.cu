@@ -1,4 +1,4 @@
-// Test driver for the double-single primitives of md_common.cuh (Sec. 2.4,
+// Test program for the double-single primitives of md_common.cuh (Sec. 2.4,
 // Algorithm 1): reads n operand pairs (a.hi, a.lo, b.hi, b.lo as float32) from
 // argv[1], evaluates ds_add(a, b), ds_mul(a, b) and ds_mul_f(a, b.hi) on the
 // GPU and writes the six result words per pair to argv[2].  Built and run by

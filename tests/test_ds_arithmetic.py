@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 
 
-def _driver(tmp_path):
+def _program(tmp_path):
     import shutil
     if shutil.which("nvcc") is None:
         pytest.skip("nvcc not available")
@@ -50,7 +50,7 @@ def _operands(rng, n):
 
 
 def test_ds_add_mul_against_exact_rationals(tmp_path):
-    exe = _driver(tmp_path)
+    exe = _program(tmp_path)
     ops = _operands(np.random.default_rng(7), 4000)
     inp, outp = tmp_path / "in.bin", tmp_path / "out.bin"
     with open(inp, "wb") as f:

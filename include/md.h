@@ -40,10 +40,13 @@
  *     md_step() returns without waiting for the GPU; the calls that return
  *     data (md_compute_forces, md_observables, md_get_state,
  *     md_get_neighbours, md_info, md_sync) wait for the stream.
- *   - Device-side failures (neighbour-list overflow, a non-finite value, a
- *     particle moving more than a quarter box in one step) stop the
- *     step loop at the end of the offending step, leave the state at that
+ *   - Device-side failures (a neighbour list longer than the cap
+ *     neigh_capacity_max, a non-finite value, a particle moving more than a
+ *     quarter box in one step, an exhausted step-loop bound) stop the step
+ *     loop at the end of the offending step, leave the positions at that
  *     step, and are reported by the next md_sync / md_observables / md_step.
+ *     A list longer than the current capacity but within the cap is not a
+ *     failure: the capacity grows on the device and the build is redone.
  */
 #ifndef MD_GB300_H
 #define MD_GB300_H
@@ -63,7 +66,7 @@ extern "C" {
 #define MD_E_NONFINITE  4  /* a position became NaN or infinite                               */
 #define MD_E_UNSTABLE   5  /* a particle moved more than a quarter box length in one step     */
 #define MD_E_TIMEOUT    6  /* the device-side step loop exceeded its iteration bound          */
-#define MD_E_CAPACITY   7  /* a neighbour list needed more than neigh_capacity entries        */
+#define MD_E_CAPACITY   7  /* a neighbour list needed more than neigh_capacity_max entries    */
 #define MD_E_BOUNDS     8  /* only in a library built with MD_CHECK_BOUNDS: a kernel index
                               left its array (the access was redirected to a valid one)     */
 
@@ -83,9 +86,16 @@ typedef struct {
     double  dt;               /* time step, > 0                                                 */
     double  skin;             /* neighbour-list skin, >= 0 (default 0.3)                        */
     int32_t precision;        /* MD_PREC_*                                                      */
-    int32_t neigh_capacity;   /* list entries per particle; 0 = derived from the density        */
+    int32_t neigh_capacity;   /* starting list entries per particle (rounded up to a multiple of
+                                 8); 0 = derived from the density.  The list of Sec. 2.2 has a
+                                 fixed size per particle; when a build finds a longer list the
+                                 library raises the size on the device (to 1.25 times the
+                                 longest list, rounded up to 8, at most neigh_capacity_max) and
+                                 redoes the build, within the same md_step                     */
     int32_t sample_interval;  /* record observables every this many steps (>= 1)                */
-    int32_t obs_capacity;     /* ring-buffer samples kept on the device (0 = 4096)              */
+    int32_t obs_capacity;     /* ring-buffer samples kept on the device (0 = 4096); also the
+                                 number of newest steps the per-step potential-energy series
+                                 keeps (md_epot_series)                                         */
     int32_t threads_per_particle; /* force-kernel lanes per particle: 0 = automatic (2 for MIXED
                                      and FP32, 4 for FP64), else a power of two in 1..32 (1..8
                                      with smooth_h > 0)                                          */
@@ -106,7 +116,15 @@ typedef struct {
                                  on how far particles can still move (speed and acceleration
                                  over the unchecked steps), so a longer interval rebuilds
                                  earlier; a check costs one conditional graph node           */
-    int32_t reserved[3];      /* must be zero                                                   */
+    int32_t neigh_capacity_max; /* cap on the list entries per particle (rounded up to 8): the
+                                 workspace holds this many; 0 = twice the starting capacity.
+                                 Only a list longer than the cap is an error (MD_E_CAPACITY);
+                                 neigh_capacity_max = neigh_capacity keeps the size fixed     */
+    int32_t step_budget;      /* 0 = automatic.  > 0: md_step's device loop stops with
+                                 MD_E_TIMEOUT after this many step-kernel executions (its
+                                 iteration bound; automatic = nsteps + 64), so the bounded-
+                                 loop path can be exercised                                     */
+    int32_t reserved[1];      /* must be zero                                                   */
 } md_params;
 
 /* one sample of the reductions of Sec. 2.2, per replica */
@@ -117,14 +135,15 @@ typedef struct {
     double  virial;           /* sum over pairs of r_ij . F_ij                                  */
     double  w[6];             /* virial tensor xx, yy, zz, xy, xz, yz                           */
     double  p[3];             /* total momentum                                                 */
-    double  max_disp;         /* largest displacement since the last list build (all replicas)  */
+    double  max_disp;         /* largest displacement of the sample's positions from those of
+                                 the last list build (over all replicas)                       */
     int64_t rebuilds;         /* neighbour-list builds so far (all replicas)                    */
 } md_obs;
 
 typedef struct {
     int64_t n_total;          /* particles over all replicas                                    */
     int32_t n_replicas;
-    int32_t neigh_capacity;   /* K in use                                                       */
+    int32_t neigh_capacity;   /* list entries per particle in use (grows up to the cap)          */
     int32_t threads_per_particle;
     int32_t cells_per_edge;   /* of replica 0 (1 when the box holds fewer than 3 cells)         */
     int64_t step;             /* MD steps done since md_create                                  */
@@ -143,7 +162,8 @@ typedef struct {
                                  read from the GPU's global timer)                              */
     int64_t step_device_launches; /* launches summed into step_device_ms (one per MD step)      */
     int32_t check_interval;   /* MD steps between rebuild checks, as resolved                   */
-    int32_t reserved;
+    int32_t neigh_capacity_max; /* the cap on neigh_capacity, as resolved                       */
+    int64_t regrows;          /* list builds redone with a larger capacity since md_create      */
 } md_info_t;
 
 typedef struct md_handle md_handle;
@@ -165,13 +185,19 @@ int md_cell_order(const md_params *p, int32_t n_replicas, const int64_t *n_per_r
 int md_workspace_size(const md_params *p, int32_t n_replicas,
                       const int64_t *n_per_replica, const double *box, size_t *bytes);
 
-/* Create a handle.  species[n_total] in {0, n_species-1}; pos[n_total][3]
- * (any real coordinates: they are wrapped into [0, box)), vel[n_total][3],
- * image[n_total][3] (may be NULL = zeros).  Uploads the state, bins the
- * particles, builds the neighbour lists, evaluates the forces and records
- * the step-0 sample.  Each box must exceed twice the largest cutoff plus
- * skin.  workspace: device memory of at least md_workspace_size() bytes.
- * cuda_stream: a cudaStream_t or NULL. */
+/* Create a handle: the problem statement of Sec. 2.2 (N particles with
+ * species, a periodic box, the pair potential of Sec. 3 with the parameters
+ * in *p, the time step).  species[n_total] in {0, n_species-1} (checked on
+ * the host: MD_E_INVAL otherwise); pos[n_total][3] (any real coordinates:
+ * they are wrapped into [0, box)), vel[n_total][3], image[n_total][3] (may
+ * be NULL = zeros).  Uploads the state, bins the particles and orders them
+ * along the cell curve, builds the neighbour lists (growing the capacity up
+ * to its cap if needed), evaluates the forces and records the step-0 sample.
+ * Each box must exceed twice the largest cutoff plus skin.  workspace:
+ * device memory of at least md_workspace_size() bytes, owned by the caller.
+ * cuda_stream: a cudaStream_t or NULL.  Errors: MD_E_INVAL, MD_E_NOMEM,
+ * MD_E_CUDA, MD_E_CAPACITY (a list longer than the cap at the first build).
+ * On failure *h is NULL and nothing is left allocated. */
 int md_create(md_handle **h, const md_params *p, int32_t n_replicas,
               const int64_t *n_per_replica, const double *box,
               const int32_t *species, const double *pos, const double *vel,
@@ -187,11 +213,6 @@ int md_step(md_handle *h, int64_t nsteps);
  * T_r = 2 E_kin,r / (3 N_r - 3)  (the exact rescale of Sec. 2.3). */
 int md_rescale_velocities(md_handle *h, const double *T_target);
 
-/* Force on every particle at the current positions, f[n_total][3] (may be
- * NULL), per-particle potential energy e[n_total] = half of each pair
- * energy (may be NULL), and per-replica totals[n_replicas] (may be NULL;
- * e_pot, virial, w are the force-kernel reductions, e_kin and p those of the
- * current velocities).  Rebuilds the lists first.  Waits for the stream. */
 /* Andersen heat bath (Sec. 2.3): every particle of replica r receives a fresh
  * Maxwell-Boltzmann velocity at T_target[r] (host array [n_replicas], >= 0);
  * then the mass-weighted mean velocity of each replica is removed and its
@@ -208,22 +229,53 @@ int md_rescale_velocities(md_handle *h, const double *T_target);
  * negative event index.                                                       */
 int md_andersen(md_handle *h, const double *T_target, uint64_t seed, int64_t event);
 
+/* The force evaluation of Sec. 2.2 on its own: pair forces of the potential of
+ * Sec. 3 (Kob-Andersen parameters of Sec. 5) over freshly built lists at the
+ * current positions.  Outputs: the force on every particle f[n_total][3]
+ * (may be NULL), the per-particle potential energy e[n_total] = half of each
+ * pair energy (may be NULL), and per-replica totals[n_replicas] (may be NULL;
+ * e_pot, virial, w are the force-kernel reductions, e_kin and p those of the
+ * current velocities; max_disp is 0, the lists having just been rebuilt).
+ * The state is not advanced.  Waits for the stream; returns any pending device status. */
 int md_compute_forces(md_handle *h, double *f, double *e, md_obs *totals);
 
-/* Copy out the samples recorded since the previous call, oldest first, as
- * [sample][replica] records; at most max_samples samples (the newest are kept
- * when more were recorded than the ring holds).  *n_samples receives the
- * number written.  Waits for the stream; returns any pending device status. */
+/* The reductions of Sec. 2.2 (potential energy, virial tensor, kinetic
+ * energy, centre-of-mass momentum, maximum displacement), recorded on the
+ * device every sample_interval steps.  Copies out the samples recorded since
+ * the previous call, oldest first, as [sample][replica] records into the
+ * caller's out[max_samples][n_replicas]; at most max_samples samples (the
+ * newest are kept when more were recorded than the ring holds).  *n_samples
+ * receives the number written.  Waits for the stream; returns any pending
+ * device status. */
 int md_observables(md_handle *h, md_obs *out, int32_t max_samples, int32_t *n_samples);
 
+/* The potential energy of every replica at every MD step: Sec. 2.2 names the
+ * potential-energy sum, with the maximum displacement, among the reductions
+ * needed every step, so the step kernel sums the pair energies in the force
+ * loop and reduces them (per block, then per replica in a fixed order, in
+ * FP64) at every step; at sample steps the value equals the e_pot of the
+ * md_observables record bit for bit.  The device keeps the newest
+ * obs_capacity steps.  Copies out the steps recorded since the previous call,
+ * oldest first (at most max_steps, the newest kept): steps[n] (the MD step of
+ * each value; step 0 is the state given to md_create) and e_pot[n][n_replicas],
+ * caller arrays.  *n_steps receives n.  Waits for the stream; returns any
+ * pending device status.  MD_E_INVAL for a null pointer. */
+int md_epot_series(md_handle *h, int64_t *steps, double *e_pot, int32_t max_steps, int32_t *n_steps);
+
 /* Current positions (wrapped into [0, box)), velocities and image counters,
- * original order.  Any output may be NULL.  Waits for the stream. */
+ * in the original order although the library keeps the particles sorted
+ * along the cell curve (Sec. 2.2 reorder).  Caller arrays pos[n_total][3],
+ * vel[n_total][3], image[n_total][3]; any may be NULL.  MIXED state is
+ * returned as the double value of each double-single pair (Sec. 2.4).
+ * Waits for the stream. */
 int md_get_state(md_handle *h, double *pos, double *vel, int32_t *image);
 
-/* Replace positions, velocities and images (original order; image may be
- * NULL = zeros), then re-bin, rebuild the lists and evaluate the forces.
- * Asynchronous: the host arrays are staged through pinned memory before
- * the call returns. */
+/* Replace positions, velocities and images (original order, layouts as in
+ * md_get_state; image may be NULL = zeros), then re-bin, rebuild the lists
+ * (Sec. 2.2) and evaluate the forces; species stay those of md_create.
+ * Non-finite values are not rejected here: the next md_step reports them as
+ * MD_E_NONFINITE.  Asynchronous: the host arrays are staged through pinned
+ * memory before the call returns. */
 int md_set_state(md_handle *h, const double *pos, const double *vel, const int32_t *image);
 
 /* Current neighbour lists, for inspection: counts[n_total] and
@@ -234,14 +286,19 @@ int md_get_neighbours(md_handle *h, int32_t *counts, int32_t *lists, int32_t kma
 /* Counters and settings of the handle.  Waits for the stream. */
 int md_info(md_handle *h, md_info_t *out);
 
-/* Wait for the stream and return the pending device status (MD_OK if none).
- * A status is reported once; the state stays at the step where it arose. */
+/* Wait for the stream and return the pending device status (MD_OK if none):
+ * the failures that the device detects during the loop of Sec. 2.2 (list
+ * overflow past the cap, non-finite or runaway positions, an exhausted loop
+ * bound).  A status is reported once; the positions stay at the step where
+ * it arose. */
 int md_sync(md_handle *h);
 
 /* Release the handle (not the workspace).  Waits for the stream. */
 int md_destroy(md_handle *h);
 
-/* Message of the last failure on h (never NULL). */
+/* Message of the last failure on h (never NULL).  With h = NULL: the message
+ * of the calling thread's last failed md_forces_noalloc call, the one call
+ * that takes no handle ("" after a success). */
 const char *md_last_error(const md_handle *h);
 
 /* Fixed name of a status code. */
@@ -261,8 +318,8 @@ const char *md_status_string(int code);
  * device), or code certified to allocate nothing after start-up.  It needs no
  * handle and no workspace.
  *
- * All arrays are DEVICE memory owned by the caller: species[n] (int32, 0 or
- * 1), pos[n][3] (float64, any real coordinates), force[n][3] (float64, out),
+ * All arrays are DEVICE memory owned by the caller: species[n] (int32, in
+ * [0, n_species)), pos[n][3] (float64, any real coordinates), force[n][3] (float64, out),
  * energy[n] (float64, out: half of each pair energy; may be NULL), totals[8]
  * (float64, out: E_pot, virial, W_xx, W_yy, W_zz, W_xy, W_xz, W_yz).  From *p
  * only the potential (n_species, eps, sigma, rcut, shift) and the precision
@@ -278,9 +335,22 @@ const char *md_status_string(int code);
  * itself; calls that overlap on the GPU (different streams, or unordered
  * calls from several threads) race on the area and give wrong totals.
  *
+ * The scratch address is looked up once per device and kept: a device reset
+ * (cudaDeviceReset) after the first call on that device is not supported.
+ *
+ * The species array is device memory, so the host cannot check it without a
+ * copy: a code outside [0, n_species) is treated as the nearest valid species
+ * for the pair parameters, the force and energy of that particle are written
+ * as NaN, and all eight totals are NaN, so that bad input never passes as a
+ * result.
+ *
+ * Cost: O(n^2) pair tests with the minimum image in FP64, in every precision
+ * mode, so the time per call grows as n^2.
+ *
  * Returns MD_OK, MD_E_INVAL (null pointer, n < 2, n > MD_NOALLOC_MAX_N, box
- * too small, bad parameters) or MD_E_CUDA.  Asynchronous on cuda_stream (a
- * cudaStream_t, NULL = legacy default stream). */
+ * too small, bad parameters; the reason is in md_last_error(NULL)) or
+ * MD_E_CUDA.  Asynchronous on cuda_stream (a cudaStream_t, NULL = legacy
+ * default stream). */
 int md_forces_noalloc(const md_params *p, int64_t n, double box, const int32_t *species,
                       const double *pos, double *force, double *energy, double *totals,
                       void *cuda_stream);

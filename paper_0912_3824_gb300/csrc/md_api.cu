@@ -37,6 +37,9 @@ static_assert(sizeof(md_params) == 192, "md_params layout is part of the ABI");
 using mdk::KArgs;
 using mdk::KernelSet;
 
+// md_noalloc.cu: message of the calling thread's last failed handle-free call
+const char *md_noalloc_message();
+
 namespace {
 // A named range on a profiler's host timeline for the duration of one API call
 // (NVTX; costs nothing when no tool is attached).
@@ -65,7 +68,7 @@ size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 struct Geometry {
     int R = 0;
     int64_t n = 0;
-    int K = 0, tpp = 8, ppb_f = 32;
+    int K = 0, Kmax = 0, tpp = 8, ppb_f = 32;   // starting list capacity, its cap
     int check = kCheck;                 // MD steps between rebuild checks of the graph
     int nblk_i = 0, nblk_f = 0, ncell = 0;
     double rl_max = 0.0;
@@ -81,6 +84,7 @@ struct Layout {
     size_t off_rref, off_image, off_image2, off_key, off_tmpidx;
     size_t off_ccount, off_ccursor, off_cstart, off_nbr, off_nnbr, off_part_f, off_part_i;
     size_t off_ring, off_totals, off_scale, off_st_pos, off_st_vel, off_st_img, off_st_code;
+    size_t off_epot, off_epot_step;
     size_t off_st_f, off_st_e, total;
 };
 
@@ -185,9 +189,12 @@ int make_geometry(const md_params *p, int R, const int64_t *nrep, const double *
         msg = "threads_per_particle must be 0 or a power of two in [1, 32]";
         return MD_E_INVAL;
     }
-    if (p->reserved0 != 0) { msg = "reserved fields must be zero"; return MD_E_INVAL; }
-    for (int k = 0; k < 3; ++k)
-        if (p->reserved[k] != 0) { msg = "reserved fields must be zero"; return MD_E_INVAL; }
+    if (p->reserved0 != 0 || p->reserved[0] != 0) { msg = "reserved fields must be zero"; return MD_E_INVAL; }
+    if (p->neigh_capacity < 0 || p->neigh_capacity_max < 0) {
+        msg = "neigh_capacity and neigh_capacity_max must be >= 0";
+        return MD_E_INVAL;
+    }
+    if (p->step_budget < 0) { msg = "step_budget must be >= 0"; return MD_E_INVAL; }
     {
         const int ci = p->check_interval;
         if (ci != 0 && (ci < 1 || ci > kUnroll || (ci & (ci - 1)) || kUnroll % ci)) {
@@ -321,6 +328,12 @@ int make_geometry(const md_params *p, int R, const int64_t *nrep, const double *
     std::vector<double> bx(box, box + R);
     std::vector<int64_t> nr(nrep, nrep + R);
     g.K = p->neigh_capacity > 0 ? (p->neigh_capacity + 7) / 8 * 8 : auto_capacity(p, g, bx, nr);
+    g.Kmax = p->neigh_capacity_max > 0 ? (p->neigh_capacity_max + 7) / 8 * 8 : 2 * g.K;
+    if (g.Kmax < g.K) {
+        msg = "neigh_capacity_max must be 0 or at least neigh_capacity";
+        return MD_E_INVAL;
+    }
+    if ((double)g.n * (double)g.Kmax > 4.0e12) { msg = "neighbour-list cap too large"; return MD_E_INVAL; }
     g.check = p->check_interval > 0 ? p->check_interval : (g.n >= kCheckLargeN ? 1 : kCheck);
     return MD_OK;
 }
@@ -359,11 +372,13 @@ Layout make_layout(const md_params *p, const Geometry &g)
     L.off_ccount = take(4 * (size_t)g.ncell);
     L.off_ccursor = take(4 * (size_t)g.ncell);
     L.off_cstart = take(4 * ((size_t)g.ncell + 1));
-    L.off_nbr = take(4 * n * (size_t)g.K);
+    L.off_nbr = take(4 * n * (size_t)g.Kmax);       // room for the cap: K grows in place
     L.off_nnbr = take(4 * n);
     L.off_part_f = take(8 * 12 * (size_t)g.nblk_f);
     L.off_part_i = take(8 * 4 * (size_t)g.nblk_i);
     L.off_ring = take(sizeof(mdk::Obs) * (size_t)cap * g.R);
+    L.off_epot = take(sizeof(double) * (size_t)cap * g.R);
+    L.off_epot_step = take(sizeof(long long) * (size_t)cap);
     L.off_totals = take(sizeof(mdk::Obs) * g.R);
     L.off_scale = take(8 * (size_t)g.R);
     L.off_st_pos = take(24 * n);
@@ -416,6 +431,7 @@ struct md_handle {
     double step_ms = 0.0, rebuild_ms = 0.0;
     int64_t step_launches = 0, rebuild_checks = 0;
     int64_t obs_read = 0;
+    int64_t epot_read = -1;          // newest step returned by md_epot_series
     int64_t n_species[2] = {0, 0};   // particles per species over all replicas
     std::string err;
 };
@@ -464,10 +480,20 @@ int rebuild_chain(const md_handle *h, ChainStep *seq)
     seq[1] = {k.scan, 1, kScanBlock};
     seq[2] = {k.scatter, nb, kIntBlock};
     seq[3] = {k.permute, nb, kIntBlock};
-    seq[4] = {k.nbuild, h->g.ncell, kNbBlock};          // one block per cell; its last block
-    return 5;                                            // makes the permuted buffers current
+    seq[4] = {k.nbuild, h->g.ncell, kNbBlock};          // one block per cell; its last block makes
+    return 5;                                            // the permuted buffers current or asks
+}                                                        // for a redo with a larger K
+
+// The redo of the build after its capacity grew: one block per cell as well.
+KArgs retry_args(const md_handle *h)
+{
+    KArgs a = h->a;
+    a.nb_retry = 1;
+    return a;
 }
 
+// Stream launches of the chain; the redo is launched every time and returns at
+// once unless the first build asked for it.
 int launch_rebuild(md_handle *h)
 {
     ChainStep seq[8];
@@ -477,7 +503,7 @@ int launch_rebuild(md_handle *h)
         if (rc)
             return rc;
     }
-    return MD_OK;
+    return launch(h, h->ks->nbuild, h->g.ncell, kNbBlock, retry_args(h));
 }
 
 // Arguments of the step kernel at position `slot` of the unrolled loop.
@@ -534,20 +560,39 @@ int add_kernel(md_handle *h, cudaGraph_t g, cudaGraphNode_t *node, const cudaGra
     return MD_OK;
 }
 
+int add_conditional(md_handle *h, cudaGraph_t g, cudaGraphNode_t *node, cudaGraphNode_t dep,
+                    cudaGraphConditionalHandle c, cudaGraphConditionalNodeType type, cudaGraph_t *body);
+
+// The rebuild chain as graph nodes, closed by a conditional redo of the build
+// that runs only when the build grew the list capacity.
 int add_rebuild_chain(md_handle *h, cudaGraph_t g)
 {
     ChainStep seq[8];
     const int ns = rebuild_chain(h, seq);
+    cudaGraphConditionalHandle c_regrow;
+    CK(h, cudaGraphConditionalHandleCreate(&c_regrow, g, 0, 0));
     cudaGraphNode_t prev = nullptr;
     for (int s = 0; s < ns; ++s) {
         cudaGraphNode_t node;
+        KArgs a = h->a;
+        if (seq[s].f == h->ks->nbuild) {
+            a.use_cond = 1;
+            a.set_regrow = 1;
+            a.h_regrow = c_regrow;
+        }
         int rc = add_kernel(h, g, &node, prev ? &prev : nullptr, prev ? 1 : 0, seq[s].f, seq[s].grid,
-                            seq[s].block, h->a);
+                            seq[s].block, a);
         if (rc)
             return rc;
         prev = node;
     }
-    return MD_OK;
+    cudaGraphNode_t n_if;
+    cudaGraph_t body;
+    int rc = add_conditional(h, g, &n_if, prev, c_regrow, cudaGraphCondTypeIf, &body);
+    if (rc)
+        return rc;
+    cudaGraphNode_t n_retry;
+    return add_kernel(h, body, &n_retry, nullptr, 0, h->ks->nbuild, h->g.ncell, kNbBlock, retry_args(h));
 }
 
 int add_conditional(md_handle *h, cudaGraph_t g, cudaGraphNode_t *node, cudaGraphNode_t dep,
@@ -692,7 +737,7 @@ const char *status_message(int code)
     switch (code) {
     case MD_E_NONFINITE: return "a position became non-finite; the step loop stopped";
     case MD_E_UNSTABLE: return "a particle moved more than a quarter box in one step; the step loop stopped";
-    case MD_E_CAPACITY: return "a neighbour list exceeded neigh_capacity; the step loop stopped";
+    case MD_E_CAPACITY: return "a neighbour list exceeded neigh_capacity_max; the step loop stopped";
     case MD_E_BOUNDS: return "an index left its array (bounds-checked build); the access was redirected";
     case MD_E_TIMEOUT: return "the device step loop exceeded its iteration bound";
     default: return "";
@@ -845,10 +890,10 @@ static int create_impl(md_handle *h, const md_params *p, const int32_t *species,
     a.n = (int)g.n;
     a.nrep = g.R;
     a.ncell = g.ncell;
-    a.K = g.K;
     a.tpp = g.tpp;
     a.si = p->sample_interval;
     a.obs_cap = h->cap;
+    a.epot_cap = h->cap;
     a.nblk_i = g.nblk_i;
     a.nblk_f = g.nblk_f;
     a.pa = w + L.off_pa; a.pb = w + L.off_pb; a.va = w + L.off_va; a.vb = w + L.off_vb;
@@ -872,6 +917,8 @@ static int create_impl(md_handle *h, const md_params *p, const int32_t *species,
     a.part_f = (double *)(w + L.off_part_f);
     a.part_i = (double *)(w + L.off_part_i);
     a.ring = (mdk::Obs *)(w + L.off_ring);
+    a.epot = (double *)(w + L.off_epot);
+    a.epot_step = (long long *)(w + L.off_epot_step);
     a.totals = (mdk::Obs *)(w + L.off_totals);
     a.ctl = (mdk::Ctl *)(w + L.off_ctl);
     a.rep = (const mdk::Rep *)(w + L.off_rep);
@@ -962,9 +1009,15 @@ static int create_impl(md_handle *h, const md_params *p, const int32_t *species,
             (rc = put(L.off_crank, g.crank.data(), sizeof(int) * g.ncell)) ||
             (rc = put(L.off_cxyz, g.cxyz.data(), sizeof(int4) * g.ncell)))
             return rc;
-        cudaError_t e = cudaMemsetAsync(a.ctl, 0, sizeof(mdk::Ctl), h->s);
-        if (e == cudaSuccess)
-            e = cudaMemsetAsync(a.ccount, 0, 4 * (size_t)g.ncell, h->s);
+        mdk::Ctl c0;
+        memset(&c0, 0, sizeof c0);
+        c0.K = g.K;
+        c0.Kmax = g.Kmax;
+        if ((rc = put(L.off_ctl, &c0, sizeof c0)))
+            return rc;
+        cudaError_t e = cudaMemsetAsync(a.ccount, 0, 4 * (size_t)g.ncell, h->s);
+        if (e == cudaSuccess)   // every slot of the per-step series empty (step -1)
+            e = cudaMemsetAsync(a.epot_step, 0xff, sizeof(long long) * (size_t)h->cap, h->s);
         if (e == cudaSuccess)
             e = cudaEventRecord(h->ev_stage, h->s);
         if (e != cudaSuccess)
@@ -1008,6 +1061,7 @@ int md_step(md_handle *h, int64_t nsteps)
     int rc;
     KArgs a = h->a;
     a.nsteps = nsteps;
+    a.budget = h->p.step_budget;
     if ((rc = launch(h, h->ks->set_steps, 1, 1, a)))
         return rc;
     if (h->p.use_graph) {
@@ -1382,6 +1436,44 @@ int md_observables(md_handle *h, md_obs *out, int32_t max_samples, int32_t *n_sa
     return MD_OK;
 }
 
+int md_epot_series(md_handle *h, int64_t *steps, double *e_pot, int32_t max_steps, int32_t *n_steps)
+{
+    ApiRange range_("md_epot_series");
+    if (!h || !n_steps || (max_steps > 0 && (!steps || !e_pot)))
+        return MD_E_INVAL;
+    *n_steps = 0;
+    mdk::Ctl c;
+    int rc = read_ctl(h, &c);
+    if (rc)
+        return rc;
+    const size_t cap = (size_t)h->cap, R = (size_t)h->g.R;
+    const size_t sb = align_up(sizeof(long long) * cap);
+    if ((rc = ensure_pinned(h, sb + sizeof(double) * cap * R)) || (rc = stage_wait(h)))
+        return rc;
+    CK(h, cudaMemcpyAsync(h->pin, h->a.epot_step, sizeof(long long) * cap, cudaMemcpyDeviceToHost, h->s));
+    CK(h, cudaMemcpyAsync(h->pin + sb, h->a.epot, sizeof(double) * cap * R, cudaMemcpyDeviceToHost, h->s));
+    CK(h, cudaStreamSynchronize(h->s));
+    const long long *st = (const long long *)h->pin;
+    const double *ev = (const double *)(h->pin + sb);
+    std::vector<std::pair<long long, size_t>> got;       // (step, slot) not yet returned
+    for (size_t k = 0; k < cap; ++k)
+        if (st[k] > h->epot_read)
+            got.push_back({st[k], k});
+    std::sort(got.begin(), got.end());
+    const size_t m = std::min<size_t>(got.size(), (size_t)std::max(max_steps, 0));
+    const size_t first = got.size() - m;                  // the newest m
+    for (size_t t = 0; t < m; ++t) {
+        steps[t] = got[first + t].first;
+        memcpy(e_pot + t * R, ev + got[first + t].second * R, sizeof(double) * R);
+    }
+    if (!got.empty())
+        h->epot_read = got.back().first;
+    *n_steps = (int32_t)m;
+    if (status_code(c.status) != MD_OK)
+        return check_device(h);
+    return MD_OK;
+}
+
 int md_get_state(md_handle *h, double *pos, double *vel, int32_t *image)
 {
     ApiRange range_("md_get_state");
@@ -1439,11 +1531,12 @@ int md_get_neighbours(md_handle *h, int32_t *counts, int32_t *lists, int32_t kma
     ApiRange range_("md_get_neighbours");
     if (!h || !counts || (lists && kmax < 1))
         return MD_E_INVAL;
-    const size_t n = (size_t)h->g.n, K = (size_t)h->g.K;
+    const size_t n = (size_t)h->g.n;
     int rc;
     mdk::Ctl c;
     if ((rc = read_ctl(h, &c)))
         return rc;
+    const size_t K = (size_t)c.K;                        // row stride of the lists in use
     if ((rc = ensure_pinned(h, 4 * n * K + 4 * n + 16 * n + 256)) || (rc = stage_wait(h)))
         return rc;
     char *q = h->pin;
@@ -1478,7 +1571,9 @@ int md_info(md_handle *h, md_info_t *out)
     memset(out, 0, sizeof *out);
     out->n_total = h->g.n;
     out->n_replicas = h->g.R;
-    out->neigh_capacity = h->g.K;
+    out->neigh_capacity = c.K;
+    out->neigh_capacity_max = h->g.Kmax;
+    out->regrows = c.regrows;
     out->threads_per_particle = h->g.tpp;
     out->check_interval = h->g.check;
     out->cells_per_edge = h->g.rep[0].nc;
@@ -1531,7 +1626,7 @@ int md_destroy(md_handle *h)
 const char *md_last_error(const md_handle *h)
 {
     if (!h)
-        return "null handle";
+        return md_noalloc_message();
     return h->err.c_str();
 }
 

@@ -38,7 +38,11 @@ struct Ctl {
     int pos_par;              // which of the two position buffers is current
     int state_par;            // which of the two velocity / image buffers is current
     int max_nbr;              // largest list length seen at the last build
-    int pad0;
+    int K;                    // list entries per particle in use (the row stride of nbr); grows
+                              // on the device when a build finds a longer list, up to Kmax
+    int Kmax;                 // capacity cap: nbr holds Kmax entries per particle
+    unsigned int regrow;      // 1: the last build overflowed K; K was raised and the build
+                              // must be redone before the lists are used
     long long step;           // time index of the current positions
     long long remaining;      // force evaluations left in the running md_step
     long long budget;         // loop-iteration bound of the running md_step
@@ -51,6 +55,7 @@ struct Ctl {
     long long dev_launches;
     float last_maxdisp2;
     float pad1;
+    long long regrows;        // builds redone with a larger K since md_create
 };
 
 struct Rep {                  // one independent system
@@ -83,10 +88,12 @@ struct __align__(32) d4 { double x, y, z, w; };
 
 // Every kernel takes this one struct by value.
 struct KArgs {
-    int n, nrep, ncell, K, tpp, si, obs_cap, imode, use_cond, fsample;
+    int n, nrep, ncell, tpp, si, obs_cap, epot_cap, imode, use_cond, fsample;
     int nblk_i, nblk_f;
     int lookahead;                    // MD steps until the next rebuild check (after this node)
     int set_rebuild, set_loop;        // this graph node sets the rebuild / loop condition
+    int nb_retry;                     // neighbour build: 0 = first pass, 1 = the redo after a regrow
+    int set_regrow;                   // this build node sets the regrow condition
     void *pa, *pb, *va, *vb;          // buffer 0: MIXED pos hi/lo, vel hi/lo (float4);
                                       // FP64 pos, vel (d4); FP32 pos, vel (float4)
     void *pa2, *pb2, *va2, *vb2;      // buffer 1 (positions: Ctl::pos_par, velocities: state_par)
@@ -103,6 +110,8 @@ struct KArgs {
                                       // chunk index, the slot of its partial sums)
     double *part_f, *part_i;          // per-block partial sums [nblk_f][12], [nblk_i][4]
     Obs *ring, *totals;
+    double *epot;                     // per-step potential energy [epot_cap][nrep], slot = step % cap
+    long long *epot_step;             // [epot_cap]: the step held by each slot (-1 = none)
     Ctl *ctl;
     const Rep *rep;
     double *st_pos, *st_vel, *st_f, *st_e;   // staging, original order
@@ -118,7 +127,8 @@ struct KArgs {
     long long nsteps;                 // for k_set_steps
     float hdtm_hi[2], hdtm_lo[2], dt_hi, dt_lo, inv_mass[2];
     float disp_thr2, disp_thr;        // (skin/2 - margin)^2 and skin/2 - margin
-    cudaGraphConditionalHandle h_loop, h_rebuild;
+    long long budget;                 // for k_set_steps: step-loop bound (0 = nsteps + 64)
+    cudaGraphConditionalHandle h_loop, h_rebuild, h_regrow;
 };
 
 // ---------------------------------------------------------------------------

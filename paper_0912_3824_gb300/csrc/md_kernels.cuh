@@ -135,6 +135,33 @@ __device__ __forceinline__ void block_max3(float &a, float &b, float &c, float *
     __syncthreads();
 }
 
+// Maxima of three non-negative floats and the sum of one double over the
+// block, valid in thread 0, with one pair of barriers.  The sum takes the
+// same steps as component 0 of block_sum (so a per-step potential energy
+// equals the one of a sample record bit for bit).
+__device__ __forceinline__ void block_max3_sum1(float &a, float &b, float &c, double &e, float *shf, double *sh)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    a = warp_max(a);
+    b = warp_max(b);
+    c = warp_max(c);
+    e = warp_sum(e);
+    if (lane == 0) {
+        shf[3 * w] = a;
+        shf[3 * w + 1] = b;
+        shf[3 * w + 2] = c;
+        sh[w] = e;
+    }
+    __syncthreads();
+    if (w == 0) {
+        a = warp_max(lane < nw ? shf[3 * lane] : 0.f);
+        b = warp_max(lane < nw ? shf[3 * lane + 1] : 0.f);
+        c = warp_max(lane < nw ? shf[3 * lane + 2] : 0.f);
+        e = warp_sum(lane < nw ? sh[lane] : 0.0);
+    }
+    __syncthreads();
+}
+
 __device__ __forceinline__ int species_of(float w) { return __float_as_int(w) & 15; }
 __device__ __forceinline__ int species_of(double w) { return (int)(__double_as_longlong(w) & 15); }
 
@@ -451,6 +478,8 @@ __device__ __forceinline__ void write_record(const KArgs &a, int mode, int r, co
     o.p[2] = v[11];
     o.max_disp = sqrt((double)md2);
     o.rebuilds = rebuilds;
+    if (mode == IM_LOOP || mode == IM_SAMPLE)
+        a.epot[(step % a.epot_cap) * a.nrep + r] = v[0];
     if (mode == IM_TOTALS)
         a.totals[r] = o;
     else if (mode == IM_KE) {
@@ -520,6 +549,34 @@ static __device__ void finish_reductions(const KArgs &a, int mode, bool from_f, 
     }
 }
 
+// The potential energy of every replica at a step that records no sample: the
+// per-block sums part_f[.][0] added exactly as finish_reductions adds them
+// (same threads, same order), into the per-step series.
+static __device__ void finish_epot(const KArgs &a, long long step, double *sh)
+{
+    const long long slot = step % a.epot_cap;
+    if (a.nrep <= 8) {
+        for (int r = 0; r < a.nrep; ++r) {
+            const Rep rp = a.rep[r];
+            double v[1] = {0.0};
+            for (int b = rp.bf0 + threadIdx.x; b < rp.bf1; b += blockDim.x)
+                v[0] += a.part_f[(size_t)b * kPartF];
+            block_sum<1>(v, sh);
+            if (threadIdx.x == 0)
+                a.epot[slot * a.nrep + r] = v[0];
+        }
+    } else {
+        for (int r = threadIdx.x; r < a.nrep; r += blockDim.x) {
+            const Rep rp = a.rep[r];
+            double v = 0.0;
+            for (int b = rp.bf0; b < rp.bf1; ++b)
+                v += a.part_f[(size_t)b * kPartF];
+            a.epot[slot * a.nrep + r] = v;
+        }
+        __syncthreads();
+    }
+}
+
 // Rebuild decision: the list built at the last rebuild holds every pair
 // within r_c + skin, so it stays complete while no particle has moved more
 // than skin/2.  The next check comes after `look` further drifts, each at
@@ -542,19 +599,25 @@ __device__ __forceinline__ unsigned int need_rebuild(const KArgs &a, float md2, 
 // carry no end-of-row masks.  Single precision: a group's contributions are
 // summed branch-free (zero factor outside the cutoff) and the group sum enters
 // a Kahan accumulator (MIXED; plain sum for FP32); lanes are combined in
-// double-single.  On return every lane of the particle holds the total force;
-// the energies and the virial come from pair_energy on sample steps.
+// double-single.  The pair potential is summed alongside, every step (the
+// potential energy is a per-step reduction of Sec. 2.2).  On return every lane
+// of the particle holds the total force and ep, half the sum of its pair
+// energies; the virial comes from pair_energy on sample steps.
 // ---------------------------------------------------------------------------
+// Entries per particle of the list rows in use (the capacity K, which the
+// neighbour build may raise on the device): read where a row starts.
+__device__ __forceinline__ int list_stride(const KArgs &a) { return a.ctl->K; }
+
 template <typename T> struct PairRow {   // parameters of (species i, species j = 0 / 1)
     T rc2[2], sig2[2], eps4[2], eps48[2], shift[2], rc[2], ihs[2];
 };
 
 template <int P, int TPP, bool SM>
 __device__ __forceinline__ void pair_forces(const KArgs &a, const Rep &rp, int pp, int ii, int nn,
-                                            FT<P> &fx, FT<P> &fy, FT<P> &fz)
+                                            FT<P> &fx, FT<P> &fy, FT<P> &fz, double &ep)
 {
     const int lane = threadIdx.x & (TPP - 1);
-    const int *lst = a.nbr + (size_t)ii * (size_t)a.K;
+    const int *lst = a.nbr + (size_t)ii * (size_t)list_stride(a);
     if constexpr (P == FP64) {
         const d4 *pos = (const d4 *)pos_a(a, pp);
         const d4 xi = pos[ii];
@@ -570,7 +633,7 @@ __device__ __forceinline__ void pair_forces(const KArgs &a, const Rep &rp, int p
             pr.rc[tj] = a.tab.rcd[ti * 2 + tj];
             pr.ihs[tj] = a.tab.ihsd[ti * 2 + tj];
         }
-        double sx = 0, sy = 0, sz = 0;
+        double sx = 0, sy = 0, sz = 0, se = 0;
         for (int k0 = 4 * lane; k0 < nn; k0 += 4 * TPP) {
             const int4 q = __ldg((const int4 *)(lst + k0));
             const int jj[4] = {q.x, q.y, q.z, q.w};
@@ -591,13 +654,13 @@ __device__ __forceinline__ void pair_forces(const KArgs &a, const Rep &rp, int p
                     const double s2 = pr.sig2[tj] * ir2;
                     const double s6 = s2 * s2 * s2;
                     double fr = pr.eps48[tj] * ir2 * s6 * (s6 - 0.5);
-                    if (SM) {
-                        double v = pr.eps4[tj] * s6 * (s6 - 1.0) - pr.shift[tj];
+                    double v = pr.eps4[tj] * s6 * (s6 - 1.0) - pr.shift[tj];
+                    if (SM)
                         smooth_pair(r2, pr.rc[tj], pr.ihs[tj], fr, v);
-                    }
                     sx += fr * dx;
                     sy += fr * dy;
                     sz += fr * dz;
+                    se += v;
                 }
             }
         }
@@ -606,8 +669,10 @@ __device__ __forceinline__ void pair_forces(const KArgs &a, const Rep &rp, int p
             sx += __shfl_xor_sync(0xffffffffu, sx, o);
             sy += __shfl_xor_sync(0xffffffffu, sy, o);
             sz += __shfl_xor_sync(0xffffffffu, sz, o);
+            se += __shfl_xor_sync(0xffffffffu, se, o);
         }
         fx = sx; fy = sy; fz = sz;
+        ep = 0.5 * se;
     } else {
         // MIXED reads the fixed-point copy (16 B per neighbour), FP32 the positions
         const float4 *pos = (const float4 *)pos_a(a, pp);
@@ -633,7 +698,7 @@ __device__ __forceinline__ void pair_forces(const KArgs &a, const Rep &rp, int p
             pr.rc[tj] = a.tab.rc[ti * 2 + tj];
             pr.ihs[tj] = a.tab.ihs[ti * 2 + tj];
         }
-        float sx = 0.f, sy = 0.f, sz = 0.f, cx = 0.f, cy = 0.f, cz = 0.f;
+        float sx = 0.f, sy = 0.f, sz = 0.f, cx = 0.f, cy = 0.f, cz = 0.f, se = 0.f, ce = 0.f;
         // list indices are loaded kPfDepth iterations ahead, so that only the
         // position gathers remain on each iteration's critical path
         // (K is a multiple of 8: every 16-byte index load is in bounds and aligned)
@@ -676,7 +741,7 @@ __device__ __forceinline__ void pair_forces(const KArgs &a, const Rep &rp, int p
                 else
                     Hs[u] = __ldg(pos + j);
             }
-            float gx = 0.f, gy = 0.f, gz = 0.f;
+            float gx = 0.f, gy = 0.f, gz = 0.f, gv = 0.f;
 #pragma unroll
             for (int u = 0; u < kUnr; ++u) {
                 int tj;
@@ -703,61 +768,69 @@ __device__ __forceinline__ void pair_forces(const KArgs &a, const Rep &rp, int p
                 const float s2 = sig2 * ir2;
                 const float s6 = s2 * s2 * s2;
                 float fr = in ? eps48 * ir2 * s6 * (s6 - 0.5f) : 0.0f;
-                if (SM) {
-                    const float eps4 = tj ? pr.eps4[1] : pr.eps4[0];
-                    const float shift = tj ? pr.shift[1] : pr.shift[0];
-                    float v = in ? eps4 * s6 * (s6 - 1.0f) - shift : 0.0f;
+                const float eps4 = tj ? pr.eps4[1] : pr.eps4[0];
+                const float shift = tj ? pr.shift[1] : pr.shift[0];
+                float v = in ? fmaf(eps4, s6 * s6 - s6, -shift) : 0.0f;
+                if (SM)
                     smooth_pair(in ? r2 : 1.0f, tj ? pr.rc[1] : pr.rc[0], tj ? pr.ihs[1] : pr.ihs[0], fr, v);
-                }
                 gx = fmaf(fr, dx, gx);
                 gy = fmaf(fr, dy, gy);
                 gz = fmaf(fr, dz, gz);
+                gv += v;
             }
             if constexpr (P == MIXED) {
                 kahan_add(sx, cx, gx);
                 kahan_add(sy, cy, gy);
                 kahan_add(sz, cz, gz);
+                kahan_add(se, ce, gv);
             } else {
                 sx += gx;
                 sy += gy;
                 sz += gz;
+                se += gv;
             }
         }
         if constexpr (P == MIXED) {
-            ds ax = ds_from(sx, -cx), ay = ds_from(sy, -cy), az = ds_from(sz, -cz);
+            ds ax = ds_from(sx, -cx), ay = ds_from(sy, -cy), az = ds_from(sz, -cz), ae = ds_from(se, -ce);
 #pragma unroll
             for (int o = TPP / 2; o > 0; o >>= 1) {
                 ds bx = ds_from(__shfl_xor_sync(0xffffffffu, ax.hi, o), __shfl_xor_sync(0xffffffffu, ax.lo, o));
                 ds by = ds_from(__shfl_xor_sync(0xffffffffu, ay.hi, o), __shfl_xor_sync(0xffffffffu, ay.lo, o));
                 ds bz = ds_from(__shfl_xor_sync(0xffffffffu, az.hi, o), __shfl_xor_sync(0xffffffffu, az.lo, o));
+                ds be = ds_from(__shfl_xor_sync(0xffffffffu, ae.hi, o), __shfl_xor_sync(0xffffffffu, ae.lo, o));
                 ax = ds_add(ax, bx);
                 ay = ds_add(ay, by);
                 az = ds_add(az, bz);
+                ae = ds_add(ae, be);
             }
             fx = __fadd_rn(ax.hi, ax.lo);
             fy = __fadd_rn(ay.hi, ay.lo);
             fz = __fadd_rn(az.hi, az.lo);
+            ep = 0.5 * ds_to_double(ae);
         } else {
 #pragma unroll
             for (int o = TPP / 2; o > 0; o >>= 1) {
                 sx += __shfl_xor_sync(0xffffffffu, sx, o);
                 sy += __shfl_xor_sync(0xffffffffu, sy, o);
                 sz += __shfl_xor_sync(0xffffffffu, sz, o);
+                se += __shfl_xor_sync(0xffffffffu, se, o);
             }
             fx = sx; fy = sy; fz = sz;
+            ep = 0.5 * (double)se;
         }
     }
 }
 
-// Potential energy, virial and virial tensor of particle ii (half of each pair,
-// Sec. 2.2 reductions), as a separate pass over the list on sample steps so
-// that the force loop carries no energy accumulators.  acc[0..7] = E, W, W_ab.
+// Virial and virial tensor of particle ii (half of each pair, the less
+// frequent reductions of Sec. 2.2), as a separate pass over the list on sample
+// steps so that the every-step loop carries no virial accumulators.
+// acc[1..7] = W, W_xx, W_yy, W_zz, W_xy, W_xz, W_yz; acc[0] is left as it is.
 template <int P, int TPP, bool SM>
-__device__ __forceinline__ void pair_energy(const KArgs &a, const Rep &rp, int pp, int ii, int nn, double *acc)
+__device__ __forceinline__ void pair_virial(const KArgs &a, const Rep &rp, int pp, int ii, int nn, double *acc)
 {
     const int lane = threadIdx.x & (TPP - 1);
-    const int *lst = a.nbr + (size_t)ii * (size_t)a.K;
-    FT<P> d8[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    const int *lst = a.nbr + (size_t)ii * (size_t)list_stride(a);
+    FT<P> d7[7] = {0, 0, 0, 0, 0, 0, 0};
     if constexpr (P == FP64) {
         const d4 *pos = (const d4 *)pos_a(a, pp);
         const d4 xi = pos[ii];
@@ -769,78 +842,73 @@ __device__ __forceinline__ void pair_energy(const KArgs &a, const Rep &rp, int p
             const double dy = sep_d(xi.y, xj.y, rp.L, rp.invL);
             const double dz = sep_d(xi.z, xj.z, rp.L, rp.invL);
             const double r2 = dx * dx + dy * dy + dz * dz;
-            if (r2 < a.tab.rc2d[ab]) {
+            if (r2 < a.tab.rc2d[ab] && r2 > 0.0) {
                 const double ir2 = 1.0 / r2;
                 const double s2 = a.tab.sig2d[ab] * ir2;
                 const double s6 = s2 * s2 * s2;
                 double fr = a.tab.eps48d[ab] * ir2 * s6 * (s6 - 0.5);
-                double v = a.tab.eps4d[ab] * s6 * (s6 - 1.0) - a.tab.shiftd[ab];
-                if (SM)
+                if (SM) {
+                    double v = a.tab.eps4d[ab] * s6 * (s6 - 1.0) - a.tab.shiftd[ab];
                     smooth_pair(r2, a.tab.rcd[ab], a.tab.ihsd[ab], fr, v);
-                d8[0] += v;
-                d8[1] += fr * r2;
-                d8[2] += fr * dx * dx; d8[3] += fr * dy * dy; d8[4] += fr * dz * dz;
-                d8[5] += fr * dx * dy; d8[6] += fr * dx * dz; d8[7] += fr * dy * dz;
-            }
-        }
-    } else if constexpr (P == MIXED) {
-        const int4 *qp = q_of(a, pp);
-        const int4 Qi = qp[ii];
-        for (int k = lane; k < nn; k += TPP) {
-            const int4 Qj = __ldg(qp + checked(a, __ldg(lst + k), a.n, ii));
-            const int ab = Qi.w * 2 + Qj.w;
-            const float dx = sep_q(Qi.x, Qj.x, rp.qunit);
-            const float dy = sep_q(Qi.y, Qj.y, rp.qunit);
-            const float dz = sep_q(Qi.z, Qj.z, rp.qunit);
-            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            if (r2 < a.tab.rc2[ab]) {
-                const float ir2 = __fdividef(1.0f, r2);
-                const float s2 = a.tab.sig2[ab] * ir2;
-                const float s6 = s2 * s2 * s2;
-                float fr = a.tab.eps48[ab] * ir2 * s6 * (s6 - 0.5f);
-                float v = a.tab.eps4[ab] * s6 * (s6 - 1.0f) - a.tab.shift[ab];
-                if (SM)
-                    smooth_pair(r2, a.tab.rc[ab], a.tab.ihs[ab], fr, v);
-                d8[0] += v;
-                d8[1] += fr * r2;
-                d8[2] += fr * dx * dx; d8[3] += fr * dy * dy; d8[4] += fr * dz * dz;
-                d8[5] += fr * dx * dy; d8[6] += fr * dx * dz; d8[7] += fr * dy * dz;
+                }
+                d7[0] += fr * r2;
+                d7[1] += fr * dx * dx; d7[2] += fr * dy * dy; d7[3] += fr * dz * dz;
+                d7[4] += fr * dx * dy; d7[5] += fr * dx * dz; d7[6] += fr * dy * dz;
             }
         }
     } else {
+        const int4 *qp = q_of(a, pp);
         const float4 *pos = (const float4 *)pos_a(a, pp);
-        const float4 Hi = pos[ii];
-        const int ti = species_of(Hi.w);
+        int4 Qi = make_int4(0, 0, 0, 0);
+        float4 Hi = make_float4(0.f, 0.f, 0.f, 0.f);
+        int ti;
+        if constexpr (P == MIXED) {
+            Qi = qp[ii];
+            ti = Qi.w;
+        } else {
+            Hi = pos[ii];
+            ti = species_of(Hi.w);
+        }
         for (int k = lane; k < nn; k += TPP) {
             const int j = checked(a, __ldg(lst + k), a.n, ii);
-            const float4 Hj = __ldg(pos + j);
-            const int ab = ti * 2 + species_of(Hj.w);
-            const float dx = sep_f(Hi.x, Hj.x, rp.Lhi, rp.invLf);
-            const float dy = sep_f(Hi.y, Hj.y, rp.Lhi, rp.invLf);
-            const float dz = sep_f(Hi.z, Hj.z, rp.Lhi, rp.invLf);
+            float dx, dy, dz;
+            int ab;
+            if constexpr (P == MIXED) {
+                const int4 Qj = __ldg(qp + j);
+                ab = ti * 2 + Qj.w;
+                dx = sep_q(Qi.x, Qj.x, rp.qunit);
+                dy = sep_q(Qi.y, Qj.y, rp.qunit);
+                dz = sep_q(Qi.z, Qj.z, rp.qunit);
+            } else {
+                const float4 Hj = __ldg(pos + j);
+                ab = ti * 2 + species_of(Hj.w);
+                dx = sep_f(Hi.x, Hj.x, rp.Lhi, rp.invLf);
+                dy = sep_f(Hi.y, Hj.y, rp.Lhi, rp.invLf);
+                dz = sep_f(Hi.z, Hj.z, rp.Lhi, rp.invLf);
+            }
             const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            if (r2 < a.tab.rc2[ab]) {
+            if (r2 < a.tab.rc2[ab] && r2 > 0.0f) {
                 const float ir2 = __fdividef(1.0f, r2);
                 const float s2 = a.tab.sig2[ab] * ir2;
                 const float s6 = s2 * s2 * s2;
                 float fr = a.tab.eps48[ab] * ir2 * s6 * (s6 - 0.5f);
-                float v = a.tab.eps4[ab] * s6 * (s6 - 1.0f) - a.tab.shift[ab];
-                if (SM)
+                if (SM) {
+                    float v = a.tab.eps4[ab] * s6 * (s6 - 1.0f) - a.tab.shift[ab];
                     smooth_pair(r2, a.tab.rc[ab], a.tab.ihs[ab], fr, v);
-                d8[0] += v;
-                d8[1] += fr * r2;
-                d8[2] += fr * dx * dx; d8[3] += fr * dy * dy; d8[4] += fr * dz * dz;
-                d8[5] += fr * dx * dy; d8[6] += fr * dx * dz; d8[7] += fr * dy * dz;
+                }
+                d7[0] += fr * r2;
+                d7[1] += fr * dx * dx; d7[2] += fr * dy * dy; d7[3] += fr * dz * dz;
+                d7[4] += fr * dx * dy; d7[5] += fr * dx * dz; d7[6] += fr * dy * dz;
             }
         }
     }
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-        double v = (double)d8[k];
+    for (int k = 0; k < 7; ++k) {
+        double v = (double)d7[k];
 #pragma unroll
         for (int o = TPP / 2; o > 0; o >>= 1)
             v += __shfl_xor_sync(0xffffffffu, v, o);
-        acc[k] = 0.5 * v;
+        acc[1 + k] = 0.5 * v;
     }
 }
 
@@ -875,20 +943,22 @@ __device__ __forceinline__ void force_only(const KArgs &a)
     const int ii = valid ? i : b.x;
     const int nn = valid ? a.nnbr[ii] : 0;
     FT<P> fx, fy, fz;
+    double ep;
     double acc[kPartF];
 #pragma unroll
     for (int k = 0; k < kPartF; ++k)
         acc[k] = 0.0;
-    pair_forces<P, TPP, SM>(a, rp, pp, ii, nn, fx, fy, fz);
+    pair_forces<P, TPP, SM>(a, rp, pp, ii, nn, fx, fy, fz, ep);
+    acc[0] = ep;
     if (SAMPLE)
-        pair_energy<P, TPP, SM>(a, rp, pp, ii, nn, acc);
+        pair_virial<P, TPP, SM>(a, rp, pp, ii, nn, acc);
     if (!(valid && lane == 0)) {
 #pragma unroll
         for (int k = 0; k < kPartF; ++k)
             acc[k] = 0.0;
     }
     if (valid && lane == 0)
-        store_force<P>(a, i, fx, fy, fz, SAMPLE ? acc[0] : 0.0);
+        store_force<P>(a, i, fx, fy, fz, ep);
     if (SAMPLE) {
         block_sum<kPartF>(acc, sh);
         if (threadIdx.x == 0)
@@ -1051,12 +1121,14 @@ __device__ __forceinline__ void step_body_split(const KArgs &a, bool active, boo
         }
     }
     FT<P> fx = 0, fy = 0, fz = 0;
+    double ep = 0.0;
 #pragma unroll
     for (int k = 0; k < kPartF; ++k)
         part[k] = 0.0;
-    pair_forces<P, TPP, SM>(a, rp, pp, ii, nn, fx, fy, fz);
+    pair_forces<P, TPP, SM>(a, rp, pp, ii, nn, fx, fy, fz, ep);
+    part[0] = ep;
     if (SAMPLE)
-        pair_energy<P, TPP, SM>(a, rp, pp, ii, nn, part);
+        pair_virial<P, TPP, SM>(a, rp, pp, ii, nn, part);
     // Every lane of the warp must reach the shuffles below, including the
     // lanes of padding particles past the end of a replica's range: they skip
     // the update and contribute zeros.
@@ -1068,7 +1140,7 @@ __device__ __forceinline__ void step_body_split(const KArgs &a, bool active, boo
             sp = species_of(((const float *)pos_a(a, pp))[4 * (size_t)i + 3]);
     }
     if (valid && lane == 0)
-        store_force<P>(a, i, fx, fy, fz, SAMPLE ? part[0] : 0.0);
+        store_force<P>(a, i, fx, fy, fz, ep);
     double ke = 0.0, p3[3] = {0.0, 0.0, 0.0};
     float dd = 0.f, vv = 0.f;
 #pragma unroll
@@ -1155,19 +1227,21 @@ __device__ __forceinline__ void step_body(const KArgs &a, bool active, bool last
     const int ii = (i < b.y) ? i : b.x;
     const int nn = valid ? a.nnbr[ii] : 0;
     FT<P> fx = 0, fy = 0, fz = 0;
+    double ep = 0.0;
 #pragma unroll
     for (int k = 0; k < kPartF; ++k)
         part[k] = 0.0;
-    pair_forces<P, TPP, SM>(a, rp, pp, ii, nn, fx, fy, fz);
+    pair_forces<P, TPP, SM>(a, rp, pp, ii, nn, fx, fy, fz, ep);
+    part[0] = ep;
     if (SAMPLE)
-        pair_energy<P, TPP, SM>(a, rp, pp, ii, nn, part);
+        pair_virial<P, TPP, SM>(a, rp, pp, ii, nn, part);
     if (!(valid && lane == 0)) {
 #pragma unroll
         for (int k = 0; k < kPartF; ++k)
             part[k] = 0.0;
         return;
     }
-    store_force<P>(a, i, fx, fy, fz, SAMPLE ? part[0] : 0.0);
+    store_force<P>(a, i, fx, fy, fz, ep);
     PState<P> s;
     load_pos<P>(a, pp, i, s);
     load_vel<P>(a, spar, i, s);
@@ -1191,7 +1265,7 @@ __global__ void __launch_bounds__(kForceBlock) k_step(KArgs a)
     __shared__ double sh[32 * kPartF];
     __shared__ float shf[96];
     __shared__ int s_last;
-    __shared__ float s_m[3];
+    __shared__ float s_m[4];
     Ctl *ctl = a.ctl;
     const unsigned int st0 = ctl->status;
     const long long step = ctl->step;
@@ -1217,14 +1291,21 @@ __global__ void __launch_bounds__(kForceBlock) k_step(KArgs a)
     if (bad)
         atomicOr(&ctl->status, bad);
 
-    block_max3(d2, v2, a2, shf);
-    if (sample)
+    if (sample) {
+        block_max3(d2, v2, a2, shf);
         block_sum<kPartF>(part, sh);
+    } else {
+        block_max3_sum1(d2, v2, a2, part[0], shf, sh);
+    }
     if (threadIdx.x == 0) {
-        if (sample)
+        const size_t pb = (size_t)a.blk_f[blockIdx.x].w * kPartF;
+        if (sample) {
 #pragma unroll
             for (int k = 0; k < kPartF; ++k)
-                a.part_f[(size_t)a.blk_f[blockIdx.x].w * kPartF + k] = part[k];
+                a.part_f[pb + k] = part[k];
+        } else {
+            a.part_f[pb] = part[0];
+        }
         if (d2 > 0.f)
             atomicMax(&ctl->maxdisp2, __float_as_uint(d2));
         if (v2 > 0.f)
@@ -1245,12 +1326,17 @@ __global__ void __launch_bounds__(kForceBlock) k_step(KArgs a)
         s_m[0] = __uint_as_float(atomicExch(&ctl->maxdisp2, 0u));
         s_m[1] = __uint_as_float(atomicExch(&ctl->maxv2, 0u));
         s_m[2] = __uint_as_float(atomicExch(&ctl->maxa2, 0u));
+        s_m[3] = ctl->last_maxdisp2;    // displacement of r(step), the positions of this sample
     }
     __syncthreads();
     const unsigned int st = atomicOr(&ctl->status, 0u);
     if (sample && st == 0u)
-        finish_reductions(a, IM_LOOP, true, step, s_m[0], sh);
+        finish_reductions(a, IM_LOOP, true, step, s_m[3], sh);   // (its E_pot enters the series)
+    else if (remaining > 0 && st == 0u)
+        finish_epot(a, step, sh);
     if (threadIdx.x == 0) {
+        if (remaining > 0 && st == 0u)
+            a.epot_step[step % a.epot_cap] = step;
         const bool drifted = active && !last;
         unsigned int reb = 0u;
         if (drifted && st == 0u) {
@@ -1387,8 +1473,10 @@ __global__ void __launch_bounds__(kIntBlock) k_integrate(KArgs a)
         }
         if (first)
             ctl->rebuild = reb;
-        if (mode == IM_SAMPLE && st == 0u)
+        if (mode == IM_SAMPLE && st == 0u) {
             ctl->obs_count += 1;
+            a.epot_step[step % a.epot_cap] = step;
+        }
         ctl->ticket = 0u;
         ctl->n_integrate += 1;
         if (a.use_cond && a.set_rebuild)
@@ -1681,10 +1769,12 @@ __device__ __forceinline__ float box_gap(float x, float c, float h, float L, flo
     return fmaxf(fabsf(sep_f(x, c, L, invL)) - h, 0.0f);
 }
 
-// Lists of the particles of cell blockIdx.x, from the positions in buffer pn
-// (the permuted copy being built).
+// Lists of the particles of cell c, from the positions in buffer pn (the
+// permuted copy being built), with rows of K entries.  Every particle's full
+// count is recorded in max_nbr; entries beyond K are dropped (the build's last
+// block then grows K and the build is redone).
 template <int P>
-__device__ __forceinline__ void nbuild_cell(const KArgs &a, int pn)
+__device__ __forceinline__ void nbuild_cell(const KArgs &a, int pn, int c, int K)
 {
     __shared__ float4 s_pos[kNbCap];
     __shared__ int s_idx[kNbCap];
@@ -1694,7 +1784,6 @@ __device__ __forceinline__ void nbuild_cell(const KArgs &a, int pn)
     __shared__ int s_wsum[kNbBlock / 32];
 
     Ctl *ctl = a.ctl;
-    const int c = blockIdx.x;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     constexpr int NW = kNbBlock / 32;
     const int4 cc = a.cxyz[c];
@@ -1810,8 +1899,8 @@ __device__ __forceinline__ void nbuild_cell(const KArgs &a, int pn)
                         const bool in = sv && jj != i && r2 < (tj ? rl1[p] : rl0[p]);
                         const unsigned mm = __ballot_sync(0xffffffffu, in);
                         const int at = cnt[p] + __popc(mm & lt_mask);
-                        if (in && at < a.K)
-                            a.nbr[(size_t)i * (size_t)a.K + at] = jj;
+                        if (in && at < K)
+                            a.nbr[(size_t)i * (size_t)K + at] = jj;
                         cnt[p] += __popc(mm);
                     }
                 }
@@ -1826,51 +1915,86 @@ __device__ __forceinline__ void nbuild_cell(const KArgs &a, int pn)
         }
         for (int o = tid; o < nown; o += kNbBlock) {
             const int cnt = s_cnt[o];
-            a.nnbr[ob + o] = cnt < a.K ? cnt : a.K;
+            a.nnbr[ob + o] = cnt < K ? cnt : K;
             // pad the row with the particle itself to a multiple of kUnr entries, so the
             // pair loop reads whole groups without masking (K is a multiple of 8)
-            for (int k = cnt; k < (cnt + kUnr - 1) / kUnr * kUnr && k < a.K; ++k)
-                a.nbr[(size_t)(ob + o) * (size_t)a.K + k] = ob + o;
+            for (int k = cnt; k < (cnt + kUnr - 1) / kUnr * kUnr && k < K; ++k)
+                a.nbr[(size_t)(ob + o) * (size_t)K + k] = ob + o;
             atomicMax(&ctl->max_nbr, cnt);
-            if (cnt > a.K) {
-                atomicOr(&ctl->status, ST_OVERFLOW);
-                __threadfence();            // performed before this block's ticket
-            }
         }
         __syncthreads();
     }
 }
 
-// The neighbour build closes the rebuild chain: the last block to finish (ticket
-// pattern) makes the permuted buffers current, unless a list overflowed.  The
-// pending check is read once per block (the status can change during the
-// launch) and every block takes a ticket.
+// List capacity after a build whose longest list held mx > K entries (the
+// fixed-size list of Sec. 2.2 grown in place): a quarter more than needed,
+// rounded up to whole groups of 8, at most the cap Kmax (a multiple of 8, so
+// the result still holds mx entries whenever mx <= Kmax).
+__device__ __forceinline__ int grown_capacity(int mx, int Kmax)
+{
+    const int want = (mx + (mx + 3) / 4 + 7) / 8 * 8;
+    return want < Kmax ? want : Kmax;
+}
+
+// The neighbour build closes the rebuild chain.  The last block to finish
+// (ticket pattern) reads the longest list of the build and
+//   - makes the permuted buffers current if every list fitted its K entries;
+//   - otherwise, if the longest list fits the cap, raises K (grown_capacity)
+//     and asks for the build to be redone (Ctl::regrow, and the graph's regrow
+//     condition): the redo (nb_retry = 1, same positions, so the same counts)
+//     then fits, and its last block makes the buffers current;
+//   - otherwise reports ST_OVERFLOW, leaving the buffers of the last completed
+//     step current.
+// The pending check is read once per block (the status can change during the
+// launch) and every block takes a ticket.  Blocks take cells blockIdx.x,
+// blockIdx.x + gridDim.x, ...
 template <int P>
 __global__ void __launch_bounds__(kNbBlock) k_nbuild(KArgs a)
 {
-    __shared__ int s_go;
+    __shared__ int s_go, s_K;
     Ctl *ctl = a.ctl;
-    if (threadIdx.x == 0)
-        s_go = rebuild_pending(ctl) ? 1 : 0;
+    if (threadIdx.x == 0) {
+        s_go = (rebuild_pending(ctl) && (a.nb_retry == 0 || ctl->regrow != 0u)) ? 1 : 0;
+        s_K = ctl->K;
+    }
     __syncthreads();
     if (s_go) {
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             atomicAdd((unsigned long long *)&ctl->n_rebuild_k, 1ull);
-            atomicAdd((unsigned long long *)&ctl->rebuilds, 1ull);
+            if (a.nb_retry)
+                atomicAdd((unsigned long long *)&ctl->regrows, 1ull);
+            else
+                atomicAdd((unsigned long long *)&ctl->rebuilds, 1ull);
         }
-        nbuild_cell<P>(a, ctl->pos_par ^ 1);
+        const int pn = ctl->pos_par ^ 1;
+        for (int c = blockIdx.x; c < a.ncell; c += gridDim.x)
+            nbuild_cell<P>(a, pn, c, s_K);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        // (the last block reads nothing the others wrote but the status word, an
-        // atomic, which an overflowing thread fenced before the barrier above)
+        __threadfence();                    // this block's list counts before its ticket
         const unsigned int t = atomicAdd(&ctl->ticket, 1u);
         if (t == gridDim.x - 1) {
-            if (ctl->rebuild != 0u && atomicOr(&ctl->status, 0u) == 0u) {
-                ctl->pos_par ^= 1;
-                ctl->state_par ^= 1;
+            __threadfence();
+            unsigned int regrow = 0u;
+            if (s_go && atomicOr(&ctl->status, 0u) == 0u) {
+                const int mx = atomicMax(&ctl->max_nbr, 0);
+                if (mx <= s_K) {
+                    ctl->pos_par ^= 1;
+                    ctl->state_par ^= 1;
+                    ctl->last_maxdisp2 = 0.f;   // the lists start from these positions
+                } else if (mx <= ctl->Kmax && a.nb_retry == 0) {
+                    ctl->K = grown_capacity(mx, ctl->Kmax);
+                    regrow = 1u;
+                } else {
+                    atomicOr(&ctl->status, ST_OVERFLOW);
+                }
             }
+            if (s_go || a.nb_retry == 0)
+                ctl->regrow = regrow;
             ctl->ticket = 0u;
+            if (a.use_cond && a.set_regrow)
+                cudaGraphSetConditional(a.h_regrow, regrow);
         }
     }
 }
@@ -2036,7 +2160,7 @@ template <int P>
 __global__ void k_set_steps(KArgs a)
 {
     a.ctl->remaining = a.nsteps;
-    a.ctl->budget = a.nsteps + 64;
+    a.ctl->budget = a.budget > 0 ? a.budget : a.nsteps + 64;
     a.ctl->n_other += 1;
 }
 

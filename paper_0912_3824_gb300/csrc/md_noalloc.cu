@@ -16,6 +16,8 @@
 // device address is looked up once per device with cudaGetSymbolAddress().
 #include <cuda_runtime.h>
 
+#include <cstddef>
+#include <cstdio>
 #include <mutex>
 
 #include "md.h"
@@ -29,12 +31,14 @@ constexpr int kMaxDevices = 64;
 
 static_assert((long long)kMaxBlocks * kBlock == MD_NOALLOC_MAX_N, "scratch sized for MD_NOALLOC_MAX_N");
 
-// Per-block partial sums and the ticket that elects the block finishing the
-// totals (512 KiB + 256 B).
+// Per-block partial sums, the ticket that elects the block finishing the
+// totals, and a flag raised by any block that met a species outside
+// [0, n_species) (512 KiB + 256 B).  ticket and bad are cleared by every call.
 struct Scratch {
     double part[kMaxBlocks * kPart];
     unsigned int ticket;
-    unsigned int pad[63];
+    unsigned int bad;
+    unsigned int pad[62];
 };
 
 static __device__ __align__(256) Scratch g_noalloc_scratch;
@@ -48,11 +52,22 @@ __device__ __forceinline__ double min_image(double d, double L, double invL)
     return d - L * rint(d * invL);
 }
 
+// Species code of a particle, clamped into [0, nsp) so that it always indexes
+// the pair table; an out-of-range code raises the call's bad flag.
+__device__ __forceinline__ int species_in_range(int t, int nsp, Scratch *s)
+{
+    if (t < 0 || t >= nsp) {
+        atomicOr(&s->bad, 1u);
+        return t < 0 ? 0 : nsp - 1;
+    }
+    return t;
+}
+
 // One thread per particle i, looping over every j through shared-memory tiles
 // of positions; pair arithmetic in double (FP64 mode) or single precision on
 // separations formed in double (the other modes).
 template <bool FP64MATH>
-__global__ void __launch_bounds__(kBlock) k_forces_allpairs(Pot pot, int n, double L, const int *species,
+__global__ void __launch_bounds__(kBlock) k_forces_allpairs(Pot pot, int n, int nsp, double L, const int *species,
                                                             const double *pos, double *force, double *energy,
                                                             double *totals, Scratch *s)
 {
@@ -64,11 +79,13 @@ __global__ void __launch_bounds__(kBlock) k_forces_allpairs(Pot pot, int n, doub
     const double invL = 1.0 / L;
     double xi = 0.0, yi = 0.0, zi = 0.0;
     int ti = 0;
+    bool ti_bad = false;
     if (i < n) {
         xi = pos[3 * (size_t)i];
         yi = pos[3 * (size_t)i + 1];
         zi = pos[3 * (size_t)i + 2];
-        ti = species[i];
+        ti_bad = species[i] < 0 || species[i] >= nsp;
+        ti = species_in_range(species[i], nsp, s);
     }
     double fx = 0.0, fy = 0.0, fz = 0.0, acc[kPart] = {0, 0, 0, 0, 0, 0, 0, 0};
     for (int j0 = 0; j0 < n; j0 += kBlock) {
@@ -77,7 +94,7 @@ __global__ void __launch_bounds__(kBlock) k_forces_allpairs(Pot pot, int n, doub
             tx[threadIdx.x] = pos[3 * (size_t)j];
             ty[threadIdx.x] = pos[3 * (size_t)j + 1];
             tz[threadIdx.x] = pos[3 * (size_t)j + 2];
-            tt[threadIdx.x] = species[j];
+            tt[threadIdx.x] = species_in_range(species[j], nsp, s);
         }
         __syncthreads();
         const int m = min(kBlock, n - j0);
@@ -122,11 +139,12 @@ __global__ void __launch_bounds__(kBlock) k_forces_allpairs(Pot pot, int n, doub
         __syncthreads();
     }
     if (i < n) {
-        force[3 * (size_t)i] = fx;
-        force[3 * (size_t)i + 1] = fy;
-        force[3 * (size_t)i + 2] = fz;
+        const double poison = ti_bad ? __longlong_as_double(0x7ff8000000000000ll) : 0.0;   // NaN
+        force[3 * (size_t)i] = fx + poison;
+        force[3 * (size_t)i + 1] = fy + poison;
+        force[3 * (size_t)i + 2] = fz + poison;
         if (energy)
-            energy[i] = 0.5 * acc[0];
+            energy[i] = 0.5 * acc[0] + poison;
     }
     // block sums in a fixed order, then the last block adds the blocks' sums
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -157,25 +175,41 @@ __global__ void __launch_bounds__(kBlock) k_forces_allpairs(Pot pot, int n, doub
         double v = 0.0;
         for (unsigned int b = 0; b < gridDim.x; ++b)
             v += ((volatile double *)s->part)[(size_t)b * kPart + threadIdx.x];
+        // a species code out of range makes every total NaN
+        if (atomicOr(&s->bad, 0u) != 0u)
+            v = __longlong_as_double(0x7ff8000000000000ll);
         totals[threadIdx.x] = v;
     }
-    if (threadIdx.x == 0)
-        s->ticket = 0u;   // the next call starts from zero
 }
 
 std::mutex g_lock;
 Scratch *g_addr[kMaxDevices] = {};
 
-int fail(int code, const char *) { return code; }
+// Message of the calling thread's last failed call (a fixed buffer: nothing is
+// allocated to report a failure); md_last_error(NULL) returns it.
+thread_local char t_msg[256] = "";
+
+int fail(int code, const char *m)
+{
+    snprintf(t_msg, sizeof t_msg, "%s", m);
+    return code;
+}
 
 }  // namespace
+
+// The message of the calling thread's last md_forces_noalloc failure ("" if
+// its last call succeeded); md_api.cu returns it from md_last_error(NULL).
+const char *md_noalloc_message() { return t_msg; }
 
 extern "C" int md_forces_noalloc(const md_params *p, int64_t n, double box, const int32_t *species,
                                  const double *pos, double *force, double *energy, double *totals,
                                  void *cuda_stream)
 {
+    t_msg[0] = '\0';
     if (!p || !species || !pos || !force || !totals)
         return fail(MD_E_INVAL, "md_forces_noalloc: null argument");
+    if (!(p->precision >= MD_PREC_FP64 && p->precision <= MD_PREC_FP32))
+        return fail(MD_E_INVAL, "md_forces_noalloc: unknown precision mode");
     if (n < 2)
         return fail(MD_E_INVAL, "md_forces_noalloc: need at least 2 particles");
     if (n > MD_NOALLOC_MAX_N)
@@ -203,8 +237,8 @@ extern "C" int md_forces_noalloc(const md_params *p, int64_t n, double box, cons
             pot.shift[k] = p->shift ? 4.0 * eps * (sr6 * sr6 - sr6) : 0.0;
             rcmax = rc > rcmax ? rc : rcmax;
         }
-    if (!(box > 2.0 * rcmax))
-        return fail(MD_E_INVAL, "md_forces_noalloc: box must exceed twice the largest cutoff");
+    if (!(box > 2.0 * rcmax) || !(box < 1e300))
+        return fail(MD_E_INVAL, "md_forces_noalloc: box must be finite and exceed twice the largest cutoff");
 
     // once per device, with that device current: the scratch array's address
     int dev = 0;
@@ -222,13 +256,17 @@ extern "C" int md_forces_noalloc(const md_params *p, int64_t n, double box, cons
         s = g_addr[dev];
     }
     cudaStream_t st = (cudaStream_t)cuda_stream;
-    if (cudaMemsetAsync(&s->ticket, 0, sizeof(unsigned int), st) != cudaSuccess)
+    static_assert(offsetof(Scratch, bad) == offsetof(Scratch, ticket) + sizeof(unsigned int), "adjacent words");
+    if (cudaMemsetAsync(&s->ticket, 0, 2 * sizeof(unsigned int), st) != cudaSuccess)
         return fail(MD_E_CUDA, "md_forces_noalloc: clearing the scratch ticket failed");
     const int grid = (int)((n + kBlock - 1) / kBlock);
+    const int nsp = p->n_species;
     if (p->precision == MD_PREC_FP64)
-        k_forces_allpairs<true><<<grid, kBlock, 0, st>>>(pot, (int)n, box, species, pos, force, energy, totals, s);
+        k_forces_allpairs<true><<<grid, kBlock, 0, st>>>(pot, (int)n, nsp, box, species, pos, force, energy, totals,
+                                                          s);
     else
-        k_forces_allpairs<false><<<grid, kBlock, 0, st>>>(pot, (int)n, box, species, pos, force, energy, totals, s);
+        k_forces_allpairs<false><<<grid, kBlock, 0, st>>>(pot, (int)n, nsp, box, species, pos, force, energy, totals,
+                                                           s);
     if (cudaGetLastError() != cudaSuccess)
         return fail(MD_E_CUDA, "md_forces_noalloc: kernel launch failed");
     return MD_OK;

@@ -36,7 +36,8 @@ class md_params(C.Structure):
                 ("sample_interval", C.c_int32), ("obs_capacity", C.c_int32),
                 ("threads_per_particle", C.c_int32), ("use_graph", C.c_int32),
                 ("reorder", C.c_int32), ("reserved0", C.c_int32), ("smooth_h", C.c_double),
-                ("check_interval", C.c_int32), ("reserved", C.c_int32 * 3)]
+                ("check_interval", C.c_int32), ("neigh_capacity_max", C.c_int32),
+                ("step_budget", C.c_int32), ("reserved", C.c_int32 * 1)]
 
 
 class md_obs(C.Structure):
@@ -53,7 +54,8 @@ class md_info_t(C.Structure):
                 ("status", C.c_int32), ("step_ms", C.c_double), ("step_launches", C.c_int64),
                 ("rebuild_ms", C.c_double), ("rebuild_checks", C.c_int64),
                 ("step_device_ms", C.c_double), ("step_device_launches", C.c_int64),
-                ("check_interval", C.c_int32), ("reserved", C.c_int32)]
+                ("check_interval", C.c_int32), ("neigh_capacity_max", C.c_int32),
+                ("regrows", C.c_int64)]
 
 
 OBS_DTYPE = np.dtype([("step", np.int64), ("e_pot", np.float64), ("e_kin", np.float64),
@@ -94,6 +96,7 @@ def _load() -> C.CDLL:
         "md_corr_destroy": ([C.c_void_p], C.c_int),
         "md_compute_forces": ([H, d, d, C.POINTER(md_obs)], C.c_int),
         "md_observables": ([H, C.POINTER(md_obs), C.c_int32, i32], C.c_int),
+        "md_epot_series": ([H, i64, d, C.c_int32, i32], C.c_int),
         "md_get_state": ([H, d, d, i32], C.c_int),
         "md_set_state": ([H, d, d, i32], C.c_int),
         "md_get_neighbours": ([H, i32, i32, C.c_int32], C.c_int),
@@ -118,7 +121,7 @@ EXPORTED = ("md_params_default", "md_workspace_size", "md_create", "md_step",
             "md_set_state", "md_get_neighbours", "md_info", "md_sync", "md_destroy",
             "md_last_error", "md_status_string", "md_forces_noalloc", "md_andersen",
             "md_corr_workspace_size", "md_corr_create", "md_corr_sample", "md_corr_result",
-            "md_corr_destroy", "md_cell_order")
+            "md_corr_destroy", "md_cell_order", "md_epot_series")
 MD_NOALLOC_MAX_N = 1048576
 
 
@@ -227,6 +230,16 @@ def md_observables(h, n_replicas: int, max_samples: int = 1 << 16):
     return arr.reshape(n.value, n_replicas)
 
 
+def md_epot_series(h, n_replicas: int, max_steps: int = 1 << 16):
+    """(steps [n], e_pot [n, n_replicas]): the per-step potential energies
+    recorded since the previous call, oldest first."""
+    steps = np.empty(max_steps, dtype=np.int64)
+    e = np.empty((max_steps, n_replicas))
+    n = C.c_int32()
+    _check(_lib.md_epot_series(h, steps.ctypes.data_as(C.POINTER(C.c_int64)), _dptr(e), max_steps, C.byref(n)), h)
+    return steps[: n.value].copy(), e[: n.value].copy()
+
+
 def md_get_state(h, n_total: int):
     pos = np.empty((n_total, 3))
     vel = np.empty((n_total, 3))
@@ -273,10 +286,12 @@ def md_forces_noalloc(p: md_params, n: int, box: float, species_ptr: int, pos_pt
                       energy_ptr: int, totals_ptr: int, stream_ptr: int):
     """Direct-sum forces without any device allocation; every pointer is a
     caller-owned device address (see md.h for the layouts)."""
-    _check(_lib.md_forces_noalloc(C.byref(p), int(n), float(box), C.c_void_p(species_ptr),
-                                  C.c_void_p(pos_ptr), C.c_void_p(force_ptr),
-                                  C.c_void_p(energy_ptr) if energy_ptr else None,
-                                  C.c_void_p(totals_ptr), C.c_void_p(stream_ptr)))
+    rc = _lib.md_forces_noalloc(C.byref(p), int(n), float(box), C.c_void_p(species_ptr),
+                                C.c_void_p(pos_ptr), C.c_void_p(force_ptr),
+                                C.c_void_p(energy_ptr) if energy_ptr else None,
+                                C.c_void_p(totals_ptr), C.c_void_p(stream_ptr))
+    if rc != MD_OK:          # the handle-free call keeps its message per thread
+        raise MDError(rc, _lib.md_last_error(None).decode())
 
 
 # ---------------------------------------------------------------------------
@@ -286,7 +301,7 @@ def md_forces_noalloc(p: md_params, n: int, box: float, species_ptr: int, pos_pt
 def make_params(pot: dict, dt: float, skin: float = 0.3, precision: int = MD_PREC_MIXED,
                 sample_interval: int = 100, neigh_capacity: int = 0, threads_per_particle: int = 0,
                 use_graph: bool = True, reorder: int = 1, obs_capacity: int = 0,
-                check_interval: int = 0) -> md_params:
+                check_interval: int = 0, neigh_capacity_max: int = 0, step_budget: int = 0) -> md_params:
     p = md_params_default()
     p.n_species = int(pot["n_species"])
     p.shift = 1 if pot.get("shift", True) else 0
@@ -307,6 +322,8 @@ def make_params(pot: dict, dt: float, skin: float = 0.3, precision: int = MD_PRE
     p.reorder = int(reorder)          # 0 x-fastest, 1 Morton, 2 Hilbert (True / False: 1 / 0)
     p.obs_capacity = int(obs_capacity)
     p.check_interval = int(check_interval)   # 0 automatic, else 1, 2, 4, 8, 16
+    p.neigh_capacity_max = int(neigh_capacity_max)   # 0: twice the starting capacity
+    p.step_budget = int(step_budget)         # 0: automatic bound of md_step's device loop
     return p
 
 
@@ -356,6 +373,9 @@ class System:
 
     def observables(self, max_samples: int = 1 << 16):
         return md_observables(self.h, self.nrep, max_samples)
+
+    def epot_series(self, max_steps: int = 1 << 16):
+        return md_epot_series(self.h, self.nrep, max_steps)
 
     def get_state(self):
         return md_get_state(self.h, self.n)

@@ -70,8 +70,20 @@ def test_workspace_size_grows_with_n_and_precision(md):
     assert b > 65536 * 128 * 4
 
 
+def test_workspace_holds_the_capacity_cap(md):
+    """The list area is sized for the cap neigh_capacity_max, so the capacity
+    can grow in place; 0 means twice the starting capacity."""
+    from paper_0912_3824_gb300 import synth
+    n, box = 65536, (65536 / 1.2) ** (1 / 3)
+    sz = lambda **kw: md.md_workspace_size(md.make_params(synth.ka_params(), 0.001, **kw), [n], [box])
+    fixed = sz(neigh_capacity=128, neigh_capacity_max=128)
+    assert sz(neigh_capacity=128, neigh_capacity_max=200) - fixed == pytest.approx(4 * n * (200 - 128), abs=512)
+    assert sz(neigh_capacity=128) - fixed == pytest.approx(4 * n * 128, abs=512)
+    assert sz(neigh_capacity=128, neigh_capacity_max=129) - fixed == pytest.approx(4 * n * 8, abs=512)
+
+
 @pytest.mark.parametrize("bad", ["box", "dt", "species", "tpp", "sample", "asym", "smooth", "smooth_tpp",
-                                 "check3", "check32"])
+                                 "check3", "check32", "capmax", "capneg", "budget", "reserved"])
 def test_argument_checks(md, bad):
     from paper_0912_3824_gb300 import synth
     pot = synth.ka_params()
@@ -97,6 +109,14 @@ def test_argument_checks(md, bad):
         p.threads_per_particle = 16
     if bad in ("check3", "check32"):     # the check interval divides the 16 steps of a graph loop
         p.check_interval = 3 if bad == "check3" else 32
+    if bad == "capmax":                  # the cap may not be below the starting capacity
+        p.neigh_capacity, p.neigh_capacity_max = 128, 64
+    if bad == "capneg":
+        p.neigh_capacity = -8
+    if bad == "budget":
+        p.step_budget = -1
+    if bad == "reserved":
+        p.reserved[0] = 1
     with pytest.raises(md.MDError) as ei:
         md.md_workspace_size(p, [1000], [box])
     assert ei.value.code == md.MD_E_INVAL
@@ -119,6 +139,7 @@ def test_params_layout_and_smoothing_field(md):
     assert ctypes.sizeof(md.md_params) == 192
     assert md.md_params.smooth_h.offset == 168
     assert md.md_params.check_interval.offset == 176
+    assert md.md_params.neigh_capacity_max.offset == 180 and md.md_params.step_budget.offset == 184
     assert md.make_params(synth.lj_params(smooth=0.005), 0.001).smooth_h == 0.005
     assert md.make_params(synth.wca_params(), 0.001).rcut[0][0] == synth.WCA_RCUT
 
@@ -135,6 +156,36 @@ def test_noalloc_rejects_smoothing_before_touching_the_device(md):
     rc = md._lib.md_forces_noalloc(ctypes.byref(p), 8, ctypes.c_double(20.0), ctypes.addressof(sp), addr, addr,
                                    addr, addr, None)
     assert rc == md.MD_E_INVAL
+    assert b"smoothed potential" in md._lib.md_last_error(None)
+
+
+@pytest.mark.parametrize("case", ["null", "small_n", "big_n", "box", "species", "precision"])
+def test_noalloc_argument_errors_carry_their_reason(md, case):
+    """Every argument the host can check is checked before any CUDA call, and
+    the reason is kept for md_last_error(NULL) (a fixed per-thread buffer)."""
+    import ctypes
+    from paper_0912_3824_gb300 import synth
+    p = md.make_params(synth.ka_params(), 0.001)
+    buf = (ctypes.c_double * 64)()
+    addr = ctypes.addressof(buf)
+    n, box, sp = 8, 20.0, addr
+    want = {"null": b"null argument", "small_n": b"at least 2", "big_n": b"MD_NOALLOC_MAX_N",
+            "box": b"box must", "species": b"n_species", "precision": b"precision"}[case]
+    if case == "null":
+        sp = None
+    if case == "small_n":
+        n = 1
+    if case == "big_n":
+        n = md.MD_NOALLOC_MAX_N + 1
+    if case == "box":
+        box = 4.0
+    if case == "species":
+        p.n_species = 3
+    if case == "precision":
+        p.precision = 7
+    rc = md._lib.md_forces_noalloc(ctypes.byref(p), n, ctypes.c_double(box), sp, addr, addr, addr, addr, None)
+    assert rc == md.MD_E_INVAL
+    assert want in md._lib.md_last_error(None)
 
 
 def _cells_in_order(md, reorder, box):

@@ -71,6 +71,9 @@ def test_forces_energy_virial_match_oracle(md, prec, kind, n):
     assert np.allclose(tot["w"][0], w7[1:], rtol=0, atol=10 * TOL_E[prec] * abs(w7[0]) + 1e-9)
     ek, mom = oracle.kinetic(s.params, s.species, s.vel)
     assert tot["e_kin"][0] == pytest.approx(ek, rel=1e-6 if prec == "fp32" else 1e-13)
+    # total momentum (velocities held as double-single in MIXED: exact to ~2^-48)
+    assert np.abs(tot["p"][0] - mom).max() <= {"fp64": 1e-12, "mixed": 1e-10, "fp32": 1e-4}[prec]
+    assert tot["max_disp"][0] == 0.0                  # lists just rebuilt
     sim.close()
 
 
@@ -200,6 +203,68 @@ def test_mixed_trajectory_close_to_oracle(md):
     e_ref = rec["e_pot"] + rec["e_kin"]
     assert np.allclose(e_gpu, e_ref, rtol=1e-6)
     assert np.abs(obs["p"]).max() < 1e-6 * s.n
+
+
+@pytest.mark.parametrize("prec,steps,tol", [("fp64", 100, 1e-11), ("mixed", 50, 1e-6)])
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_epot_every_step_matches_oracle(md, prec, steps, tol, use_graph):
+    """The potential energy at every MD step (a per-step reduction of Sec. 2.2),
+    against the oracle's trajectory sampled at every step; at the sample steps
+    it equals the e_pot of the observables record bit for bit; a second call
+    returns only the steps recorded since the first."""
+    s = _system("lj", 864, amp=0.02)
+    sim = _sim(md, s, prec, dt=0.005, sample_interval=10, use_graph=use_graph)
+    sim.step(steps)
+    assert sim.sync() == md.MD_OK
+    st, e = sim.epot_series()
+    obs = sim.observables()[:, 0]
+    _, _, _, _, rec = oracle.vv_run(s.params, s.box, s.species, s.pos, s.vel, s.image, 0.005, steps, sample=1)
+    assert np.array_equal(st, np.arange(steps + 1))
+    assert np.abs(e[:, 0] - rec["e_pot"]).max() <= tol * np.abs(rec["e_pot"]).max()
+    assert np.array_equal(e[obs["step"], 0], obs["e_pot"])
+    sim.step(7)
+    st2, e2 = sim.epot_series()
+    assert np.array_equal(st2, np.arange(steps + 1, steps + 8))
+    assert sim.epot_series()[0].size == 0
+    sim.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "fp32"])
+def test_max_displacement_matches_host_displacement(md, prec):
+    """max_disp of a sample record is the largest displacement of that step's
+    positions from those of the last list build.  With a wide skin no rebuild
+    happens in 30 steps, so it is max_i |r_i(t) - r_i(0)|, computed here from
+    the oracle's trajectory (the device tests it in single precision against
+    positions rounded at the build: a few 1e-6 sigma)."""
+    s = _system("ka", 1000, amp=0.02)
+    sim = _sim(md, s, prec, dt=0.001, sample_interval=10, skin=0.6)
+    sim.step(30)
+    assert sim.sync() == md.MD_OK
+    assert sim.info()["rebuilds"] == 1              # the build of md_create only
+    obs = sim.observables()[:, 0]
+    sim.close()
+    r0 = s.pos + s.image * s.box
+    for t, got in zip(obs["step"], obs["max_disp"]):
+        rp, _, ri, _, _ = oracle.vv_run(s.params, s.box, s.species, s.pos, s.vel, s.image, 0.001, int(t))
+        want = np.sqrt((((rp + ri * s.box) - r0) ** 2).sum(axis=1)).max()
+        assert abs(got - want) <= 2e-5, (t, got, want)
+    assert obs["max_disp"][0] == 0.0 and obs["max_disp"][-1] > 1e-3
+
+
+def test_e1_sparse_corner_trajectory(md):
+    """The sparse corner of the performance measurement of Sec. 3: LJ at
+    density 0.2, T = 1.5, skin 0.5, dt = 0.001, N = 1372 (4 x 7^3).  FP64
+    follows the oracle trajectory; MIXED stays within the mixed tolerances."""
+    s = synth.perturb(synth.lj_fluid(1372, density=0.2, temperature=1.5, seed=4), 0.05, 41)
+    rp, rv, ri, _, rec = oracle.vv_run(s.params, s.box, s.species, s.pos, s.vel, s.image, 0.001, 300,
+                                       sample=50)
+    pos, vel, img, obs, info = _trajectory(md, s, "fp64", 0.001, 300, 50, skin=0.5)
+    assert np.abs((pos + img * s.box) - (rp + ri * s.box)).max() < 1e-9
+    assert np.allclose(obs["e_pot"], rec["e_pot"], rtol=1e-11)
+    assert np.allclose(obs["p"], rec["p"], rtol=0, atol=1e-11)
+    pos, vel, img, obs, info = _trajectory(md, s, "mixed", 0.001, 300, 50, skin=0.5)
+    assert np.abs((pos + img * s.box) - (rp + ri * s.box)).max() < 1e-5
+    assert np.allclose(obs["e_pot"] + obs["e_kin"], rec["e_pot"] + rec["e_kin"], rtol=1e-6)
 
 
 def test_graph_and_stream_launches_agree_bitwise(md):
@@ -375,35 +440,97 @@ def test_momentum_conserved_over_long_mixed_run(md):
     sim.close()
 
 
-def test_capacity_overflow_is_reported(md):
+def test_capacity_past_the_cap_is_reported(md):
+    """A list longer than the cap neigh_capacity_max is the one capacity
+    error (MD_E_CAPACITY), here at the first build of md_create."""
     s = _system("ka", 1000)
     with pytest.raises(md.MDError) as ei:
+        _sim(md, s, "mixed", neigh_capacity=16, neigh_capacity_max=16)
+    assert ei.value.code == md.MD_E_CAPACITY
+    with pytest.raises(md.MDError) as ei:       # default cap: twice the start, still too small
         _sim(md, s, "mixed", neigh_capacity=16)
     assert ei.value.code == md.MD_E_CAPACITY
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "fp32"])
+def test_capacity_grows_at_create_within_the_cap(md, prec):
+    """A starting capacity far below the lists (fixed-size list of Sec. 2.2):
+    the first build grows it on the device and is redone; the forces equal
+    those of a handle created with room to spare, bit for bit."""
+    s = _system("ka", 1000)
+    sim = _sim(md, s, prec, neigh_capacity=16, neigh_capacity_max=256)
+    info = sim.info()
+    mx = info["max_neighbours"]
+    assert info["regrows"] == 1
+    assert info["neigh_capacity"] == min(256, -(-(mx + (mx + 3) // 4) // 8) * 8)
+    assert info["neigh_capacity"] >= mx and info["neigh_capacity_max"] == 256
+    f, e, tot = sim.forces()
+    sim.close()
+    ref = _sim(md, s, prec, neigh_capacity=256)
+    fr, er, totr = ref.forces()
+    assert ref.info()["regrows"] == 0
+    ref.close()
+    assert np.array_equal(f, fr) and np.array_equal(e, er)
+    assert tot["e_pot"][0] == totr["e_pot"][0] and tot["virial"][0] == totr["virial"][0]
+
+
+def _heated_run(md, s, nsteps, use_graph, **kw):
+    sim = _sim(md, s, "mixed", dt=0.002, use_graph=use_graph, **kw)
+    sim.rescale(2.0)
+    sim.step(nsteps)
+    return sim
+
+
 @pytest.mark.parametrize("use_graph", [True, False])
-def test_overflow_during_run_keeps_the_last_consistent_state(md, use_graph):
-    """A list capacity that fits the start but not the heated liquid: the step
-    loop stops at the rebuild that overflows, MD_E_CAPACITY is reported, and the
-    buffers stay those of the last completed step (the build's last block does
-    not make the half-written permutation current), so the positions equal
-    those of an unconstrained run after the same number of steps."""
+def test_capacity_grows_during_a_run(md, use_graph):
+    """A capacity that fits the start but not the heated liquid, with a cap to
+    grow into: the run finishes with MD_OK, the capacity has grown in place
+    (a redone build inside the CUDA graph's rebuild branch, or in the stream
+    launches), and the trajectory equals that of a run with room to spare from
+    the start, bit for bit (the list contents and their order do not depend on
+    the capacity)."""
     s = _melted(synth.ka_params(), 2000, 1.2, 1.0)     # longest list 112 at the start, on a
     probe = _sim(md, s, "mixed")                        # multiple of 8: no slack in the capacity
     cap = (probe.info()["max_neighbours"] + 7) // 8 * 8
     probe.close()
-    sim = _sim(md, s, "mixed", dt=0.002, neigh_capacity=cap, use_graph=use_graph)
-    sim.rescale(2.0)
-    sim.step(3000)
+    sim = _heated_run(md, s, 3000, use_graph, neigh_capacity=cap, neigh_capacity_max=2 * cap)
+    assert sim.sync() == md.MD_OK
+    info = sim.info()
+    assert info["step"] == 3000
+    assert info["regrows"] >= 1 and info["neigh_capacity"] > cap
+    assert info["neigh_capacity"] >= info["max_neighbours"]
+    pos, vel, img = sim.get_state()
+    obs = sim.observables()
+    sim.close()
+    ref = _heated_run(md, s, 3000, use_graph, neigh_capacity=2 * cap)
+    assert ref.sync() == md.MD_OK
+    assert ref.info()["regrows"] == 0
+    rp, rv, ri = ref.get_state()
+    robs = ref.observables()
+    ref.close()
+    assert np.array_equal(pos, rp) and np.array_equal(img, ri) and np.array_equal(vel, rv)
+    assert np.array_equal(obs["e_pot"], robs["e_pot"])
+
+
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_overflow_past_the_cap_keeps_the_last_consistent_state(md, use_graph):
+    """The same heated run with the capacity fixed (cap = start): the step loop
+    stops at the rebuild whose list exceeds the cap, MD_E_CAPACITY is reported,
+    and the buffers stay those of the last completed step (the build's last
+    block does not make the half-written permutation current), so the
+    positions equal those of an unconstrained run after the same number of
+    steps."""
+    s = _melted(synth.ka_params(), 2000, 1.2, 1.0)
+    probe = _sim(md, s, "mixed")
+    cap = (probe.info()["max_neighbours"] + 7) // 8 * 8
+    probe.close()
+    sim = _heated_run(md, s, 3000, use_graph, neigh_capacity=cap, neigh_capacity_max=cap)
     assert sim.sync() == md.MD_E_CAPACITY
     k = sim.info()["step"]
     assert 0 < k < 3000
     pos, _, img = sim.get_state()
     sim.close()
-    ref = _sim(md, s, "mixed", dt=0.002, use_graph=use_graph)
-    ref.rescale(2.0)
-    ref.step(k)
+    ref = _heated_run(md, s, k, use_graph)
     assert ref.sync() == md.MD_OK
     rp, _, ri = ref.get_state()
     ref.close()
@@ -420,6 +547,65 @@ def test_instability_is_reported_and_state_kept(md):
     info = sim.info()
     assert info["step"] <= 1
     sim.close()
+
+
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_exhausted_step_budget_is_reported_and_state_kept(md, use_graph):
+    """md_step's device loop is bounded.  With the bound lowered to 40 step-
+    kernel executions (step_budget), md_step(100) stops inside the loop with
+    MD_E_TIMEOUT, reported once, and the positions are those of an
+    unconstrained run of the same number of steps."""
+    s = _system("ka", 1000)
+    sim = _sim(md, s, "mixed", step_budget=40, use_graph=use_graph)
+    sim.step(100)
+    assert sim.sync() == md.MD_E_TIMEOUT
+    assert sim.sync() == md.MD_OK               # reported once
+    k = sim.info()["step"]
+    assert 30 <= k <= 42
+    pos, _, img = sim.get_state()
+    sim.close()
+    ref = _sim(md, s, "mixed", use_graph=use_graph)
+    ref.step(k)
+    assert ref.sync() == md.MD_OK
+    rp, _, ri = ref.get_state()
+    ref.close()
+    assert np.array_equal(pos + img * s.box, rp + ri * s.box)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "fp32"])
+def test_nonfinite_state_is_reported(md, prec):
+    """A NaN velocity planted on the host through md_set_state: the first drift
+    makes that position non-finite, md_step stops with MD_E_NONFINITE (reported
+    once), and the current positions stay those before the step."""
+    s = _system("ka", 1000)
+    sim = _sim(md, s, prec)
+    pos, vel, img = sim.get_state()
+    vel[17, 1] = np.nan
+    sim.set_state(pos, vel, img)
+    sim.step(50)
+    assert sim.sync() == md.MD_E_NONFINITE
+    assert sim.sync() == md.MD_OK
+    assert sim.info()["step"] == 0
+    p2, _, i2 = sim.get_state()
+    sim.close()
+    assert np.array_equal(p2 + i2 * s.box, pos + img * s.box)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "fp32"])
+def test_overlapping_particles_are_reported(md, prec):
+    """Two particles 1e-3 sigma apart (repulsion ~ 48 / r^13): the first step
+    either overflows single precision (MD_E_NONFINITE) or throws a particle
+    more than a quarter box (MD_E_UNSTABLE); the run stops at step 0 with
+    finite positions."""
+    s = _system("lj", 864)
+    s.pos[5] = s.pos[4] + np.array([1e-3, 0.0, 0.0])
+    sim = _sim(md, s, prec, dt=0.005)
+    sim.step(10)
+    assert sim.sync() in (md.MD_E_NONFINITE, md.MD_E_UNSTABLE)
+    assert sim.info()["step"] == 0
+    pos, _, _ = sim.get_state()
+    sim.close()
+    assert np.isfinite(pos).all()
 
 
 def test_full_size_sampled_parity_ka65536(md):

@@ -25,7 +25,8 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmdgb300.so")
 OUT_DIR_CHECKED = os.path.join(HERE, "_build_checked")
 LIB_CHECKED = os.path.join(HERE, "libmdgb300_checked.so")
-SOURCES = ["md_api.cu", "md_kernels_mixed.cu", "md_kernels_fp64.cu", "md_kernels_fp32.cu", "md_noalloc.cu"]
+SOURCES = ["md_api.cu", "md_kernels_mixed.cu", "md_kernels_fp64.cu", "md_kernels_fp32.cu", "md_noalloc.cu",
+           "md_peak.cu"]
 HEADERS = ["md_common.cuh", "md_kernels.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -51,7 +52,8 @@ def _stale(lib: str) -> bool:
     if not os.path.exists(lib):
         return True
     t = os.path.getmtime(lib)
-    deps = [os.path.join(CSRC, s) for s in SOURCES + HEADERS] + [os.path.join(INCLUDE, "md.h"), __file__]
+    deps = [os.path.join(CSRC, s) for s in SOURCES + HEADERS] + \
+        [os.path.join(INCLUDE, h) for h in ("md.h", "md_bench.h")] + [__file__]
     return any(os.path.getmtime(d) > t for d in deps)
 
 

@@ -82,7 +82,7 @@ struct Layout {
     size_t off_ctl, off_rep, off_blk_i, off_blk_f, off_crank, off_cxyz;
     size_t off_pa, off_pb, off_va, off_vb, off_pa2, off_pb2, off_va2, off_vb2, off_qa, off_qb, off_force;
     size_t off_rref, off_image, off_image2, off_key, off_tmpidx;
-    size_t off_ccount, off_ccursor, off_cstart, off_nbr, off_nnbr, off_part_f, off_part_i;
+    size_t off_ccount, off_ccursor, off_cstart, off_nbr, off_nnbr, off_part_f, off_part_i, off_part_e;
     size_t off_ring, off_totals, off_scale, off_st_pos, off_st_vel, off_st_img, off_st_code;
     size_t off_epot, off_epot_step;
     size_t off_st_f, off_st_e, total;
@@ -376,6 +376,7 @@ Layout make_layout(const md_params *p, const Geometry &g)
     L.off_nnbr = take(4 * n);
     L.off_part_f = take(8 * 12 * (size_t)g.nblk_f);
     L.off_part_i = take(8 * 4 * (size_t)g.nblk_i);
+    L.off_part_e = take(8 * 2 * (size_t)(kForceBlock / 32) * (size_t)g.nblk_f);   // per warp, 2 parities
     L.off_ring = take(sizeof(mdk::Obs) * (size_t)cap * g.R);
     L.off_epot = take(sizeof(double) * (size_t)cap * g.R);
     L.off_epot_step = take(sizeof(long long) * (size_t)cap);
@@ -528,10 +529,17 @@ KArgs first_args(const md_handle *h)
     return a;
 }
 
+// Energies of a step still awaiting their sum go into the per-step series
+// first: the force kernel reuses the partials' storage.
+int flush_epot(md_handle *h) { return launch(h, h->ks->epot_flush, 1, kForceBlock, h->a); }
+
 int launch_force(md_handle *h, int fsample)
 {
     KArgs a = h->a;
     a.fsample = fsample;
+    int rc = flush_epot(h);
+    if (rc)
+        return rc;
     return launch(h, h->ks->force[h->p.smooth_h > 0.0][force_index(h->g.tpp)], h->g.nblk_f, kForceBlock, a);
 }
 
@@ -890,6 +898,7 @@ static int create_impl(md_handle *h, const md_params *p, const int32_t *species,
     a.n = (int)g.n;
     a.nrep = g.R;
     a.ncell = g.ncell;
+    a.Kstride = g.Kmax;
     a.tpp = g.tpp;
     a.si = p->sample_interval;
     a.obs_cap = h->cap;
@@ -916,6 +925,7 @@ static int create_impl(md_handle *h, const md_params *p, const int32_t *species,
     a.blk_f = (const int4 *)(w + L.off_blk_f);
     a.part_f = (double *)(w + L.off_part_f);
     a.part_i = (double *)(w + L.off_part_i);
+    a.part_e = w + L.off_part_e;
     a.ring = (mdk::Obs *)(w + L.off_ring);
     a.epot = (double *)(w + L.off_epot);
     a.epot_step = (long long *)(w + L.off_epot_step);
@@ -956,6 +966,8 @@ static int create_impl(md_handle *h, const md_params *p, const int32_t *species,
             a.tab.ihsd[k] = ihs;
             a.tab.rc[k] = (float)rc;
             a.tab.ihs[k] = (float)ihs;
+            a.tab.vcd[k] = eps != 0.0 ? shift / (4.0 * eps) : 0.0;
+            a.tab.vc[k] = (float)a.tab.vcd[k];
         }
     for (int s = 0; s < 2; ++s) {
         const int ss = std::min(s, p->n_species - 1);
@@ -1013,6 +1025,7 @@ static int create_impl(md_handle *h, const md_params *p, const int32_t *species,
         memset(&c0, 0, sizeof c0);
         c0.K = g.K;
         c0.Kmax = g.Kmax;
+        c0.epot_pending = -1;
         if ((rc = put(L.off_ctl, &c0, sizeof c0)))
             return rc;
         cudaError_t e = cudaMemsetAsync(a.ccount, 0, 4 * (size_t)g.ncell, h->s);
@@ -1442,9 +1455,11 @@ int md_epot_series(md_handle *h, int64_t *steps, double *e_pot, int32_t max_step
     if (!h || !n_steps || (max_steps > 0 && (!steps || !e_pot)))
         return MD_E_INVAL;
     *n_steps = 0;
-    mdk::Ctl c;
-    int rc = read_ctl(h, &c);
+    int rc = flush_epot(h);
     if (rc)
+        return rc;
+    mdk::Ctl c;
+    if ((rc = read_ctl(h, &c)))
         return rc;
     const size_t cap = (size_t)h->cap, R = (size_t)h->g.R;
     const size_t sb = align_up(sizeof(long long) * cap);
@@ -1536,7 +1551,7 @@ int md_get_neighbours(md_handle *h, int32_t *counts, int32_t *lists, int32_t kma
     mdk::Ctl c;
     if ((rc = read_ctl(h, &c)))
         return rc;
-    const size_t K = (size_t)c.K;                        // row stride of the lists in use
+    const size_t K = (size_t)h->g.Kmax;                  // row stride of the lists (the cap)
     if ((rc = ensure_pinned(h, 4 * n * K + 4 * n + 16 * n + 256)) || (rc = stage_wait(h)))
         return rc;
     char *q = h->pin;

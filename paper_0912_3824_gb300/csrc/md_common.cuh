@@ -38,9 +38,9 @@ struct Ctl {
     int pos_par;              // which of the two position buffers is current
     int state_par;            // which of the two velocity / image buffers is current
     int max_nbr;              // largest list length seen at the last build
-    int K;                    // list entries per particle in use (the row stride of nbr); grows
-                              // on the device when a build finds a longer list, up to Kmax
-    int Kmax;                 // capacity cap: nbr holds Kmax entries per particle
+    int K;                    // list entries per particle in use; grows on the device when a
+                              // build finds a longer list, up to Kmax
+    int Kmax;                 // capacity cap: the row stride of nbr (KArgs::Kstride)
     unsigned int regrow;      // 1: the last build overflowed K; K was raised and the build
                               // must be redone before the lists are used
     long long step;           // time index of the current positions
@@ -56,6 +56,7 @@ struct Ctl {
     float last_maxdisp2;
     float pad1;
     long long regrows;        // builds redone with a larger K since md_create
+    long long epot_pending;   // a step whose warp energy partials still await their sum (-1: none)
 };
 
 struct Rep {                  // one independent system
@@ -74,8 +75,9 @@ struct Rep {                  // one independent system
 struct PairTab {              // [a*2+b]
     float rc2[4], rl2[4], sig2[4], eps4[4], eps48[4], shift[4];
     float rc[4], ihs[4];      // r_c and 1 / (h sigma) of the smoothing (Sec. 4)
+    float vc[4];              // S_ab / (4 eps_ab) (0 where eps_ab = 0): V = 4 eps_ab (s6^2 - s6 - vc)
     double rc2d[4], rl2d[4], sig2d[4], eps4d[4], eps48d[4], shiftd[4];
-    double rcd[4], ihsd[4];
+    double rcd[4], ihsd[4], vcd[4];
 };
 
 struct Obs {                  // identical layout to md_obs
@@ -89,6 +91,8 @@ struct __align__(32) d4 { double x, y, z, w; };
 // Every kernel takes this one struct by value.
 struct KArgs {
     int n, nrep, ncell, tpp, si, obs_cap, epot_cap, imode, use_cond, fsample;
+    int Kstride;                      // list row stride: the capacity cap (Ctl::Kmax); the rows hold
+                                      // at most Ctl::K entries, so K can grow without a new layout
     int nblk_i, nblk_f;
     int lookahead;                    // MD steps until the next rebuild check (after this node)
     int set_rebuild, set_loop;        // this graph node sets the rebuild / loop condition
@@ -109,6 +113,8 @@ struct KArgs {
     const int4 *blk_i, *blk_f;        // per block: first particle, end, replica (blk_f: + its
                                       // chunk index, the slot of its partial sums)
     double *part_f, *part_i;          // per-block partial sums [nblk_f][12], [nblk_i][4]
+    void *part_e;                     // per-block potential energy [nblk_f]: double (FP64 mode) or
+                                      // float2 double-single (MIXED, FP32)
     Obs *ring, *totals;
     double *epot;                     // per-step potential energy [epot_cap][nrep], slot = step % cap
     long long *epot_step;             // [epot_cap]: the step held by each slot (-1 = none)
@@ -190,7 +196,7 @@ struct KernelSet {
     const void *integrate, *force[2][6], *step[2][6];   // [smoothed][log2 lanes per particle]
     const void *bin, *scan, *scatter, *permute, *nbuild;
     const void *load, *getstate, *expforce, *scale, *set_steps, *reset, *mark_rebuild;
-    const void *andersen, *andersen_fix, *snapshot;
+    const void *andersen, *andersen_fix, *snapshot, *epot_flush;
 };
 
 const KernelSet &kernels_fp64();

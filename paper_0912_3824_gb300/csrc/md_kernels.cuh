@@ -162,6 +162,38 @@ __device__ __forceinline__ void block_max3_sum1(float &a, float &b, float &c, do
     __syncthreads();
 }
 
+// The same with the energy sum in double-single (FP32 arithmetic): warps add
+// by shuffles in a fixed butterfly order, then warp 0 adds the warps' sums.
+// shf: 3 * 32 + 2 * 32 floats.
+__device__ __forceinline__ void block_max3_sum1(float &a, float &b, float &c, ds &e, float *shf, double *)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    a = warp_max(a);
+    b = warp_max(b);
+    c = warp_max(c);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        e = ds_add(e, ds_from(__shfl_xor_sync(0xffffffffu, e.hi, o), __shfl_xor_sync(0xffffffffu, e.lo, o)));
+    if (lane == 0) {
+        shf[3 * w] = a;
+        shf[3 * w + 1] = b;
+        shf[3 * w + 2] = c;
+        shf[96 + 2 * w] = e.hi;
+        shf[97 + 2 * w] = e.lo;
+    }
+    __syncthreads();
+    if (w == 0) {
+        a = warp_max(lane < nw ? shf[3 * lane] : 0.f);
+        b = warp_max(lane < nw ? shf[3 * lane + 1] : 0.f);
+        c = warp_max(lane < nw ? shf[3 * lane + 2] : 0.f);
+        e = lane < nw ? ds_from(shf[96 + 2 * lane], shf[97 + 2 * lane]) : ds_from(0.f, 0.f);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+            e = ds_add(e, ds_from(__shfl_xor_sync(0xffffffffu, e.hi, o), __shfl_xor_sync(0xffffffffu, e.lo, o)));
+    }
+    __syncthreads();
+}
+
 __device__ __forceinline__ int species_of(float w) { return __float_as_int(w) & 15; }
 __device__ __forceinline__ int species_of(double w) { return (int)(__double_as_longlong(w) & 15); }
 
@@ -267,6 +299,22 @@ __device__ __forceinline__ void smooth_pair(double r2, double rc, double ihs, do
 }
 
 template <int P> using FT = typename std::conditional<P == FP64, double, float>::type;
+
+// Per-particle potential energy and its block sums: double in FP64 mode,
+// double-single (FP32 arithmetic) otherwise, so that the every-step energy
+// reduction adds no FP64 instruction to the single-precision modes.
+template <int P> using ET = typename std::conditional<P == FP64, double, ds>::type;
+__device__ __forceinline__ double e_value(double e) { return e; }
+__device__ __forceinline__ double e_value(ds e) { return ds_to_double(e); }
+__device__ __forceinline__ float e_float(double e) { return (float)e; }
+__device__ __forceinline__ float e_float(ds e) { return __fadd_rn(e.hi, e.lo); }
+template <int P> __device__ __forceinline__ ET<P> e_zero()
+{
+    if constexpr (P == FP64)
+        return 0.0;
+    else
+        return ds_from(0.f, 0.f);
+}
 
 // ---------------------------------------------------------------------------
 // Per-particle velocity-Verlet pieces (Sec. 2.2), in the precision's state
@@ -491,11 +539,107 @@ __device__ __forceinline__ void write_record(const KArgs &a, int mode, int r, co
         a.ring[slot * a.nrep + r] = o;
 }
 
+// Potential-energy partial sums, one per warp of the force / step kernels
+// (part_e): double in FP64 mode, double-single elsewhere, so that the every-
+// step energy reduction costs no FP64 arithmetic in the single-precision
+// modes.  Two sets, by the parity of the step the energies belong to, so that
+// a step's partials survive the next step until they are added up.
+constexpr int kWarpsF = kForceBlock / 32;
+
+template <int P>
+__device__ __forceinline__ size_t epart_index(const KArgs &a, long long step, int chunk, int warp)
+{
+    return (size_t)(step & 1) * (size_t)a.nblk_f * kWarpsF + (size_t)chunk * kWarpsF + warp;
+}
+
+template <int P>
+__device__ __forceinline__ void put_epart(const KArgs &a, size_t k, ET<P> e)
+{
+    if constexpr (P == FP64)
+        ((double *)a.part_e)[k] = e;
+    else
+        ((float2 *)a.part_e)[k] = make_float2(e.hi, e.lo);
+}
+
+template <int P>
+__device__ __forceinline__ ET<P> get_epart(const KArgs &a, size_t k)
+{
+    if constexpr (P == FP64) {
+        return ((const double *)a.part_e)[k];
+    } else {
+        const float2 x = ((const float2 *)a.part_e)[k];
+        return ds_from(x.x, x.y);
+    }
+}
+
+__device__ __forceinline__ double e_add(double x, double y) { return x + y; }
+__device__ __forceinline__ ds e_add(ds x, ds y) { return ds_add(x, y); }
+
+__device__ __forceinline__ double e_warp_sum(double e) { return warp_sum(e); }
+__device__ __forceinline__ ds e_warp_sum(ds e)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        e = ds_add(e, ds_from(__shfl_xor_sync(0xffffffffu, e.hi, o), __shfl_xor_sync(0xffffffffu, e.lo, o)));
+    return e;
+}
+
+// The warp's energy sum into its partial of step `step`.  Every lane of the
+// warp calls it (the sum is a full-warp shuffle); lane 0 writes if `write`.
+template <int P>
+__device__ __forceinline__ void store_warp_energy(const KArgs &a, long long step, int chunk, ET<P> e, bool write)
+{
+    e = e_warp_sum(e);
+    if ((threadIdx.x & 31) == 0 && write)
+        put_epart<P>(a, epart_index<P>(a, step, chunk, threadIdx.x >> 5), e);
+}
+
+// Potential energy of one replica at `step` from its warps' partials, by the
+// whole block: thread t adds partials p0 + t, p0 + t + blockDim, ... in that
+// order (eight loads in flight), then the threads' sums are added in a fixed
+// tree.  Valid in thread 0.  Every thread of the block must call it.
+template <int P>
+__device__ double epot_sum_block(const KArgs &a, const Rep &rp, long long step, float *shf, double *sh)
+{
+    ET<P> v = e_zero<P>();
+    const int stride = blockDim.x;
+    const size_t base = epart_index<P>(a, step, 0, 0);
+    int b = rp.bf0 * kWarpsF + threadIdx.x;
+    const int end = rp.bf1 * kWarpsF;
+    for (; b + 7 * stride < end; b += 8 * stride) {
+        ET<P> x[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            x[u] = get_epart<P>(a, base + b + u * stride);
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            v = e_add(v, x[u]);
+    }
+    for (; b < end; b += stride)
+        v = e_add(v, get_epart<P>(a, base + b));
+    float d0 = 0.f, d1 = 0.f, d2 = 0.f;
+    block_max3_sum1(d0, d1, d2, v, shf, sh);
+    return e_value(v);
+}
+
+// The same by one thread, for handles with many replicas (one thread each).
+template <int P>
+__device__ double epot_sum_seq(const KArgs &a, const Rep &rp, long long step)
+{
+    ET<P> v = e_zero<P>();
+    const size_t base = epart_index<P>(a, step, 0, 0);
+    for (int b = rp.bf0 * kWarpsF; b < rp.bf1 * kWarpsF; ++b)
+        v = e_add(v, get_epart<P>(a, base + b));
+    return e_value(v);
+}
+
 // Per-replica sums of the block partials, in a fixed order (deterministic).
-// Potential-side values come from part_f[.][0..7]; kinetic values from
-// part_f[.][8..11] (step kernel, from_f = true) or part_i[.][0..3].
-static __device__ void finish_reductions(const KArgs &a, int mode, bool from_f, long long step, float md2,
-                                         double *sh)
+// Potential-side values come from part_f[.][1..7] and the energy sums
+// part_e; kinetic values from part_f[.][8..11] (step kernel, from_f = true)
+// or part_i[.][0..3].
+template <int P>
+__device__ void finish_reductions(const KArgs &a, int mode, bool from_f, long long step, float md2, double *sh,
+                                  float *shf)
 {
     const Ctl *ctl = a.ctl;
     const long long slot = ctl->obs_count % (long long)a.obs_cap;
@@ -511,7 +655,7 @@ static __device__ void finish_reductions(const KArgs &a, int mode, bool from_f, 
             if (want_f || from_f)
                 for (int b = rp.bf0 + threadIdx.x; b < rp.bf1; b += blockDim.x)
 #pragma unroll
-                    for (int k = 0; k < kPartF; ++k)
+                    for (int k = 1; k < kPartF; ++k)
                         v[k] += a.part_f[(size_t)b * kPartF + k];
             if (!from_f) {
 #pragma unroll
@@ -523,8 +667,11 @@ static __device__ void finish_reductions(const KArgs &a, int mode, bool from_f, 
                         v[8 + k] += a.part_i[(size_t)b * 4 + k];
             }
             block_sum<12>(v, sh);
-            if (threadIdx.x == 0)
+            const double e = want_f ? epot_sum_block<P>(a, rp, step, shf, sh) : 0.0;
+            if (threadIdx.x == 0) {
+                v[0] = e;
                 write_record(a, mode, r, v, step, md2, rebuilds, slot);
+            }
         }
     } else {
         for (int r = threadIdx.x; r < a.nrep; r += blockDim.x) {
@@ -534,7 +681,7 @@ static __device__ void finish_reductions(const KArgs &a, int mode, bool from_f, 
                 v[k] = 0.0;
             if (want_f || from_f)
                 for (int b = rp.bf0; b < rp.bf1; ++b)
-                    for (int k = 0; k < kPartF; ++k)
+                    for (int k = 1; k < kPartF; ++k)
                         v[k] += a.part_f[(size_t)b * kPartF + k];
             if (!from_f) {
                 for (int k = 8; k < 12; ++k)
@@ -543,38 +690,34 @@ static __device__ void finish_reductions(const KArgs &a, int mode, bool from_f, 
                     for (int k = 0; k < 4; ++k)
                         v[8 + k] += a.part_i[(size_t)b * 4 + k];
             }
+            if (want_f)
+                v[0] = epot_sum_seq<P>(a, rp, step);
             write_record(a, mode, r, v, step, md2, rebuilds, slot);
         }
         __syncthreads();
     }
 }
 
-// The potential energy of every replica at a step that records no sample: the
-// per-block sums part_f[.][0] added exactly as finish_reductions adds them
-// (same threads, same order), into the per-step series.
-static __device__ void finish_epot(const KArgs &a, long long step, double *sh)
+// The potential energy of every replica at `step` (a step that recorded no
+// sample) into the per-step series: the same sums as finish_reductions takes.
+// Run by one whole block.
+template <int P>
+__device__ void finish_epot(const KArgs &a, long long step, double *sh, float *shf)
 {
     const long long slot = step % a.epot_cap;
     if (a.nrep <= 8) {
         for (int r = 0; r < a.nrep; ++r) {
-            const Rep rp = a.rep[r];
-            double v[1] = {0.0};
-            for (int b = rp.bf0 + threadIdx.x; b < rp.bf1; b += blockDim.x)
-                v[0] += a.part_f[(size_t)b * kPartF];
-            block_sum<1>(v, sh);
+            const double e = epot_sum_block<P>(a, a.rep[r], step, shf, sh);
             if (threadIdx.x == 0)
-                a.epot[slot * a.nrep + r] = v[0];
+                a.epot[slot * a.nrep + r] = e;
         }
     } else {
-        for (int r = threadIdx.x; r < a.nrep; r += blockDim.x) {
-            const Rep rp = a.rep[r];
-            double v = 0.0;
-            for (int b = rp.bf0; b < rp.bf1; ++b)
-                v += a.part_f[(size_t)b * kPartF];
-            a.epot[slot * a.nrep + r] = v;
-        }
+        for (int r = threadIdx.x; r < a.nrep; r += blockDim.x)
+            a.epot[slot * a.nrep + r] = epot_sum_seq<P>(a, a.rep[r], step);
         __syncthreads();
     }
+    if (threadIdx.x == 0)
+        a.epot_step[slot] = step;
 }
 
 // Rebuild decision: the list built at the last rebuild holds every pair
@@ -604,20 +747,21 @@ __device__ __forceinline__ unsigned int need_rebuild(const KArgs &a, float md2, 
 // of the particle holds the total force and ep, half the sum of its pair
 // energies; the virial comes from pair_energy on sample steps.
 // ---------------------------------------------------------------------------
-// Entries per particle of the list rows in use (the capacity K, which the
-// neighbour build may raise on the device): read where a row starts.
-__device__ __forceinline__ int list_stride(const KArgs &a) { return a.ctl->K; }
+// 1/24 as a double-single pair (the accumulated energies are 12 V; a particle
+// takes half of each pair)
+constexpr float kE24hi = (float)(1.0 / 24.0);
+constexpr float kE24lo = (float)(1.0 / 24.0 - (double)(float)(1.0 / 24.0));
 
 template <typename T> struct PairRow {   // parameters of (species i, species j = 0 / 1)
-    T rc2[2], sig2[2], eps4[2], eps48[2], shift[2], rc[2], ihs[2];
+    T rc2[2], sig2[2], eps4[2], eps48[2], shift[2], rc[2], ihs[2], c[2];
 };
 
 template <int P, int TPP, bool SM>
 __device__ __forceinline__ void pair_forces(const KArgs &a, const Rep &rp, int pp, int ii, int nn,
-                                            FT<P> &fx, FT<P> &fy, FT<P> &fz, double &ep)
+                                            FT<P> &fx, FT<P> &fy, FT<P> &fz, ET<P> &ep)
 {
     const int lane = threadIdx.x & (TPP - 1);
-    const int *lst = a.nbr + (size_t)ii * (size_t)list_stride(a);
+    const int *lst = a.nbr + (size_t)ii * (size_t)a.Kstride;
     if constexpr (P == FP64) {
         const d4 *pos = (const d4 *)pos_a(a, pp);
         const d4 xi = pos[ii];
@@ -632,8 +776,9 @@ __device__ __forceinline__ void pair_forces(const KArgs &a, const Rep &rp, int p
             pr.shift[tj] = a.tab.shiftd[ti * 2 + tj];
             pr.rc[tj] = a.tab.rcd[ti * 2 + tj];
             pr.ihs[tj] = a.tab.ihsd[ti * 2 + tj];
+            pr.c[tj] = a.tab.vcd[ti * 2 + tj];
         }
-        double sx = 0, sy = 0, sz = 0, se = 0;
+        double sx = 0, sy = 0, sz = 0, se = 0;          // se: sum of 12 V
         for (int k0 = 4 * lane; k0 < nn; k0 += 4 * TPP) {
             const int4 q = __ldg((const int4 *)(lst + k0));
             const int jj[4] = {q.x, q.y, q.z, q.w};
@@ -654,13 +799,16 @@ __device__ __forceinline__ void pair_forces(const KArgs &a, const Rep &rp, int p
                     const double s2 = pr.sig2[tj] * ir2;
                     const double s6 = s2 * s2 * s2;
                     double fr = pr.eps48[tj] * ir2 * s6 * (s6 - 0.5);
-                    double v = pr.eps4[tj] * s6 * (s6 - 1.0) - pr.shift[tj];
-                    if (SM)
+                    if (SM) {
+                        double v = pr.eps4[tj] * s6 * (s6 - 1.0) - pr.shift[tj];
                         smooth_pair(r2, pr.rc[tj], pr.ihs[tj], fr, v);
+                        se = fma(12.0, v, se);
+                    } else {
+                        se = fma(pr.eps48[tj], fma(s6, s6, -(s6 + pr.c[tj])), se);
+                    }
                     sx += fr * dx;
                     sy += fr * dy;
                     sz += fr * dz;
-                    se += v;
                 }
             }
         }
@@ -672,7 +820,7 @@ __device__ __forceinline__ void pair_forces(const KArgs &a, const Rep &rp, int p
             se += __shfl_xor_sync(0xffffffffu, se, o);
         }
         fx = sx; fy = sy; fz = sz;
-        ep = 0.5 * se;
+        ep = se * (1.0 / 24.0);
     } else {
         // MIXED reads the fixed-point copy (16 B per neighbour), FP32 the positions
         const float4 *pos = (const float4 *)pos_a(a, pp);
@@ -697,7 +845,10 @@ __device__ __forceinline__ void pair_forces(const KArgs &a, const Rep &rp, int p
             pr.shift[tj] = a.tab.shift[ti * 2 + tj];
             pr.rc[tj] = a.tab.rc[ti * 2 + tj];
             pr.ihs[tj] = a.tab.ihs[ti * 2 + tj];
+            pr.c[tj] = a.tab.vc[ti * 2 + tj];
         }
+        // the energy is accumulated as 12 V = eps48_ab (s6^2 - s6 - c_ab), c_ab = S_ab / (4 eps_ab):
+        // eps48, masked by the cutoff test, serves the force and the energy alike
         float sx = 0.f, sy = 0.f, sz = 0.f, cx = 0.f, cy = 0.f, cz = 0.f, se = 0.f, ce = 0.f;
         // list indices are loaded kPfDepth iterations ahead, so that only the
         // position gathers remain on each iteration's critical path
@@ -763,20 +914,24 @@ __device__ __forceinline__ void pair_forces(const KArgs &a, const Rep &rp, int p
                 // (the particle itself, r2 = 0 exactly, is never inside)
                 const bool in = r2 > 0.0f && r2 < (tj ? pr.rc2[1] : pr.rc2[0]);
                 const float sig2 = tj ? pr.sig2[1] : pr.sig2[0];
-                const float eps48 = tj ? pr.eps48[1] : pr.eps48[0];
+                const float e48 = in ? (tj ? pr.eps48[1] : pr.eps48[0]) : 0.0f;
                 const float ir2 = __fdividef(1.0f, in ? r2 : 1.0f);
                 const float s2 = sig2 * ir2;
                 const float s6 = s2 * s2 * s2;
-                float fr = in ? eps48 * ir2 * s6 * (s6 - 0.5f) : 0.0f;
-                const float eps4 = tj ? pr.eps4[1] : pr.eps4[0];
-                const float shift = tj ? pr.shift[1] : pr.shift[0];
-                float v = in ? fmaf(eps4, s6 * s6 - s6, -shift) : 0.0f;
-                if (SM)
+                float fr = e48 * ir2 * s6 * (s6 - 0.5f);
+                if (SM) {
+                    const float eps4 = tj ? pr.eps4[1] : pr.eps4[0];
+                    const float shift = tj ? pr.shift[1] : pr.shift[0];
+                    float v = in ? fmaf(eps4, s6 * s6 - s6, -shift) : 0.0f;
                     smooth_pair(in ? r2 : 1.0f, tj ? pr.rc[1] : pr.rc[0], tj ? pr.ihs[1] : pr.ihs[0], fr, v);
+                    gv = fmaf(12.0f, v, gv);
+                } else {
+                    const float c = tj ? pr.c[1] : pr.c[0];
+                    gv = fmaf(e48, fmaf(s6, s6, -(s6 + c)), gv);
+                }
                 gx = fmaf(fr, dx, gx);
                 gy = fmaf(fr, dy, gy);
                 gz = fmaf(fr, dz, gz);
-                gv += v;
             }
             if constexpr (P == MIXED) {
                 kahan_add(sx, cx, gx);
@@ -806,7 +961,7 @@ __device__ __forceinline__ void pair_forces(const KArgs &a, const Rep &rp, int p
             fx = __fadd_rn(ax.hi, ax.lo);
             fy = __fadd_rn(ay.hi, ay.lo);
             fz = __fadd_rn(az.hi, az.lo);
-            ep = 0.5 * ds_to_double(ae);
+            ep = ds_mul(ae, ds_from(kE24hi, kE24lo));         // half of the sum of V = (12 V) / 24
         } else {
 #pragma unroll
             for (int o = TPP / 2; o > 0; o >>= 1) {
@@ -816,7 +971,7 @@ __device__ __forceinline__ void pair_forces(const KArgs &a, const Rep &rp, int p
                 se += __shfl_xor_sync(0xffffffffu, se, o);
             }
             fx = sx; fy = sy; fz = sz;
-            ep = 0.5 * (double)se;
+            ep = ds_from(se * (1.0f / 24.0f), 0.f);
         }
     }
 }
@@ -829,7 +984,7 @@ template <int P, int TPP, bool SM>
 __device__ __forceinline__ void pair_virial(const KArgs &a, const Rep &rp, int pp, int ii, int nn, double *acc)
 {
     const int lane = threadIdx.x & (TPP - 1);
-    const int *lst = a.nbr + (size_t)ii * (size_t)list_stride(a);
+    const int *lst = a.nbr + (size_t)ii * (size_t)a.Kstride;
     FT<P> d7[7] = {0, 0, 0, 0, 0, 0, 0};
     if constexpr (P == FP64) {
         const d4 *pos = (const d4 *)pos_a(a, pp);
@@ -912,15 +1067,15 @@ __device__ __forceinline__ void pair_virial(const KArgs &a, const Rep &rp, int p
     }
 }
 
-template <int P>
-__device__ __forceinline__ void store_force(const KArgs &a, int i, FT<P> fx, FT<P> fy, FT<P> fz, double e)
+template <int P, typename E>
+__device__ __forceinline__ void store_force(const KArgs &a, int i, FT<P> fx, FT<P> fy, FT<P> fz, E e)
 {
     if constexpr (P == FP64) {
         d4 f;
-        f.x = fx; f.y = fy; f.z = fz; f.w = e;
+        f.x = fx; f.y = fy; f.z = fz; f.w = e_value(e);
         ((d4 *)a.force)[i] = f;
     } else {
-        ((float4 *)a.force)[i] = make_float4(fx, fy, fz, (float)e);
+        ((float4 *)a.force)[i] = make_float4(fx, fy, fz, e_float(e));
     }
 }
 
@@ -943,13 +1098,13 @@ __device__ __forceinline__ void force_only(const KArgs &a)
     const int ii = valid ? i : b.x;
     const int nn = valid ? a.nnbr[ii] : 0;
     FT<P> fx, fy, fz;
-    double ep;
+    ET<P> ep;
     double acc[kPartF];
 #pragma unroll
     for (int k = 0; k < kPartF; ++k)
         acc[k] = 0.0;
     pair_forces<P, TPP, SM>(a, rp, pp, ii, nn, fx, fy, fz, ep);
-    acc[0] = ep;
+    acc[0] = e_value(ep);
     if (SAMPLE)
         pair_virial<P, TPP, SM>(a, rp, pp, ii, nn, acc);
     if (!(valid && lane == 0)) {
@@ -960,6 +1115,7 @@ __device__ __forceinline__ void force_only(const KArgs &a)
     if (valid && lane == 0)
         store_force<P>(a, i, fx, fy, fz, ep);
     if (SAMPLE) {
+        store_warp_energy<P>(a, ctl->step, b.w, (valid && lane == 0) ? ep : e_zero<P>(), true);
         block_sum<kPartF>(acc, sh);
         if (threadIdx.x == 0)
 #pragma unroll
@@ -1092,7 +1248,8 @@ __device__ __forceinline__ void component_update(const KArgs &a, const Rep &rp, 
 // neighbour loop so that their latency is hidden.
 template <int P, int TPP, bool SAMPLE, bool SM>
 __device__ __forceinline__ void step_body_split(const KArgs &a, bool active, bool last, int pp, int spar,
-                                                double *part, float &d2, float &v2, float &a2, unsigned int &bad)
+                                                double *part, ET<P> &eo, float &d2, float &v2, float &a2,
+                                                unsigned int &bad)
 {
     constexpr int NC = TPP >= 4 ? 1 : 4 / TPP;
     const int4 b = a.blk_f[blockIdx.x];
@@ -1121,12 +1278,12 @@ __device__ __forceinline__ void step_body_split(const KArgs &a, bool active, boo
         }
     }
     FT<P> fx = 0, fy = 0, fz = 0;
-    double ep = 0.0;
+    ET<P> ep = e_zero<P>();
 #pragma unroll
     for (int k = 0; k < kPartF; ++k)
         part[k] = 0.0;
+    eo = e_zero<P>();
     pair_forces<P, TPP, SM>(a, rp, pp, ii, nn, fx, fy, fz, ep);
-    part[0] = ep;
     if (SAMPLE)
         pair_virial<P, TPP, SM>(a, rp, pp, ii, nn, part);
     // Every lane of the warp must reach the shuffles below, including the
@@ -1196,6 +1353,7 @@ __device__ __forceinline__ void step_body_split(const KArgs &a, bool active, boo
             part[k] = 0.0;
         return;
     }
+    eo = ep;
     if (SAMPLE) {
         part[8] = ke;
         part[9] = p3[0];
@@ -1213,10 +1371,11 @@ __device__ __forceinline__ void step_body_split(const KArgs &a, bool active, boo
 
 template <int P, int TPP, bool SAMPLE, bool SM>
 __device__ __forceinline__ void step_body(const KArgs &a, bool active, bool last, int pp, int spar,
-                                          double *part, float &d2, float &v2, float &a2, unsigned int &bad)
+                                          double *part, ET<P> &eo, float &d2, float &v2, float &a2,
+                                          unsigned int &bad)
 {
     if constexpr (kSplitUpdate || TPP >= 4) {
-        step_body_split<P, TPP, SAMPLE, SM>(a, active, last, pp, spar, part, d2, v2, a2, bad);
+        step_body_split<P, TPP, SAMPLE, SM>(a, active, last, pp, spar, part, eo, d2, v2, a2, bad);
         return;
     }
     const int4 b = a.blk_f[blockIdx.x];
@@ -1227,12 +1386,12 @@ __device__ __forceinline__ void step_body(const KArgs &a, bool active, bool last
     const int ii = (i < b.y) ? i : b.x;
     const int nn = valid ? a.nnbr[ii] : 0;
     FT<P> fx = 0, fy = 0, fz = 0;
-    double ep = 0.0;
+    ET<P> ep = e_zero<P>();
 #pragma unroll
     for (int k = 0; k < kPartF; ++k)
         part[k] = 0.0;
+    eo = e_zero<P>();
     pair_forces<P, TPP, SM>(a, rp, pp, ii, nn, fx, fy, fz, ep);
-    part[0] = ep;
     if (SAMPLE)
         pair_virial<P, TPP, SM>(a, rp, pp, ii, nn, part);
     if (!(valid && lane == 0)) {
@@ -1241,6 +1400,7 @@ __device__ __forceinline__ void step_body(const KArgs &a, bool active, bool last
             part[k] = 0.0;
         return;
     }
+    eo = ep;
     store_force<P>(a, i, fx, fy, fz, ep);
     PState<P> s;
     load_pos<P>(a, pp, i, s);
@@ -1259,17 +1419,24 @@ __device__ __forceinline__ void step_body(const KArgs &a, bool active, bool last
     store_vel<P>(a, spar, i, s);
 }
 
+// Blocks per SM the unsmoothed single-precision step kernels are compiled for:
+// 7 x 128 threads at <= 72 registers, so that a 1024-block launch (KA N=65536
+// at 2 lanes per particle) is a single wave on 152 SMs.  FP64 and the smoothed
+// kernels keep the compiler's own register choice (they would spill).
+template <int P, bool SM> constexpr int step_min_blocks() { return (P != FP64 && !SM) ? 7 : 0; }
+
 template <int P, int TPP, bool SM>
-__global__ void __launch_bounds__(kForceBlock) k_step(KArgs a)
+__global__ void __launch_bounds__(kForceBlock, step_min_blocks<P, SM>()) k_step(KArgs a)
 {
     __shared__ double sh[32 * kPartF];
-    __shared__ float shf[96];
-    __shared__ int s_last;
+    __shared__ float shf[160];
+    __shared__ int s_last, s_first;
     __shared__ float s_m[4];
     Ctl *ctl = a.ctl;
     const unsigned int st0 = ctl->status;
     const long long step = ctl->step;
     const long long remaining = ctl->remaining;
+    const long long pend = ctl->epot_pending;   // an earlier step whose energies await their sum
     const int pp = ctl->pos_par, spar = ctl->state_par;
     // The status word can change while the launch runs (another block's atomicOr),
     // so threads of one block may read different values: it gates only per-particle
@@ -1282,29 +1449,31 @@ __global__ void __launch_bounds__(kForceBlock) k_step(KArgs a)
         atomicMax(&ctl->t_first_inv, ~global_ns());
 
     double part[kPartF];
+    ET<P> eo;
     float d2 = 0.f, v2 = 0.f, a2 = 0.f;
     unsigned int bad = 0u;
     if (sample)
-        step_body<P, TPP, true, SM>(a, active, last, pp, spar, part, d2, v2, a2, bad);
+        step_body<P, TPP, true, SM>(a, active, last, pp, spar, part, eo, d2, v2, a2, bad);
     else
-        step_body<P, TPP, false, SM>(a, active, last, pp, spar, part, d2, v2, a2, bad);
+        step_body<P, TPP, false, SM>(a, active, last, pp, spar, part, eo, d2, v2, a2, bad);
     if (bad)
         atomicOr(&ctl->status, bad);
 
-    if (sample) {
-        block_max3(d2, v2, a2, shf);
+    // This step's potential energy, every step: one partial per warp (written
+    // only by active launches, so that an idle one never overwrites partials
+    // that still await their sum; the shuffles run in every lane regardless).
+    // Block sums of the maxima every step, of the other reductions on sample
+    // steps (their component 0 stays unused).
+    store_warp_energy<P>(a, step, a.blk_f[blockIdx.x].w, eo, active);
+    block_max3(d2, v2, a2, shf);
+    if (sample)
         block_sum<kPartF>(part, sh);
-    } else {
-        block_max3_sum1(d2, v2, a2, part[0], shf, sh);
-    }
     if (threadIdx.x == 0) {
         const size_t pb = (size_t)a.blk_f[blockIdx.x].w * kPartF;
         if (sample) {
 #pragma unroll
-            for (int k = 0; k < kPartF; ++k)
+            for (int k = 1; k < kPartF; ++k)
                 a.part_f[pb + k] = part[k];
-        } else {
-            a.part_f[pb] = part[0];
         }
         if (d2 > 0.f)
             atomicMax(&ctl->maxdisp2, __float_as_uint(d2));
@@ -1314,9 +1483,15 @@ __global__ void __launch_bounds__(kForceBlock) k_step(KArgs a)
             atomicMax(&ctl->maxa2, __float_as_uint(a2));
         __threadfence();
         const unsigned int t = atomicAdd(&ctl->ticket, 1u);
+        s_first = (t == 0);
         s_last = (t == gridDim.x - 1);
     }
     __syncthreads();
+    // The first block to finish adds up the energies of the earlier step that
+    // still awaits its sum (the previous step, written by the previous launch):
+    // the other blocks are still working, so this is off the critical path.
+    if (s_first && pend >= 0)
+        finish_epot<P>(a, pend, sh, shf);
     if (!s_last)
         return;
 
@@ -1331,12 +1506,13 @@ __global__ void __launch_bounds__(kForceBlock) k_step(KArgs a)
     __syncthreads();
     const unsigned int st = atomicOr(&ctl->status, 0u);
     if (sample && st == 0u)
-        finish_reductions(a, IM_LOOP, true, step, s_m[3], sh);   // (its E_pot enters the series)
-    else if (remaining > 0 && st == 0u)
-        finish_epot(a, step, sh);
+        finish_reductions<P>(a, IM_LOOP, true, step, s_m[3], sh, shf);   // (its E_pot enters the series)
     if (threadIdx.x == 0) {
-        if (remaining > 0 && st == 0u)
+        if (sample && st == 0u)
             a.epot_step[step % a.epot_cap] = step;
+        // this step's energies: summed into the series here (sample) or by the
+        // first block to finish the next launch (or by k_epot_flush)
+        ctl->epot_pending = (remaining > 0 && st == 0u && !sample) ? step : -1ll;
         const bool drifted = active && !last;
         unsigned int reb = 0u;
         if (drifted && st == 0u) {
@@ -1387,7 +1563,7 @@ template <int P>
 __global__ void __launch_bounds__(kIntBlock) k_integrate(KArgs a)
 {
     __shared__ double sh[32 * 12];
-    __shared__ float shf[96];
+    __shared__ float shf[160];
     __shared__ int s_last;
     __shared__ float s_m[3];
     Ctl *ctl = a.ctl;
@@ -1462,7 +1638,7 @@ __global__ void __launch_bounds__(kIntBlock) k_integrate(KArgs a)
     __syncthreads();
     const unsigned int st = atomicOr(&ctl->status, 0u);
     if (rec && st == 0u)
-        finish_reductions(a, mode, false, step, s_m[0], sh);
+        finish_reductions<P>(a, mode, false, step, s_m[0], sh, shf);
     if (threadIdx.x == 0) {
         unsigned int reb = 0u;
         if (first && !halted && st == 0u) {
@@ -1770,9 +1946,10 @@ __device__ __forceinline__ float box_gap(float x, float c, float h, float L, flo
 }
 
 // Lists of the particles of cell c, from the positions in buffer pn (the
-// permuted copy being built), with rows of K entries.  Every particle's full
-// count is recorded in max_nbr; entries beyond K are dropped (the build's last
-// block then grows K and the build is redone).
+// permuted copy being built): row i starts at nbr[i * Kstride] (the cap) and
+// holds at most K entries (the capacity in use).  Every particle's full count
+// is recorded in max_nbr; entries beyond K are dropped (the build's last block
+// then grows K and the build is redone).
 template <int P>
 __device__ __forceinline__ void nbuild_cell(const KArgs &a, int pn, int c, int K)
 {
@@ -1900,7 +2077,7 @@ __device__ __forceinline__ void nbuild_cell(const KArgs &a, int pn, int c, int K
                         const unsigned mm = __ballot_sync(0xffffffffu, in);
                         const int at = cnt[p] + __popc(mm & lt_mask);
                         if (in && at < K)
-                            a.nbr[(size_t)i * (size_t)K + at] = jj;
+                            a.nbr[(size_t)i * (size_t)a.Kstride + at] = jj;
                         cnt[p] += __popc(mm);
                     }
                 }
@@ -1919,7 +2096,7 @@ __device__ __forceinline__ void nbuild_cell(const KArgs &a, int pn, int c, int K
             // pad the row with the particle itself to a multiple of kUnr entries, so the
             // pair loop reads whole groups without masking (K is a multiple of 8)
             for (int k = cnt; k < (cnt + kUnr - 1) / kUnr * kUnr && k < K; ++k)
-                a.nbr[(size_t)(ob + o) * (size_t)K + k] = ob + o;
+                a.nbr[(size_t)(ob + o) * (size_t)a.Kstride + k] = ob + o;
             atomicMax(&ctl->max_nbr, cnt);
         }
         __syncthreads();
@@ -2325,6 +2502,24 @@ __global__ void __launch_bounds__(kIntBlock) k_snapshot(KArgs a)
     a.snap_species[t] = sp;
 }
 
+// Sum the energies of a step that still awaits it into the per-step series
+// (before the host reads the series, and before a force evaluation outside
+// the step loop reuses the partials).  One block.
+template <int P>
+__global__ void __launch_bounds__(kForceBlock) k_epot_flush(KArgs a)
+{
+    __shared__ double sh[32 * kPartF];
+    __shared__ float shf[160];
+    const long long pend = a.ctl->epot_pending;
+    if (pend >= 0)
+        finish_epot<P>(a, pend, sh, shf);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        a.ctl->epot_pending = -1;
+        a.ctl->n_other += 1;
+    }
+}
+
 // request a list rebuild before the next force evaluation
 template <int P>
 __global__ void k_mark_rebuild(KArgs a)
@@ -2375,6 +2570,7 @@ KernelSet make_kernel_set()
     k.set_steps = (const void *)k_set_steps<P>;
     k.reset = (const void *)k_reset<P>;
     k.mark_rebuild = (const void *)k_mark_rebuild<P>;
+    k.epot_flush = (const void *)k_epot_flush<P>;
     k.andersen = (const void *)k_andersen<P>;
     k.andersen_fix = (const void *)k_andersen_fix<P>;
     k.snapshot = (const void *)k_snapshot<P>;

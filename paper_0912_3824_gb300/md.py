@@ -107,6 +107,8 @@ def _load() -> C.CDLL:
         "md_status_string": ([C.c_int], C.c_char_p),
         "md_forces_noalloc": ([P, C.c_int64, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                C.c_void_p, C.c_void_p], C.c_int),
+        # measurement helper (include/md_bench.h)
+        "md_fma_peak": ([C.c_int32, C.c_int64, d, d], C.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -123,6 +125,7 @@ EXPORTED = ("md_params_default", "md_workspace_size", "md_create", "md_step",
             "md_corr_workspace_size", "md_corr_create", "md_corr_sample", "md_corr_result",
             "md_corr_destroy", "md_cell_order", "md_epot_series")
 MD_NOALLOC_MAX_N = 1048576
+EXPORTED_BENCH = ("md_fma_peak",)
 
 
 def _status_name(code: int) -> str:
@@ -280,6 +283,17 @@ def md_destroy(h):
 
 def md_last_error(h) -> str:
     return _lib.md_last_error(h).decode()
+
+
+def md_fma_peak(precision: int, iters: int = 2000) -> tuple[float, float]:
+    """Measured CUDA-core FMA peak of the current GPU (md_bench.h): (TFLOP/s,
+    ms of the fastest timed launch) for precision MD_PREC_FP64 or MD_PREC_FP32."""
+    t = C.c_double()
+    ms = C.c_double()
+    rc = _lib.md_fma_peak(int(precision), int(iters), C.byref(t), C.byref(ms))
+    if rc != 0:
+        raise MDError(rc, "md_fma_peak failed")
+    return t.value, ms.value
 
 
 def md_forces_noalloc(p: md_params, n: int, box: float, species_ptr: int, pos_ptr: int, force_ptr: int,

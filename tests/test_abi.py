@@ -38,6 +38,18 @@ def test_library_exports_every_declared_symbol(md):
     assert set(_declared()) == set(md.EXPORTED)
 
 
+def test_library_exports_the_measurement_helpers(md):
+    """include/md_bench.h (the FMA-peak microbenchmark the roofline divides by)."""
+    import ctypes
+    src = open(os.path.join(ROOT, "include", "md_bench.h")).read()
+    names = sorted(set(re.findall(r"^\s*int\s*(md_\w+)\s*\(", src, re.M)))
+    assert names == sorted(md.EXPORTED_BENCH)
+    lib = ctypes.CDLL(md.LIB_PATH)
+    for name in names:
+        assert hasattr(lib, name), name
+    assert md._lib.md_fma_peak(1, 10, None, None) == 1          # argument checks come first
+
+
 def test_bounds_checked_library_builds_and_exports_the_same_symbols(md):
     """The bounds-checked variant used by tests/test_bounds_checked.py compiles
     (nvcc cross-compiles without a GPU) and exports the same entry points."""

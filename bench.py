@@ -35,6 +35,12 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "particle-steps/s at KA N=65536 (mixed vs FP64 on GB300) at stated energy drift/step"
+
+# Workload constants of the paper's protocols
+KA_DT = 0.001                                     # Kob-Andersen time step (Sec. 5)
+E1 = {"temperature": 1.5, "dt": 0.001, "skin": 0.5}   # performance measurements (Sec. 3)
+STABILITY = {"n": 10000, "density": 0.75, "temperature": 1.12, "dts": (0.001, 0.003),
+             "smooth": (0.0, 0.005)}              # stability protocol (Sec. 4)
 UNIT = "particle-steps/s"
 
 
@@ -554,7 +560,7 @@ def run_e1(args, local):
     dt = 0.001, skin 0.5, N = 1372 ... 864000 (4 n^3) and densities 0.2 ... 1.2."""
     cases = [(n, rho) for rho in (args.densities or [0.2, 0.4, 0.8, 1.2])
              for n in (args.sizes or [1372, 10976, 87808, 864000])]
-    return lj_cases(args, local, cases, "e1", temperature=1.5, dt=0.001, skin=0.5)
+    return lj_cases(args, local, cases, "e1", **E1)
 
 
 def lj_cases(args, local, cases, workload, temperature, dt, skin):
@@ -563,7 +569,8 @@ def lj_cases(args, local, cases, workload, temperature, dt, skin):
     for n, rho in cases:
         s = synth.lj_fluid(n=n, density=rho, temperature=temperature, seed=3)
         sim = md.System.from_synth(s, dt=dt, skin=skin, precision=md.PRECISIONS[args.precision],
-                                   sample_interval=100, device=device, threads_per_particle=args.tpp)
+                                   sample_interval=100, device=device, threads_per_particle=args.tpp,
+                                   use_graph=not args.no_graph)
         equilibrate(sim, max(1.5, temperature), temperature, melt_blocks=5, final_blocks=5)
         trials = None
         if not args.no_tune:
@@ -571,7 +578,7 @@ def lj_cases(args, local, cases, workload, temperature, dt, skin):
             from paper_0912_3824_gb300 import tune
             pos0, vel0, img0 = sim.get_state()
             base = md.make_params(s.params, dt, skin=skin, precision=md.PRECISIONS[args.precision],
-                                  sample_interval=100, threads_per_particle=args.tpp)
+                                  sample_interval=100, threads_per_particle=args.tpp, use_graph=not args.no_graph)
             base, trials = tune.autotune(base, [s.n], [s.box], s.species, pos0, vel0, img0, device=device,
                                          skins=(skin,))
             sim.close()
@@ -582,10 +589,14 @@ def lj_cases(args, local, cases, workload, temperature, dt, skin):
         info0 = sim.info()
         clocks = ClockSampler(local)
         clocks.start()
+        torch.cuda.profiler.start()          # (ncu --profile-from-start off sees the timed region)
         ms = time_chunks(torch, sim, args.inner, args.steps, flush, stream)
+        torch.cuda.profiler.stop()
         clk = clocks.stop()
         status = sim.sync()
         info1 = sim.info()
+        n_dev = info1["step_device_launches"] - info0["step_device_launches"]
+        k_ms = (info1["step_device_ms"] - info0["step_device_ms"]) / max(1, n_dev)
         n_list, n_cut = list_statistics(sim, s.params)
         t_step = ms * 1e-3 / (args.inner * args.steps)
         flops = (FLOP_PER_ENTRY_METHOD * n_list + FLOP_PER_PAIR_METHOD * n_cut) * n
@@ -599,7 +610,11 @@ def lj_cases(args, local, cases, workload, temperature, dt, skin):
                 "mean_list": float(n_list), "mean_in_cutoff": float(n_cut),
                 "neigh_capacity": info1["neigh_capacity"], "threads_per_particle": info1["threads_per_particle"],
                 "alu_tflops_whole_step": flops / t_step / 1e12,
-                "hbm_algorithmic_gbs_whole_step": hbm / t_step / 1e9, "clocks": clk,
+                "hbm_algorithmic_gbs_whole_step": hbm / t_step / 1e9,
+                "step_kernel_us": k_ms * 1e3,
+                "step_kernel_alu_tflops": flops / (k_ms * 1e-3) / 1e12 if k_ms > 0 else None,
+                "step_kernel_list_gbs": n * (4 * n_list + 52) / (k_ms * 1e-3) / 1e9 if k_ms > 0 else None,
+                "clocks": clk,
                 "autotune": [{k: (round(v, 5) if isinstance(v, float) else v) for k, v in t.items()}
                              for t in trials] if trials else None}
         if n <= 32768 and not args.no_extras:
@@ -740,7 +755,7 @@ def run_stats(args, local):
     from paper_0912_3824_gb300 import synth
     seeds = args.seeds or [5, 6, 7, 8]
     precs = tuple(args.precisions or ("fp32", "mixed", "fp64"))
-    cases = [(f"ka65536-s{sd}", lambda sd=sd: synth.ka_mixture(65536, temperature=2.0, seed=sd), 0.001,
+    cases = [(f"ka65536-s{sd}", lambda sd=sd: synth.ka_mixture(65536, temperature=2.0, seed=sd), KA_DT,
               (2.0, 0.5), args.md_steps) for sd in seeds]
     lags = sorted({int(round(10 ** (k / 2))) for k in range(2, 13)})     # 10, 32, 100, ... 10^6
     emit = lambda ln: print(json.dumps(ln), flush=True)
@@ -777,14 +792,16 @@ def run_stability(args, local):
     each in FP32, mixed and FP64 from the same equilibrated state."""
     from paper_0912_3824_gb300 import synth
     cases = []
+    st = STABILITY
     for pot in ("wca", "lj"):
-        for h in (0.0, 0.005):
-            for dt in (0.001, 0.003):
+        for h in st["smooth"]:
+            for dt in st["dts"]:
                 mk = synth.wca_params if pot == "wca" else synth.lj_params
                 params = mk(smooth=h)
                 cases.append((f"{pot}-h{h}-dt{dt}",
-                               lambda params=params: synth.make_system(10000, 0.75, 1.12, 12, params),
-                               dt, (1.12, 1.12), args.md_steps))
+                               lambda params=params: synth.make_system(st["n"], st["density"], st["temperature"],
+                                                                       12, params),
+                               dt, (st["temperature"], st["temperature"]), args.md_steps))
     return nve_cases(args, local, cases, "stability")
 
 

@@ -54,7 +54,8 @@ struct ApiRange {
 namespace {
 
 constexpr size_t kAlign = 256;
-constexpr int kIntBlock = 256, kForceBlock = 128, kNbBlock = 256, kScanBlock = 1024;
+constexpr int kIntBlock = 256, kForceBlock = 128, kScanBlock = 1024;
+constexpr int kNbCells = 4, kNbBlock = 32 * kNbCells;   // neighbour build: one warp per cell
 constexpr double kCellMargin = 1e-3;   // cell edge exceeds the largest list radius by this
 constexpr int kUnroll = 16;            // step kernels per loop iteration of the graph
 constexpr int kCheck = 4;              // automatic check interval below kCheckLargeN particles
@@ -81,7 +82,7 @@ struct Geometry {
 struct Layout {
     size_t off_ctl, off_rep, off_blk_i, off_blk_f, off_crank, off_cxyz;
     size_t off_pa, off_pb, off_va, off_vb, off_pa2, off_pb2, off_va2, off_vb2, off_qa, off_qb, off_force;
-    size_t off_rref, off_image, off_image2, off_key, off_tmpidx;
+    size_t off_rref, off_image, off_image2, off_key, off_tmpidx, off_skey;
     size_t off_ccount, off_ccursor, off_cstart, off_nbr, off_nnbr, off_part_f, off_part_i, off_part_e;
     size_t off_ring, off_totals, off_scale, off_st_pos, off_st_vel, off_st_img, off_st_code;
     size_t off_epot, off_epot_step;
@@ -369,6 +370,7 @@ Layout make_layout(const md_params *p, const Geometry &g)
     L.off_image2 = take(16 * n);
     L.off_key = take(4 * n);
     L.off_tmpidx = take(4 * n);
+    L.off_skey = take(4 * n);
     L.off_ccount = take(4 * (size_t)g.ncell);
     L.off_ccursor = take(4 * (size_t)g.ncell);
     L.off_cstart = take(4 * ((size_t)g.ncell + 1));
@@ -473,6 +475,9 @@ int grid_n(int64_t n, int per) { return (int)((n + per - 1) / per); }
 // The rebuild chain: kernel, grid, block.
 struct ChainStep { const void *f; int grid, block; };
 
+// blocks of the neighbour build: kNbCells cells each
+int nb_grid(const md_handle *h) { return (h->g.ncell + kNbCells - 1) / kNbCells; }
+
 int rebuild_chain(const md_handle *h, ChainStep *seq)
 {
     const KernelSet &k = *h->ks;
@@ -481,7 +486,7 @@ int rebuild_chain(const md_handle *h, ChainStep *seq)
     seq[1] = {k.scan, 1, kScanBlock};
     seq[2] = {k.scatter, nb, kIntBlock};
     seq[3] = {k.permute, nb, kIntBlock};
-    seq[4] = {k.nbuild, h->g.ncell, kNbBlock};          // one block per cell; its last block makes
+    seq[4] = {k.nbuild, nb_grid(h), kNbBlock};          // one warp per cell; its last block makes
     return 5;                                            // the permuted buffers current or asks
 }                                                        // for a redo with a larger K
 
@@ -504,7 +509,7 @@ int launch_rebuild(md_handle *h)
         if (rc)
             return rc;
     }
-    return launch(h, h->ks->nbuild, h->g.ncell, kNbBlock, retry_args(h));
+    return launch(h, h->ks->nbuild, nb_grid(h), kNbBlock, retry_args(h));
 }
 
 // Arguments of the step kernel at position `slot` of the unrolled loop.
@@ -600,7 +605,7 @@ int add_rebuild_chain(md_handle *h, cudaGraph_t g)
     if (rc)
         return rc;
     cudaGraphNode_t n_retry;
-    return add_kernel(h, body, &n_retry, nullptr, 0, h->ks->nbuild, h->g.ncell, kNbBlock, retry_args(h));
+    return add_kernel(h, body, &n_retry, nullptr, 0, h->ks->nbuild, nb_grid(h), kNbBlock, retry_args(h));
 }
 
 int add_conditional(md_handle *h, cudaGraph_t g, cudaGraphNode_t *node, cudaGraphNode_t dep,
@@ -914,6 +919,7 @@ static int create_impl(md_handle *h, const md_params *p, const int32_t *species,
     a.image2 = (int4 *)(w + L.off_image2);
     a.key = (int *)(w + L.off_key);
     a.tmpidx = (int *)(w + L.off_tmpidx);
+    a.skey = (int *)(w + L.off_skey);
     a.ccount = (int *)(w + L.off_ccount);
     a.ccursor = (int *)(w + L.off_ccursor);
     a.cstart = (int *)(w + L.off_cstart);

@@ -107,6 +107,7 @@ struct KArgs {
     float4 *rref;                     // positions at the last list build
     int4 *image, *image2;             // image counters (w = original index), by state_par
     int *key, *ccount, *cstart, *ccursor, *tmpidx;
+    int *skey;                        // sub-cell code of each particle (order inside its cell)
     const int *crank;                 // [global linear cell] -> global sorted cell id
     const int4 *cxyz;                 // [global sorted cell id] -> cx, cy, cz, replica
     int *nbr, *nnbr;

@@ -33,7 +33,8 @@ namespace mdk {
 
 constexpr int kIntBlock = 256;   // per-particle kernels: one thread per particle
 constexpr int kForceBlock = 128; // force / step kernels: tpp threads per particle
-constexpr int kNbBlock = 256;    // neighbour build: one block per cell
+constexpr int kNbCells = 4;      // neighbour build: cells per block, one warp each
+constexpr int kNbBlock = 32 * kNbCells;
 constexpr int kScanBlock = 1024;
 constexpr int kScanPer = 8;      // cell counts per thread and tile of the scan
 constexpr int kPartF = 12;       // doubles per block partial of the force / step kernels
@@ -1687,6 +1688,28 @@ __device__ __forceinline__ int cell_coord_f(float x, float cscale, int nc)
     return c < 0 ? 0 : (c >= nc ? nc - 1 : c);
 }
 
+// Position of a coordinate inside its cell on a 4-point grid (0..3); three of
+// them interleave into the particle's sub-cell code along a Morton curve, the
+// order of the particles inside a cell after each rebuild, so that the
+// particles a warp holds are close in space (their neighbours overlap).
+__device__ __forceinline__ unsigned int sub4(double x, double cscale, int c)
+{
+    const int s = (int)floor((x * cscale - (double)c) * 4.0);
+    return (unsigned int)(s < 0 ? 0 : (s > 3 ? 3 : s));
+}
+
+__device__ __forceinline__ unsigned int sub4f(float x, float cscale, int c)
+{
+    const int s = (int)floorf((x * cscale - (float)c) * 4.0f);
+    return (unsigned int)(s < 0 ? 0 : (s > 3 ? 3 : s));
+}
+
+__device__ __forceinline__ int morton6(unsigned int x, unsigned int y, unsigned int z)
+{
+    return (int)((x & 1u) | ((y & 1u) << 1) | ((z & 1u) << 2) | ((x & 2u) << 2) | ((y & 2u) << 3) |
+                 ((z & 2u) << 4));
+}
+
 template <int P>
 __global__ void __launch_bounds__(kIntBlock) k_bin(KArgs a)
 {
@@ -1703,20 +1726,23 @@ __global__ void __launch_bounds__(kIntBlock) k_bin(KArgs a)
         return;
     const Rep rp = a.rep[b.z];
     const int pp = ctl->pos_par;
-    int cx, cy, cz;
+    int cx, cy, cz, sub;
     if constexpr (P == FP64) {
         const d4 x = ((const d4 *)pos_a(a, pp))[i];
         cx = cell_coord(x.x, rp.cscale, rp.nc);
         cy = cell_coord(x.y, rp.cscale, rp.nc);
         cz = cell_coord(x.z, rp.cscale, rp.nc);
+        sub = morton6(sub4(x.x, rp.cscale, cx), sub4(x.y, rp.cscale, cy), sub4(x.z, rp.cscale, cz));
     } else {
         const float4 x = ((const float4 *)pos_a(a, pp))[i];
         cx = cell_coord_f(x.x, rp.cscalef, rp.nc);
         cy = cell_coord_f(x.y, rp.cscalef, rp.nc);
         cz = cell_coord_f(x.z, rp.cscalef, rp.nc);
+        sub = morton6(sub4f(x.x, rp.cscalef, cx), sub4f(x.y, rp.cscalef, cy), sub4f(x.z, rp.cscalef, cz));
     }
     const int key = checked(a, a.crank[rp.cell0 + (cz * rp.nc + cy) * rp.nc + cx], a.ncell, 0);
     a.key[i] = key;
+    a.skey[i] = sub;
     atomicAdd(&a.ccount[key], 1);
 }
 
@@ -1819,8 +1845,9 @@ __global__ void __launch_bounds__(kIntBlock) k_scatter(KArgs a)
 }
 
 // Final slot of each particle: its cell's start plus the number of particles
-// of the same cell with a smaller current index (stable, deterministic), then
-// gather of the whole state into the other buffers.
+// of the same cell that come before it in (sub-cell code, current index)
+// order (deterministic), then gather of the whole state into the other
+// buffers.
 template <int P>
 __global__ void __launch_bounds__(kIntBlock) k_permute(KArgs a)
 {
@@ -1836,9 +1863,13 @@ __global__ void __launch_bounds__(kIntBlock) k_permute(KArgs a)
     const int i = checked(a, a.tmpidx[s], a.n, 0);
     const int k = checked(a, a.key[i], a.ncell, 0);
     const int b0 = a.cstart[k], b1 = a.cstart[k + 1];
+    const int si = a.skey[i];
     int rank = 0;
-    for (int t = b0; t < b1; ++t)
-        rank += (a.tmpidx[t] < i) ? 1 : 0;
+    for (int t = b0; t < b1; ++t) {
+        const int j = checked(a, a.tmpidx[t], a.n, 0);
+        const int sj = a.skey[j];
+        rank += (sj < si || (sj == si && j < i)) ? 1 : 0;
+    }
     const int d = checked(a, b0 + rank, a.n, 0);
     if constexpr (P == FP64) {
         const d4 x = ((const d4 *)pos_a(a, pp))[i];
@@ -1860,25 +1891,33 @@ __global__ void __launch_bounds__(kIntBlock) k_permute(KArgs a)
 }
 
 // ---------------------------------------------------------------------------
-// Neighbour-list build (Sec. 2.2), one block per cell.  The block stages the
-// particles of the 27 surrounding cells (all cells of the replica when fewer
-// than three fit along its edge) in shared memory, in a fixed order (stencil
-// order, then slot order inside a cell), dropping those farther than the
-// largest list radius from the cell's own box.  Each warp then takes
-// kNbPass particles of the cell at a time and keeps the staged particles
-// closer than r_c,ab + skin (plus a rounding margin), 32 candidates per
-// ballot, writing each particle's row of the particle-major list
-// nbr[i*K + k] in that order.  Distances
-// are single precision: from the fixed-point copy in MIXED mode, from the
+// Neighbour-list build (Sec. 2.2), one warp per cell, one lane per particle
+// of the cell (batches of 32).  The warp stages the particles of the 27
+// surrounding cells (all cells of the replica when fewer than three fit along
+// its edge) in shared memory, in a fixed order (stencil order, then slot order
+// inside a cell), dropping those farther than the largest list radius from
+// the cell's own box; then every lane tests the staged candidates one after
+// the other (each read is a broadcast) against its own particle and appends
+// those closer than r_c,ab + skin (plus a rounding margin) to its row, in that
+// order: a small per-lane buffer in shared memory is written out to the
+// particle-major list nbr[i*Kstride + k] 16 entries at a time.  No block
+// barrier: the cells of a block never wait for one another.  Distances are
+// single precision: from the fixed-point copy in MIXED mode, from the
 // (rounded) positions otherwise; the list only has to contain every pair
-// within r_c + skin, and the margin covers the rounding.
-// Reads the permuted positions (other buffer).  More candidates than fit in
-// shared memory, or more particles in the cell than one batch holds, are
-// processed in rounds, so no cell size is too large.
+// within r_c + skin, and the margin covers the rounding.  Reads the permuted
+// positions (other buffer).  More candidates than fit in shared memory, or
+// more particles in the cell than 32, are processed in rounds, so no cell
+// size is too large.
 // ---------------------------------------------------------------------------
-constexpr int kNbCap = 1024;     // staged candidates per round
-constexpr int kNbOwn = 256;      // own-cell particles per batch
-constexpr int kNbPass = 2;       // own-cell particles tested per warp pass over the candidates
+constexpr int kNbStage = 256;    // staged candidates per round and warp
+constexpr int kNbBuf = 16;       // list entries a lane collects before writing them out
+
+struct NbWarp {
+    float4 pos[kNbStage];
+    int idx[kNbStage];
+    int buf[32][kNbBuf + 1];     // (+1: lanes in different banks)
+    int cell[27];
+};
 
 // Position word staged by the neighbour build: MIXED stages the fixed-point copy
 // (bits of X, Y, Z, species), whose wrapped differences give the exact minimum
@@ -1946,23 +1985,16 @@ __device__ __forceinline__ float box_gap(float x, float c, float h, float L, flo
 }
 
 // Lists of the particles of cell c, from the positions in buffer pn (the
-// permuted copy being built): row i starts at nbr[i * Kstride] (the cap) and
-// holds at most K entries (the capacity in use).  Every particle's full count
-// is recorded in max_nbr; entries beyond K are dropped (the build's last block
-// then grows K and the build is redone).
+// permuted copy being built), by one warp: row i starts at nbr[i * Kstride]
+// (the cap) and holds at most K entries (the capacity in use).  Every
+// particle's full count is recorded in max_nbr; entries beyond K are dropped
+// (the build's last block then grows K and the build is redone).
 template <int P>
-__device__ __forceinline__ void nbuild_cell(const KArgs &a, int pn, int c, int K)
+__device__ __forceinline__ void nbuild_cell(const KArgs &a, int pn, int c, int K, NbWarp &S)
 {
-    __shared__ float4 s_pos[kNbCap];
-    __shared__ int s_idx[kNbCap];
-    __shared__ int s_cnt[kNbOwn];
-    __shared__ int s_pref[28];
-    __shared__ int s_cell[27];
-    __shared__ int s_wsum[kNbBlock / 32];
-
+    constexpr unsigned FULL = 0xffffffffu;
     Ctl *ctl = a.ctl;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    constexpr int NW = kNbBlock / 32;
+    const int lane = threadIdx.x & 31;
     const int4 cc = a.cxyz[c];
     const Rep rp = a.rep[cc.w];
     const int nc = rp.nc;
@@ -1970,27 +2002,16 @@ __device__ __forceinline__ void nbuild_cell(const KArgs &a, int pn, int c, int K
     const int c0 = a.cstart[c], c1 = a.cstart[c + 1];
     if (c0 == c1)
         return;
-
-    if (tid < nst) {
+    if (lane < nst) {
         int x = cc.x, y = cc.y, z = cc.z;
         if (nst == 27) {
-            x = (x + tid % 3 - 1 + nc) % nc;
-            y = (y + (tid / 3) % 3 - 1 + nc) % nc;
-            z = (z + tid / 9 - 1 + nc) % nc;
+            x = (x + lane % 3 - 1 + nc) % nc;
+            y = (y + (lane / 3) % 3 - 1 + nc) % nc;
+            z = (z + lane / 9 - 1 + nc) % nc;
         }
-        s_cell[tid] = a.crank[rp.cell0 + (z * nc + y) * nc + x];
+        S.cell[lane] = a.crank[rp.cell0 + (z * nc + y) * nc + x];
     }
-    __syncthreads();
-    if (tid == 0) {
-        int s = 0;
-        for (int k = 0; k < nst; ++k) {
-            s_pref[k] = s;
-            s += a.cstart[s_cell[k] + 1] - a.cstart[s_cell[k]];
-        }
-        s_pref[nst] = s;
-    }
-    __syncthreads();
-    const int total = s_pref[nst];
+    __syncwarp();
 
     // own cell box (centre, half edge) for the candidate filter
     const float edge = rp.Lhi / (float)nc;
@@ -2001,105 +2022,91 @@ __device__ __forceinline__ void nbuild_cell(const KArgs &a, int pn, int c, int K
     const unsigned lt_mask = (1u << lane) - 1u;
     // nb_r2 of the fixed-point words is in units of qunit^2: the list radii follow
     const float r2unit = (P == MIXED && kNbFixed) ? 1.0f / (rp.qunit * rp.qunit) : 1.0f;
+    int *buf = S.buf[lane];
 
-    for (int ob = c0; ob < c1; ob += kNbOwn) {
-        const int nown = min(kNbOwn, c1 - ob);
-        for (int t = tid; t < nown; t += kNbBlock)
-            s_cnt[t] = 0;
+    for (int ob = c0; ob < c1; ob += 32) {
+        const int i = ob + lane;
+        const bool own = i < c1;
+        const float4 H = nb_word<P>(a, pn, own ? i : ob);
+        const int ti = nb_species<P>(H);
+        const float rl0 = own ? a.tab.rl2[ti * 2] * r2unit : -1.0f;      // -1: nothing passes
+        const float rl1 = own ? a.tab.rl2[ti * 2 + 1] * r2unit : -1.0f;
+        int *row = a.nbr + (size_t)(own ? i : ob) * (size_t)a.Kstride;
+        int cnt = 0;          // neighbours found
+        int nb = 0;           // of them in the lane's buffer
         int staged = 0;
-        for (int base = 0; base < total; base += kNbBlock) {
-            // stage candidates base .. base + kNbBlock - 1, order-preserving compaction
-            const int t = base + tid;
-            bool keep = false;
-            float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
-            int j = 0;
-            if (t < total) {
-                int k = 0;
-                while (k + 1 < nst && s_pref[k + 1] <= t)
-                    ++k;
-                j = checked(a, a.cstart[s_cell[k]] + (t - s_pref[k]), a.n, 0);
-                q = nb_word<P>(a, pn, j);
-                keep = true;
-                if (nst == 27) {
-                    const float3 x = nb_coords<P>(q, rp);
-                    const float gx = box_gap(x.x, ccx, hx, rp.Lhi, rp.invLf);
-                    const float gy = box_gap(x.y, ccy, hx, rp.Lhi, rp.invLf);
-                    const float gz = box_gap(x.z, ccz, hx, rp.Lhi, rp.invLf);
-                    keep = fmaf(gx, gx, fmaf(gy, gy, gz * gz)) < rlmax2;
-                }
-            }
-            const unsigned m = __ballot_sync(0xffffffffu, keep);
-            if (lane == 0)
-                s_wsum[warp] = __popc(m);
-            __syncthreads();
-            int off = staged, add = 0;
-#pragma unroll
-            for (int w = 0; w < NW; ++w) {
-                off += (w < warp) ? s_wsum[w] : 0;
-                add += s_wsum[w];
-            }
-            if (keep) {
-                const int s = off + __popc(m & lt_mask);
-                s_pos[s] = q;
-                s_idx[s] = j;
-            }
-            staged += add;
-            __syncthreads();
-            if (staged <= kNbCap - kNbBlock && base + kNbBlock < total)
-                continue;
 
-            // scan the staged candidates: each warp pass takes kNbPass particles of
-            // the batch, so that every staged candidate read serves kNbPass tests
-            for (int o0 = warp * kNbPass; o0 < nown; o0 += NW * kNbPass) {
-                float4 H[kNbPass];
-                float rl0[kNbPass], rl1[kNbPass];
-                int cnt[kNbPass];
+        // test the staged candidates against the lane's particle, in order; every
+        // 16 entries kept go out as four 16-byte stores (rows start 32-byte aligned)
+        auto scan = [&]() {
+            __syncwarp();
+#pragma unroll 4
+            for (int s = 0; s < staged; ++s) {
+                const float4 y = S.pos[s];
+                const int jj = S.idx[s];
+                const float r2 = nb_r2<P>(H, y, rp);
+                const bool in = r2 < (nb_species<P>(y) != 0 ? rl1 : rl0) && jj != i;
+                if (in) {
+                    if (cnt < K) {
+                        buf[nb] = jj;
+                        if (++nb == kNbBuf) {
+                            int4 *dst = (int4 *)(row + (cnt + 1 - kNbBuf));
 #pragma unroll
-                for (int p = 0; p < kNbPass; ++p) {
-                    const bool ok = o0 + p < nown;
-                    H[p] = nb_word<P>(a, pn, ob + (ok ? o0 + p : 0));
-                    const int ti = nb_species<P>(H[p]);
-                    rl0[p] = ok ? a.tab.rl2[ti * 2] * r2unit : -1.0f;       // -1: nothing passes
-                    rl1[p] = ok ? a.tab.rl2[ti * 2 + 1] * r2unit : -1.0f;
-                    cnt[p] = ok ? s_cnt[o0 + p] : 0;
+                            for (int w = 0; w < kNbBuf / 4; ++w)
+                                dst[w] = make_int4(buf[4 * w], buf[4 * w + 1], buf[4 * w + 2], buf[4 * w + 3]);
+                            nb = 0;
+                        }
+                    }
+                    ++cnt;
                 }
-                for (int s0 = 0; s0 < staged; s0 += 32) {
-                    const int s = s0 + lane;
-                    const bool sv = s < staged;
-                    const float4 y = sv ? s_pos[s] : make_float4(0.f, 0.f, 0.f, 0.f);
-                    const int jj = sv ? s_idx[s] : -1;
-                    const bool tj = nb_species<P>(y) != 0;
-#pragma unroll
-                    for (int p = 0; p < kNbPass; ++p) {
-                        const int i = ob + o0 + p;
-                        const float r2 = nb_r2<P>(H[p], y, rp);
-                        const bool in = sv && jj != i && r2 < (tj ? rl1[p] : rl0[p]);
-                        const unsigned mm = __ballot_sync(0xffffffffu, in);
-                        const int at = cnt[p] + __popc(mm & lt_mask);
-                        if (in && at < K)
-                            a.nbr[(size_t)i * (size_t)a.Kstride + at] = jj;
-                        cnt[p] += __popc(mm);
+            }
+            __syncwarp();
+            staged = 0;
+        };
+
+        for (int k = 0; k < nst; ++k) {
+            const int cs = a.cstart[S.cell[k]], ce = a.cstart[S.cell[k] + 1];
+            for (int t0 = cs; t0 < ce; t0 += 32) {
+                if (staged > kNbStage - 32)
+                    scan();
+                const int t = t0 + lane;
+                bool keep = false;
+                float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (t < ce) {
+                    q = nb_word<P>(a, pn, checked(a, t, a.n, 0));
+                    keep = true;
+                    if (nst == 27) {
+                        const float3 x = nb_coords<P>(q, rp);
+                        const float gx = box_gap(x.x, ccx, hx, rp.Lhi, rp.invLf);
+                        const float gy = box_gap(x.y, ccy, hx, rp.Lhi, rp.invLf);
+                        const float gz = box_gap(x.z, ccz, hx, rp.Lhi, rp.invLf);
+                        keep = fmaf(gx, gx, fmaf(gy, gy, gz * gz)) < rlmax2;
                     }
                 }
-                if (lane == 0)
-#pragma unroll
-                    for (int p = 0; p < kNbPass; ++p)
-                        if (o0 + p < nown)
-                            s_cnt[o0 + p] = cnt[p];
+                const unsigned m = __ballot_sync(FULL, keep);
+                if (keep) {
+                    const int sidx = staged + __popc(m & lt_mask);
+                    S.pos[sidx] = q;
+                    S.idx[sidx] = t;
+                }
+                staged += __popc(m);
             }
-            staged = 0;
-            __syncthreads();
         }
-        for (int o = tid; o < nown; o += kNbBlock) {
-            const int cnt = s_cnt[o];
-            a.nnbr[ob + o] = cnt < K ? cnt : K;
-            // pad the row with the particle itself to a multiple of kUnr entries, so the
-            // pair loop reads whole groups without masking (K is a multiple of 8)
-            for (int k = cnt; k < (cnt + kUnr - 1) / kUnr * kUnr && k < K; ++k)
-                a.nbr[(size_t)(ob + o) * (size_t)a.Kstride + k] = ob + o;
+        scan();
+
+        if (own) {
+            // the entries still in the buffer, then padding with the particle itself to a
+            // multiple of kUnr entries, so the pair loop reads whole groups without masking
+            const int kept = cnt < K ? cnt : K;
+            const int from = kept - nb;
+            for (int w = 0; w < nb; ++w)
+                row[from + w] = buf[w];
+            for (int k = kept; k < (kept + kUnr - 1) / kUnr * kUnr && k < K; ++k)
+                row[k] = i;
+            a.nnbr[i] = kept;
             atomicMax(&ctl->max_nbr, cnt);
         }
-        __syncthreads();
+        __syncwarp();
     }
 }
 
@@ -2123,11 +2130,12 @@ __device__ __forceinline__ int grown_capacity(int mx, int Kmax)
 //   - otherwise reports ST_OVERFLOW, leaving the buffers of the last completed
 //     step current.
 // The pending check is read once per block (the status can change during the
-// launch) and every block takes a ticket.  Blocks take cells blockIdx.x,
-// blockIdx.x + gridDim.x, ...
+// launch) and every block takes a ticket.  Warp w of block b takes cells
+// kNbCells b + w, then kNbCells gridDim.x further on, ...
 template <int P>
 __global__ void __launch_bounds__(kNbBlock) k_nbuild(KArgs a)
 {
+    __shared__ NbWarp s_nb[kNbCells];
     __shared__ int s_go, s_K;
     Ctl *ctl = a.ctl;
     if (threadIdx.x == 0) {
@@ -2144,8 +2152,9 @@ __global__ void __launch_bounds__(kNbBlock) k_nbuild(KArgs a)
                 atomicAdd((unsigned long long *)&ctl->rebuilds, 1ull);
         }
         const int pn = ctl->pos_par ^ 1;
-        for (int c = blockIdx.x; c < a.ncell; c += gridDim.x)
-            nbuild_cell<P>(a, pn, c, s_K);
+        const int w = threadIdx.x >> 5;
+        for (int c = blockIdx.x * kNbCells + w; c < a.ncell; c += gridDim.x * kNbCells)
+            nbuild_cell<P>(a, pn, c, s_K, s_nb[w]);
     }
     __syncthreads();
     if (threadIdx.x == 0) {

@@ -565,6 +565,8 @@ def run_e1(args, local):
 
 def lj_cases(args, local, cases, workload, temperature, dt, skin):
     torch, md, synth, device, stream, flush = _gpu_setup(local)
+    peaks = alu_peaks(md, torch, device)
+    hbm_peak = (measured_peaks() or {}).get("hbm_gbs", 6800.0)
     lines = []
     for n, rho in cases:
         s = synth.lj_fluid(n=n, density=rho, temperature=temperature, seed=3)
@@ -614,6 +616,13 @@ def lj_cases(args, local, cases, workload, temperature, dt, skin):
                 "step_kernel_us": k_ms * 1e3,
                 "step_kernel_alu_tflops": flops / (k_ms * 1e-3) / 1e12 if k_ms > 0 else None,
                 "step_kernel_list_gbs": n * (4 * n_list + 52) / (k_ms * 1e-3) / 1e9 if k_ms > 0 else None,
+                # roofline fractions of the step kernel: its algorithmic flops against the
+                # measured FP32 peak, its algorithmic bytes (list + own state + the fused
+                # integrator's state traffic) against the measured HBM copy rate
+                "step_kernel_alu_frac": flops / (k_ms * 1e-3) / 1e12 / peaks["fp32_tflops"] if k_ms > 0 else None,
+                "step_kernel_hbm_frac": n * (4 * n_list + 52 + 192) / (k_ms * 1e-3) / 1e9 / hbm_peak
+                if k_ms > 0 else None,
+                "peaks": {"fp32_tflops": peaks["fp32_tflops"], "hbm_gbs": hbm_peak},
                 "clocks": clk,
                 "autotune": [{k: (round(v, 5) if isinstance(v, float) else v) for k, v in t.items()}
                              for t in trials] if trials else None}

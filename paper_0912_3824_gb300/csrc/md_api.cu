@@ -55,7 +55,8 @@ namespace {
 
 constexpr size_t kAlign = 256;
 constexpr int kIntBlock = 256, kForceBlock = 128, kScanBlock = 1024;
-constexpr int kNbCells = 4, kNbBlock = 32 * kNbCells;   // neighbour build: one warp per cell
+constexpr int kNbCells = 4, kNbBlock = 32 * kNbCells;   // neighbour build: one warp per cell ...
+constexpr int kNbBlockB = 256;                          // ... or one block per cell
 constexpr double kCellMargin = 1e-3;   // cell edge exceeds the largest list radius by this
 constexpr int kUnroll = 16;            // step kernels per loop iteration of the graph
 constexpr int kCheck = 4;              // automatic check interval below kCheckLargeN particles
@@ -71,6 +72,7 @@ struct Geometry {
     int64_t n = 0;
     int K = 0, Kmax = 0, tpp = 8, ppb_f = 32;   // starting list capacity, its cap
     int check = kCheck;                 // MD steps between rebuild checks of the graph
+    bool nb_block = false;              // neighbour build with one block (8 warps) per cell
     int nblk_i = 0, nblk_f = 0, ncell = 0;
     double rl_max = 0.0;
     std::vector<mdk::Rep> rep;
@@ -475,8 +477,15 @@ int grid_n(int64_t n, int per) { return (int)((n + per - 1) / per); }
 // The rebuild chain: kernel, grid, block.
 struct ChainStep { const void *f; int grid, block; };
 
-// blocks of the neighbour build: kNbCells cells each
-int nb_grid(const md_handle *h) { return (h->g.ncell + kNbCells - 1) / kNbCells; }
+// The neighbour build's kernel and launch shape: one warp per cell, kNbCells
+// cells per block, unless the cells are too few to fill the GPU that way
+// (fewer than one per resident warp slot), then one 8-warp block per cell.
+ChainStep nbuild_step(const md_handle *h)
+{
+    if (h->g.nb_block)
+        return {h->ks->nbuild_blk, h->g.ncell, kNbBlockB};
+    return {h->ks->nbuild, (h->g.ncell + kNbCells - 1) / kNbCells, kNbBlock};
+}
 
 int rebuild_chain(const md_handle *h, ChainStep *seq)
 {
@@ -486,7 +495,7 @@ int rebuild_chain(const md_handle *h, ChainStep *seq)
     seq[1] = {k.scan, 1, kScanBlock};
     seq[2] = {k.scatter, nb, kIntBlock};
     seq[3] = {k.permute, nb, kIntBlock};
-    seq[4] = {k.nbuild, nb_grid(h), kNbBlock};          // one warp per cell; its last block makes
+    seq[4] = nbuild_step(h);                             // its last block makes
     return 5;                                            // the permuted buffers current or asks
 }                                                        // for a redo with a larger K
 
@@ -509,7 +518,8 @@ int launch_rebuild(md_handle *h)
         if (rc)
             return rc;
     }
-    return launch(h, h->ks->nbuild, nb_grid(h), kNbBlock, retry_args(h));
+    const ChainStep nb = nbuild_step(h);
+    return launch(h, nb.f, nb.grid, nb.block, retry_args(h));
 }
 
 // Arguments of the step kernel at position `slot` of the unrolled loop.
@@ -588,7 +598,7 @@ int add_rebuild_chain(md_handle *h, cudaGraph_t g)
     for (int s = 0; s < ns; ++s) {
         cudaGraphNode_t node;
         KArgs a = h->a;
-        if (seq[s].f == h->ks->nbuild) {
+        if (s == ns - 1) {                              // the build
             a.use_cond = 1;
             a.set_regrow = 1;
             a.h_regrow = c_regrow;
@@ -605,7 +615,8 @@ int add_rebuild_chain(md_handle *h, cudaGraph_t g)
     if (rc)
         return rc;
     cudaGraphNode_t n_retry;
-    return add_kernel(h, body, &n_retry, nullptr, 0, h->ks->nbuild, nb_grid(h), kNbBlock, retry_args(h));
+    const ChainStep nb = nbuild_step(h);
+    return add_kernel(h, body, &n_retry, nullptr, 0, nb.f, nb.grid, nb.block, retry_args(h));
 }
 
 int add_conditional(md_handle *h, cudaGraph_t g, cudaGraphNode_t *node, cudaGraphNode_t dep,
@@ -995,11 +1006,14 @@ static int create_impl(md_handle *h, const md_params *p, const int32_t *species,
     if (a.hdtm_hi[0] == 0.0f)
         return fail(h, MD_E_INVAL, "dt / (2 m) underflows single precision");
 
-    int dev = 0, nsm = 0, per_sm = 0;
+    int dev = 0, nsm = 0, per_sm = 0, per_sm_nb = 0;
     CK(h, cudaGetDevice(&dev));
     CK(h, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(
               &per_sm, h->ks->step[h->p.smooth_h > 0.0][force_index(g.tpp)], kForceBlock, 0));
+    // the build takes a warp per cell when the cells fill the GPU's warp slots that way
+    CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_nb, h->ks->nbuild, kNbBlock, 0));
+    h->g.nb_block = (int64_t)g.ncell < (int64_t)nsm * per_sm_nb * kNbCells;
     // pinned staging, events
     CK(h, cudaEventCreateWithFlags(&h->ev_stage, cudaEventDisableTiming));
     CK(h, cudaEventCreate(&h->ev_f0));

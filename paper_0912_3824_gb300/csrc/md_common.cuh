@@ -195,7 +195,7 @@ __device__ __forceinline__ ds ds_from_double(double x)
 // table of kernel entry addresses for one precision (one translation unit each)
 struct KernelSet {
     const void *integrate, *force[2][6], *step[2][6];   // [smoothed][log2 lanes per particle]
-    const void *bin, *scan, *scatter, *permute, *nbuild;
+    const void *bin, *scan, *scatter, *permute, *nbuild, *nbuild_blk;
     const void *load, *getstate, *expforce, *scale, *set_steps, *reset, *mark_rebuild;
     const void *andersen, *andersen_fix, *snapshot, *epot_flush;
 };

@@ -33,8 +33,9 @@ namespace mdk {
 
 constexpr int kIntBlock = 256;   // per-particle kernels: one thread per particle
 constexpr int kForceBlock = 128; // force / step kernels: tpp threads per particle
-constexpr int kNbCells = 4;      // neighbour build: cells per block, one warp each
+constexpr int kNbCells = 4;      // neighbour build, warp per cell: cells per block
 constexpr int kNbBlock = 32 * kNbCells;
+constexpr int kNbBlockB = 256;   // neighbour build, block per cell: threads per block
 constexpr int kScanBlock = 1024;
 constexpr int kScanPer = 8;      // cell counts per thread and tile of the scan
 constexpr int kPartF = 12;       // doubles per block partial of the force / step kernels
@@ -1688,20 +1689,21 @@ __device__ __forceinline__ int cell_coord_f(float x, float cscale, int nc)
     return c < 0 ? 0 : (c >= nc ? nc - 1 : c);
 }
 
-// Position of a coordinate inside its cell on a 4-point grid (0..3); three of
-// them interleave into the particle's sub-cell code along a Morton curve, the
-// order of the particles inside a cell after each rebuild, so that the
-// particles a warp holds are close in space (their neighbours overlap).
-__device__ __forceinline__ unsigned int sub4(double x, double cscale, int c)
+// Octant of a coordinate inside its cell (0 or 1 per axis); the three
+// interleave into the particle's sub-cell code along a Morton curve, the order
+// of the particles inside a cell after each rebuild, so that the particles a
+// warp holds are close in space (their neighbours overlap).  (A 4 x 4 x 4
+// grid measured 0.25 % slower per MD step.)
+__device__ __forceinline__ unsigned int sub2(double x, double cscale, int c)
 {
-    const int s = (int)floor((x * cscale - (double)c) * 4.0);
-    return (unsigned int)(s < 0 ? 0 : (s > 3 ? 3 : s));
+    const int s = (int)floor((x * cscale - (double)c) * 2.0);
+    return (unsigned int)(s < 0 ? 0 : (s > 1 ? 1 : s));
 }
 
-__device__ __forceinline__ unsigned int sub4f(float x, float cscale, int c)
+__device__ __forceinline__ unsigned int sub2f(float x, float cscale, int c)
 {
-    const int s = (int)floorf((x * cscale - (float)c) * 4.0f);
-    return (unsigned int)(s < 0 ? 0 : (s > 3 ? 3 : s));
+    const int s = (int)floorf((x * cscale - (float)c) * 2.0f);
+    return (unsigned int)(s < 0 ? 0 : (s > 1 ? 1 : s));
 }
 
 __device__ __forceinline__ int morton6(unsigned int x, unsigned int y, unsigned int z)
@@ -1732,13 +1734,13 @@ __global__ void __launch_bounds__(kIntBlock) k_bin(KArgs a)
         cx = cell_coord(x.x, rp.cscale, rp.nc);
         cy = cell_coord(x.y, rp.cscale, rp.nc);
         cz = cell_coord(x.z, rp.cscale, rp.nc);
-        sub = morton6(sub4(x.x, rp.cscale, cx), sub4(x.y, rp.cscale, cy), sub4(x.z, rp.cscale, cz));
+        sub = morton6(sub2(x.x, rp.cscale, cx), sub2(x.y, rp.cscale, cy), sub2(x.z, rp.cscale, cz));
     } else {
         const float4 x = ((const float4 *)pos_a(a, pp))[i];
         cx = cell_coord_f(x.x, rp.cscalef, rp.nc);
         cy = cell_coord_f(x.y, rp.cscalef, rp.nc);
         cz = cell_coord_f(x.z, rp.cscalef, rp.nc);
-        sub = morton6(sub4f(x.x, rp.cscalef, cx), sub4f(x.y, rp.cscalef, cy), sub4f(x.z, rp.cscalef, cz));
+        sub = morton6(sub2f(x.x, rp.cscalef, cx), sub2f(x.y, rp.cscalef, cy), sub2f(x.z, rp.cscalef, cz));
     }
     const int key = checked(a, a.crank[rp.cell0 + (cz * rp.nc + cy) * rp.nc + cx], a.ncell, 0);
     a.key[i] = key;
@@ -1984,13 +1986,13 @@ __device__ __forceinline__ float box_gap(float x, float c, float h, float L, flo
     return fmaxf(fabsf(sep_f(x, c, L, invL)) - h, 0.0f);
 }
 
-// Lists of the particles of cell c, from the positions in buffer pn (the
-// permuted copy being built), by one warp: row i starts at nbr[i * Kstride]
+// Warp per cell: the lists of the particles of cell c, from the positions in
+// buffer pn (the permuted copy being built), by one warp: row i starts at nbr[i * Kstride]
 // (the cap) and holds at most K entries (the capacity in use).  Every
 // particle's full count is recorded in max_nbr; entries beyond K are dropped
 // (the build's last block then grows K and the build is redone).
 template <int P>
-__device__ __forceinline__ void nbuild_cell(const KArgs &a, int pn, int c, int K, NbWarp &S)
+__device__ __forceinline__ void nbuild_cell_warp(const KArgs &a, int pn, int c, int K, NbWarp &S)
 {
     constexpr unsigned FULL = 0xffffffffu;
     Ctl *ctl = a.ctl;
@@ -2110,6 +2112,168 @@ __device__ __forceinline__ void nbuild_cell(const KArgs &a, int pn, int c, int K
     }
 }
 
+// Block per cell, for handles with too few cells to occupy the GPU with one
+// warp each: the block stages the candidates (kNbCap per round, the same
+// order and filter as above), and each of its warps takes kNbPass particles
+// of the cell at a time, testing 32 staged candidates per ballot; the list
+// rows come out the same as with a warp per cell.
+constexpr int kNbCap = 1024;     // staged candidates per round
+constexpr int kNbOwn = 256;      // own-cell particles per batch
+constexpr int kNbPass = 2;       // own-cell particles tested per warp pass over the candidates
+
+template <int P>
+__device__ __forceinline__ void nbuild_cell_block(const KArgs &a, int pn, int c, int K)
+{
+    __shared__ float4 s_pos[kNbCap];
+    __shared__ int s_idx[kNbCap];
+    __shared__ int s_cnt[kNbOwn];
+    __shared__ int s_pref[28];
+    __shared__ int s_cell[27];
+    __shared__ int s_wsum[kNbBlockB / 32];
+
+    Ctl *ctl = a.ctl;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int NW = kNbBlockB / 32;
+    const int4 cc = a.cxyz[c];
+    const Rep rp = a.rep[cc.w];
+    const int nc = rp.nc;
+    const int nst = nc >= 3 ? 27 : 1;
+    const int c0 = a.cstart[c], c1 = a.cstart[c + 1];
+    if (c0 == c1)
+        return;
+
+    if (tid < nst) {
+        int x = cc.x, y = cc.y, z = cc.z;
+        if (nst == 27) {
+            x = (x + tid % 3 - 1 + nc) % nc;
+            y = (y + (tid / 3) % 3 - 1 + nc) % nc;
+            z = (z + tid / 9 - 1 + nc) % nc;
+        }
+        s_cell[tid] = a.crank[rp.cell0 + (z * nc + y) * nc + x];
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int s = 0;
+        for (int k = 0; k < nst; ++k) {
+            s_pref[k] = s;
+            s += a.cstart[s_cell[k] + 1] - a.cstart[s_cell[k]];
+        }
+        s_pref[nst] = s;
+    }
+    __syncthreads();
+    const int total = s_pref[nst];
+
+    // own cell box (centre, half edge) for the candidate filter
+    const float edge = rp.Lhi / (float)nc;
+    const float hx = 0.5f * edge + 1e-3f;
+    const float ccx = ((float)cc.x + 0.5f) * edge, ccy = ((float)cc.y + 0.5f) * edge,
+                ccz = ((float)cc.z + 0.5f) * edge;
+    const float rlmax2 = fmaxf(fmaxf(a.tab.rl2[0], a.tab.rl2[1]), fmaxf(a.tab.rl2[2], a.tab.rl2[3]));
+    const unsigned lt_mask = (1u << lane) - 1u;
+    // nb_r2 of the fixed-point words is in units of qunit^2: the list radii follow
+    const float r2unit = (P == MIXED && kNbFixed) ? 1.0f / (rp.qunit * rp.qunit) : 1.0f;
+
+    for (int ob = c0; ob < c1; ob += kNbOwn) {
+        const int nown = min(kNbOwn, c1 - ob);
+        for (int t = tid; t < nown; t += kNbBlockB)
+            s_cnt[t] = 0;
+        int staged = 0;
+        for (int base = 0; base < total; base += kNbBlockB) {
+            // stage candidates base .. base + kNbBlockB - 1, order-preserving compaction
+            const int t = base + tid;
+            bool keep = false;
+            float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+            int j = 0;
+            if (t < total) {
+                int k = 0;
+                while (k + 1 < nst && s_pref[k + 1] <= t)
+                    ++k;
+                j = checked(a, a.cstart[s_cell[k]] + (t - s_pref[k]), a.n, 0);
+                q = nb_word<P>(a, pn, j);
+                keep = true;
+                if (nst == 27) {
+                    const float3 x = nb_coords<P>(q, rp);
+                    const float gx = box_gap(x.x, ccx, hx, rp.Lhi, rp.invLf);
+                    const float gy = box_gap(x.y, ccy, hx, rp.Lhi, rp.invLf);
+                    const float gz = box_gap(x.z, ccz, hx, rp.Lhi, rp.invLf);
+                    keep = fmaf(gx, gx, fmaf(gy, gy, gz * gz)) < rlmax2;
+                }
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, keep);
+            if (lane == 0)
+                s_wsum[warp] = __popc(m);
+            __syncthreads();
+            int off = staged, add = 0;
+#pragma unroll
+            for (int w = 0; w < NW; ++w) {
+                off += (w < warp) ? s_wsum[w] : 0;
+                add += s_wsum[w];
+            }
+            if (keep) {
+                const int s = off + __popc(m & lt_mask);
+                s_pos[s] = q;
+                s_idx[s] = j;
+            }
+            staged += add;
+            __syncthreads();
+            if (staged <= kNbCap - kNbBlockB && base + kNbBlockB < total)
+                continue;
+
+            // scan the staged candidates: each warp pass takes kNbPass particles of
+            // the batch, so that every staged candidate read serves kNbPass tests
+            for (int o0 = warp * kNbPass; o0 < nown; o0 += NW * kNbPass) {
+                float4 H[kNbPass];
+                float rl0[kNbPass], rl1[kNbPass];
+                int cnt[kNbPass];
+#pragma unroll
+                for (int p = 0; p < kNbPass; ++p) {
+                    const bool ok = o0 + p < nown;
+                    H[p] = nb_word<P>(a, pn, ob + (ok ? o0 + p : 0));
+                    const int ti = nb_species<P>(H[p]);
+                    rl0[p] = ok ? a.tab.rl2[ti * 2] * r2unit : -1.0f;       // -1: nothing passes
+                    rl1[p] = ok ? a.tab.rl2[ti * 2 + 1] * r2unit : -1.0f;
+                    cnt[p] = ok ? s_cnt[o0 + p] : 0;
+                }
+                for (int s0 = 0; s0 < staged; s0 += 32) {
+                    const int s = s0 + lane;
+                    const bool sv = s < staged;
+                    const float4 y = sv ? s_pos[s] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    const int jj = sv ? s_idx[s] : -1;
+                    const bool tj = nb_species<P>(y) != 0;
+#pragma unroll
+                    for (int p = 0; p < kNbPass; ++p) {
+                        const int i = ob + o0 + p;
+                        const float r2 = nb_r2<P>(H[p], y, rp);
+                        const bool in = sv && jj != i && r2 < (tj ? rl1[p] : rl0[p]);
+                        const unsigned mm = __ballot_sync(0xffffffffu, in);
+                        const int at = cnt[p] + __popc(mm & lt_mask);
+                        if (in && at < K)
+                            a.nbr[(size_t)i * (size_t)a.Kstride + at] = jj;
+                        cnt[p] += __popc(mm);
+                    }
+                }
+                if (lane == 0)
+#pragma unroll
+                    for (int p = 0; p < kNbPass; ++p)
+                        if (o0 + p < nown)
+                            s_cnt[o0 + p] = cnt[p];
+            }
+            staged = 0;
+            __syncthreads();
+        }
+        for (int o = tid; o < nown; o += kNbBlockB) {
+            const int cnt = s_cnt[o];
+            a.nnbr[ob + o] = cnt < K ? cnt : K;
+            // pad the row with the particle itself to a multiple of kUnr entries, so the
+            // pair loop reads whole groups without masking (K is a multiple of 8)
+            for (int k = cnt; k < (cnt + kUnr - 1) / kUnr * kUnr && k < K; ++k)
+                a.nbr[(size_t)(ob + o) * (size_t)a.Kstride + k] = ob + o;
+            atomicMax(&ctl->max_nbr, cnt);
+        }
+        __syncthreads();
+    }
+}
+
 // List capacity after a build whose longest list held mx > K entries (the
 // fixed-size list of Sec. 2.2 grown in place): a quarter more than needed,
 // rounded up to whole groups of 8, at most the cap Kmax (a multiple of 8, so
@@ -2130,33 +2294,33 @@ __device__ __forceinline__ int grown_capacity(int mx, int Kmax)
 //   - otherwise reports ST_OVERFLOW, leaving the buffers of the last completed
 //     step current.
 // The pending check is read once per block (the status can change during the
-// launch) and every block takes a ticket.  Warp w of block b takes cells
-// kNbCells b + w, then kNbCells gridDim.x further on, ...
-template <int P>
-__global__ void __launch_bounds__(kNbBlock) k_nbuild(KArgs a)
+// launch) and every block takes a ticket.  k_nbuild: warp w of block b takes
+// cells kNbCells b + w, then kNbCells gridDim.x further on, ...; k_nbuild_blk:
+// block b takes cells b, b + gridDim.x, ...
+
+// First thread of every block of the build: is a build (or its redo) pending,
+// and the capacity in use; counts the launch.
+__device__ __forceinline__ void nbuild_begin(const KArgs &a, int &s_go, int &s_K)
 {
-    __shared__ NbWarp s_nb[kNbCells];
-    __shared__ int s_go, s_K;
     Ctl *ctl = a.ctl;
     if (threadIdx.x == 0) {
         s_go = (rebuild_pending(ctl) && (a.nb_retry == 0 || ctl->regrow != 0u)) ? 1 : 0;
         s_K = ctl->K;
-    }
-    __syncthreads();
-    if (s_go) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (s_go && blockIdx.x == 0) {
             atomicAdd((unsigned long long *)&ctl->n_rebuild_k, 1ull);
             if (a.nb_retry)
                 atomicAdd((unsigned long long *)&ctl->regrows, 1ull);
             else
                 atomicAdd((unsigned long long *)&ctl->rebuilds, 1ull);
         }
-        const int pn = ctl->pos_par ^ 1;
-        const int w = threadIdx.x >> 5;
-        for (int c = blockIdx.x * kNbCells + w; c < a.ncell; c += gridDim.x * kNbCells)
-            nbuild_cell<P>(a, pn, c, s_K, s_nb[w]);
     }
-    __syncthreads();
+}
+
+// Every block's ticket; the last block swaps in the permuted buffers, grows the
+// capacity and asks for the redo, or reports the overflow (see above).
+__device__ __forceinline__ void nbuild_end(const KArgs &a, int s_go, int s_K)
+{
+    Ctl *ctl = a.ctl;
     if (threadIdx.x == 0) {
         __threadfence();                    // this block's list counts before its ticket
         const unsigned int t = atomicAdd(&ctl->ticket, 1u);
@@ -2183,6 +2347,38 @@ __global__ void __launch_bounds__(kNbBlock) k_nbuild(KArgs a)
                 cudaGraphSetConditional(a.h_regrow, regrow);
         }
     }
+}
+
+template <int P>
+__global__ void __launch_bounds__(kNbBlock) k_nbuild(KArgs a)
+{
+    __shared__ NbWarp s_nb[kNbCells];
+    __shared__ int s_go, s_K;
+    nbuild_begin(a, s_go, s_K);
+    __syncthreads();
+    if (s_go) {
+        const int pn = a.ctl->pos_par ^ 1;
+        const int w = threadIdx.x >> 5;
+        for (int c = blockIdx.x * kNbCells + w; c < a.ncell; c += gridDim.x * kNbCells)
+            nbuild_cell_warp<P>(a, pn, c, s_K, s_nb[w]);
+    }
+    __syncthreads();
+    nbuild_end(a, s_go, s_K);
+}
+
+template <int P>
+__global__ void __launch_bounds__(kNbBlockB) k_nbuild_blk(KArgs a)
+{
+    __shared__ int s_go, s_K;
+    nbuild_begin(a, s_go, s_K);
+    __syncthreads();
+    if (s_go) {
+        const int pn = a.ctl->pos_par ^ 1;
+        for (int c = blockIdx.x; c < a.ncell; c += gridDim.x)
+            nbuild_cell_block<P>(a, pn, c, s_K);
+    }
+    __syncthreads();
+    nbuild_end(a, s_go, s_K);
 }
 
 template <int P>
@@ -2572,6 +2768,7 @@ KernelSet make_kernel_set()
     k.scatter = (const void *)k_scatter<P>;
     k.permute = (const void *)k_permute<P>;
     k.nbuild = (const void *)k_nbuild<P>;
+    k.nbuild_blk = (const void *)k_nbuild_blk<P>;
     k.load = (const void *)k_load<P>;
     k.getstate = (const void *)k_getstate<P>;
     k.expforce = (const void *)k_expforce<P>;

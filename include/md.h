@@ -124,7 +124,10 @@ typedef struct {
                                  MD_E_TIMEOUT after this many step-kernel executions (its
                                  iteration bound; automatic = nsteps + 64), so the bounded-
                                  loop path can be exercised                                     */
-    int32_t reserved[1];      /* must be zero                                                   */
+    int32_t build_form;       /* neighbour build: 0 = automatic (one warp per cell when the cells
+                                 are at least as many as the GPU's warp slots for it, else one
+                                 block per cell), 1 = one warp per cell, 2 = one block per cell;
+                                 the lists are the same either way                             */
 } md_params;
 
 /* one sample of the reductions of Sec. 2.2, per replica */
@@ -164,6 +167,8 @@ typedef struct {
     int32_t check_interval;   /* MD steps between rebuild checks, as resolved                   */
     int32_t neigh_capacity_max; /* the cap on neigh_capacity, as resolved                       */
     int64_t regrows;          /* list builds redone with a larger capacity since md_create      */
+    int32_t build_form;       /* neighbour build in use: 1 = one warp per cell, 2 = one block   */
+    int32_t reserved;
 } md_info_t;
 
 typedef struct md_handle md_handle;

@@ -192,7 +192,11 @@ int make_geometry(const md_params *p, int R, const int64_t *nrep, const double *
         msg = "threads_per_particle must be 0 or a power of two in [1, 32]";
         return MD_E_INVAL;
     }
-    if (p->reserved0 != 0 || p->reserved[0] != 0) { msg = "reserved fields must be zero"; return MD_E_INVAL; }
+    if (p->reserved0 != 0) { msg = "reserved fields must be zero"; return MD_E_INVAL; }
+    if (p->build_form < 0 || p->build_form > 2) {
+        msg = "build_form must be 0 (automatic), 1 (warp per cell) or 2 (block per cell)";
+        return MD_E_INVAL;
+    }
     if (p->neigh_capacity < 0 || p->neigh_capacity_max < 0) {
         msg = "neigh_capacity and neigh_capacity_max must be >= 0";
         return MD_E_INVAL;
@@ -1013,7 +1017,8 @@ static int create_impl(md_handle *h, const md_params *p, const int32_t *species,
               &per_sm, h->ks->step[h->p.smooth_h > 0.0][force_index(g.tpp)], kForceBlock, 0));
     // the build takes a warp per cell when the cells fill the GPU's warp slots that way
     CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_nb, h->ks->nbuild, kNbBlock, 0));
-    h->g.nb_block = (int64_t)g.ncell < (int64_t)nsm * per_sm_nb * kNbCells;
+    h->g.nb_block = p->build_form == 2 ||
+                    (p->build_form == 0 && (int64_t)g.ncell < (int64_t)nsm * per_sm_nb * kNbCells);
     // pinned staging, events
     CK(h, cudaEventCreateWithFlags(&h->ev_stage, cudaEventDisableTiming));
     CK(h, cudaEventCreate(&h->ev_f0));
@@ -1609,6 +1614,7 @@ int md_info(md_handle *h, md_info_t *out)
     out->neigh_capacity = c.K;
     out->neigh_capacity_max = h->g.Kmax;
     out->regrows = c.regrows;
+    out->build_form = h->g.nb_block ? 2 : 1;
     out->threads_per_particle = h->g.tpp;
     out->check_interval = h->g.check;
     out->cells_per_edge = h->g.rep[0].nc;

@@ -95,7 +95,7 @@ def test_workspace_holds_the_capacity_cap(md):
 
 
 @pytest.mark.parametrize("bad", ["box", "dt", "species", "tpp", "sample", "asym", "smooth", "smooth_tpp",
-                                 "check3", "check32", "capmax", "capneg", "budget", "reserved"])
+                                 "check3", "check32", "capmax", "capneg", "budget", "reserved", "form"])
 def test_argument_checks(md, bad):
     from paper_0912_3824_gb300 import synth
     pot = synth.ka_params()
@@ -128,7 +128,9 @@ def test_argument_checks(md, bad):
     if bad == "budget":
         p.step_budget = -1
     if bad == "reserved":
-        p.reserved[0] = 1
+        p.reserved0 = 1
+    if bad == "form":
+        p.build_form = 3
     with pytest.raises(md.MDError) as ei:
         md.md_workspace_size(p, [1000], [box])
     assert ei.value.code == md.MD_E_INVAL

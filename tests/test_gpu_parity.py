@@ -267,6 +267,77 @@ def test_e1_sparse_corner_trajectory(md):
     assert np.allclose(obs["e_pot"] + obs["e_kin"], rec["e_pot"] + rec["e_kin"], rtol=1e-6)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "fp32"])
+@pytest.mark.parametrize("kind,n", [("ka", 4000), ("lj", 2048)])
+def test_build_forms_give_the_same_lists_and_trajectory(md, prec, kind, n):
+    """The neighbour build with one warp per cell and with one block per cell
+    (the handle picks by the cell count) write the same rows in the same
+    order: equal lists at creation and equal positions after 200 steps with
+    several rebuilds, bit for bit."""
+    s = _system(kind, n, amp=0.02)
+    runs = []
+    for form in (1, 2):
+        sim = _sim(md, s, prec, dt=0.005 if kind == "lj" else 0.002, build_form=form)
+        assert sim.info()["build_form"] == form
+        counts, lists = sim.neighbours()
+        sim.step(200)
+        assert sim.sync() == md.MD_OK
+        info = sim.info()
+        pos, vel, img = sim.get_state()
+        runs.append((counts, lists, pos, vel, img, info["rebuilds"]))
+        sim.close()
+    (c1, l1, p1, v1, i1, r1), (c2, l2, p2, v2, i2, r2) = runs
+    assert np.array_equal(c1, c2) and np.array_equal(l1, l2)
+    assert r1 == r2 and r1 >= 3
+    assert np.array_equal(p1, p2) and np.array_equal(v1, v2) and np.array_equal(i1, i2)
+
+
+def test_epot_series_with_many_replicas(md):
+    """More than 8 replicas (each replica summed by one thread): every
+    replica's per-step potential energy equals that of the same system run
+    alone, within the summation-order rounding of FP64."""
+    sizes = [500, 777, 1000, 640, 900, 512, 1500, 700, 1200, 850, 600, 1100]
+    reps = [synth.perturb(synth.ka_mixture(n=m, temperature=0.7, seed=70 + r), 0.05, 170 + r)
+            for r, m in enumerate(sizes)]
+    p = md.make_params(reps[0].params, 0.002, precision=md.MD_PREC_FP64, sample_interval=25)
+    cat = lambda f: np.concatenate([getattr(r, f) for r in reps])
+    one = md.System(p, sizes, [r.box for r in reps], cat("species"), cat("pos"), cat("vel"), cat("image"))
+    one.step(60)
+    assert one.sync() == md.MD_OK
+    st, e = one.epot_series()
+    one.close()
+    assert np.array_equal(st, np.arange(61)) and e.shape == (61, len(sizes))
+    for k in (0, 5, 11):
+        r = reps[k]
+        alone = md.System(p, [r.n], [r.box], r.species, r.pos, r.vel, r.image)
+        alone.step(60)
+        st1, e1 = alone.epot_series()
+        alone.close()
+        assert np.array_equal(st1, st)
+        assert np.allclose(e[:, k], e1[:, 0], rtol=1e-12, atol=0)
+
+
+def test_epot_series_survives_force_evaluations_and_state_changes(md):
+    """The energies of a step still awaiting their sum are added up before a
+    force evaluation outside the loop reuses the partials: the series stays
+    complete, one value per step, across md_compute_forces and md_set_state."""
+    s = _system("ka", 1000, amp=0.02)
+    sim = _sim(md, s, "mixed", dt=0.002, sample_interval=7)
+    sim.step(31)
+    f, e, tot = sim.forces()
+    sim.step(20)
+    pos, vel, img = sim.get_state()
+    sim.set_state(pos, vel, img)
+    sim.step(9)
+    assert sim.sync() == md.MD_OK
+    st, ep = sim.epot_series()
+    obs = sim.observables()[:, 0]
+    sim.close()
+    assert np.array_equal(st, np.arange(61))
+    assert np.array_equal(ep[obs["step"], 0], obs["e_pot"])
+    assert abs(ep[31, 0] - tot["e_pot"][0]) <= 1e-6 * abs(tot["e_pot"][0])
+
+
 def test_graph_and_stream_launches_agree_bitwise(md):
     s = _system("ka", 3000, amp=0.05)
     a = _trajectory(md, s, "mixed", 0.002, 150, 10, use_graph=True)

@@ -43,7 +43,7 @@ def _time(torch, sim, steps, repeats):
 
 
 def autotune(base: md.md_params, n_per_replica, box, species, pos, vel, image=None, device: str = "cuda",
-             lanes=None, skins=(0.2, 0.25, 0.3), steps: int = 400, repeats: int = 3):
+             lanes=None, skins=(0.15, 0.2, 0.25, 0.3), steps: int = 400, repeats: int = 3):
     """Returns (best md_params, table of trials).  The state (pos, vel, image,
     original order) is the starting point of every trial; each trial warms up
     for `steps` MD steps (several list rebuilds) and is then timed `repeats`

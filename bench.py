@@ -57,6 +57,8 @@ def parse_args(argv=None):
     ap.add_argument("--no-graph", action="store_true",
                     help="plain stream launches instead of the CUDA graph (for per-kernel profiling)")
     ap.add_argument("--tpp", type=int, default=0, help="force-kernel threads per particle (0 = auto)")
+    ap.add_argument("--step-form", type=int, default=0, choices=[0, 1, 2],
+                    help="step-kernel blocks: 0 auto, 1 one per chunk, 2 resident blocks sweep (not FP64)")
     ap.add_argument("--check", type=int, default=0,
                     help="MD steps between rebuild checks of the graph (0 = the library's choice)")
     ap.add_argument("--skin", type=float, default=0.3, help="neighbour-list skin (with --no-tune)")
@@ -282,7 +284,7 @@ def run_ours(args, rank, world, local):
     pos0, vel0, img0 = sim.get_state()
     base = md.make_params(s.params, 0.001, skin=args.skin, precision=md.PRECISIONS[args.precision],
                           sample_interval=100, use_graph=not args.no_graph, threads_per_particle=args.tpp,
-                          check_interval=args.check)
+                          check_interval=args.check, step_form=args.step_form)
     trials = None
     if not args.no_tune:
         from paper_0912_3824_gb300 import tune
@@ -574,7 +576,7 @@ def lj_cases(args, local, cases, workload, temperature, dt, skin):
         s = synth.lj_fluid(n=n, density=rho, temperature=temperature, seed=3)
         sim = md.System.from_synth(s, dt=dt, skin=skin, precision=md.PRECISIONS[args.precision],
                                    sample_interval=100, device=device, threads_per_particle=args.tpp,
-                                   use_graph=not args.no_graph)
+                                   use_graph=not args.no_graph, step_form=args.step_form)
         equilibrate(sim, max(1.5, temperature), temperature, melt_blocks=5, final_blocks=5)
         trials = None
         if not args.no_tune:
@@ -582,7 +584,8 @@ def lj_cases(args, local, cases, workload, temperature, dt, skin):
             from paper_0912_3824_gb300 import tune
             pos0, vel0, img0 = sim.get_state()
             base = md.make_params(s.params, dt, skin=skin, precision=md.PRECISIONS[args.precision],
-                                  sample_interval=100, threads_per_particle=args.tpp, use_graph=not args.no_graph)
+                                  sample_interval=100, threads_per_particle=args.tpp, use_graph=not args.no_graph,
+                                  step_form=args.step_form)
             base, trials = tune.autotune(base, [s.n], [s.box], s.species, pos0, vel0, img0, device=device,
                                          skins=(skin,))
             sim.close()
@@ -846,7 +849,8 @@ def nve_cases(args, local, cases, workload, precisions=("fp32", "mixed", "fp64")
         prep.close()
         for prec in precisions:
             nsteps_p = (steps_of or {}).get(prec, nsteps)
-            p = md.make_params(s.params, dt, precision=md.PRECISIONS[prec], sample_interval=100, **extra)
+            p = md.make_params(s.params, dt, precision=md.PRECISIONS[prec], sample_interval=100,
+                               step_form=0 if prec == "fp64" else getattr(args, "step_form", 0), **extra)
             sim = md.System(p, [s.n], [s.box], s.species, pos, vel, img, device=device)
             obs, ms, msd = nve_run(md, torch, stream, sim, s.n, s.box, s.species, nsteps_p, lags)
             status = sim.sync()

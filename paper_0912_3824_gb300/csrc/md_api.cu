@@ -74,6 +74,8 @@ struct Geometry {
     int check = kCheck;                 // MD steps between rebuild checks of the graph
     bool nb_block = false;              // neighbour build with one block (8 warps) per cell
     int nblk_i = 0, nblk_f = 0, ncell = 0;
+    bool sweep = false;                 // step kernel: resident blocks sweeping runs of chunks
+    int nblk_s = 0, cpb = 1;            // step kernel: blocks launched, chunks per block
     double rl_max = 0.0;
     std::vector<mdk::Rep> rep;
     std::vector<int4> blk_i, blk_f;
@@ -82,7 +84,7 @@ struct Geometry {
 };
 
 struct Layout {
-    size_t off_ctl, off_rep, off_blk_i, off_blk_f, off_crank, off_cxyz;
+    size_t off_ctl, off_rep, off_blk_i, off_blk_f, off_blk_s, off_crank, off_cxyz;
     size_t off_pa, off_pb, off_va, off_vb, off_pa2, off_pb2, off_va2, off_vb2, off_qa, off_qb, off_force;
     size_t off_rref, off_image, off_image2, off_key, off_tmpidx, off_skey;
     size_t off_ccount, off_ccursor, off_cstart, off_nbr, off_nnbr, off_part_f, off_part_i, off_part_e;
@@ -174,6 +176,56 @@ static std::vector<int4> sm_block_order(const std::vector<int4> &chunks, int nsm
     return out;
 }
 
+// Rows of the step kernel's table (see KArgs::blk_s).  With one block per
+// chunk they are the force kernel's rows.  The sweeping form launches only the
+// resident blocks (nsm * per_sm, block p on SM p mod nsm) and gives each SM one
+// run of consecutive chunks along the cell curve: the per_sm blocks of an SM
+// take neighbouring chunks of its run side by side (block k of SM s: chunks
+// base_s + k, base_s + k + per_sm, ...), so that at any time they work on one
+// compact region and share the neighbour positions they gather in the SM's L1
+// (with one block per chunk, a launch longer than one wave hands each freed
+// slot the next chunk, so an SM's blocks lie anywhere in the resident region).
+// Each row carries its chunk index in w; a block's rows end in padding
+// (w = -1).  Returns the rows, cpb per block.
+static std::vector<int4> step_table(const std::vector<int4> &order, const std::vector<int4> &chunks, bool sweep,
+                                    int nsm, int per_sm, int &nblk_s, int &cpb)
+{
+    const int nb = (int)chunks.size();
+    if (!sweep || nsm < 1 || per_sm < 1) {
+        nblk_s = nb;
+        cpb = 1;
+        return order;
+    }
+    if ((int64_t)nsm * per_sm > nb) {           // fewer chunks than resident blocks: at most nb blocks
+        if (nb < nsm) {
+            nsm = nb;
+            per_sm = 1;
+        } else {
+            per_sm = nb / nsm;
+        }
+    }
+    const int resident = nsm * per_sm;           // <= nb, so the rows (< nb + resident) fit 2 nb
+    nblk_s = resident;
+    cpb = (nb + resident - 1) / resident;
+    std::vector<int4> rows((size_t)resident * cpb, make_int4(0, 0, 0, -1));
+    int base = 0;
+    for (int s = 0; s < nsm; ++s) {
+        const int ns = nb / nsm + (s < nb % nsm ? 1 : 0);   // chunks of SM s
+        for (int k = 0; k < per_sm; ++k) {
+            const int b = s + k * nsm;
+            for (int q = 0; q < cpb; ++q) {
+                const int c = q * per_sm + k;
+                if (c >= ns)
+                    break;
+                rows[(size_t)b * cpb + q] = chunks[base + c];
+                rows[(size_t)b * cpb + q].w = base + c;
+            }
+        }
+        base += ns;
+    }
+    return rows;
+}
+
 // Returns MD_OK or MD_E_INVAL with *msg set.
 int make_geometry(const md_params *p, int R, const int64_t *nrep, const double *box, Geometry &g,
                   std::string &msg)
@@ -192,7 +244,10 @@ int make_geometry(const md_params *p, int R, const int64_t *nrep, const double *
         msg = "threads_per_particle must be 0 or a power of two in [1, 32]";
         return MD_E_INVAL;
     }
-    if (p->reserved0 != 0) { msg = "reserved fields must be zero"; return MD_E_INVAL; }
+    if (p->step_form < 0 || p->step_form > 2) {
+        msg = "step_form must be 0 (automatic), 1 (one block per chunk) or 2 (resident blocks sweep)";
+        return MD_E_INVAL;
+    }
     if (p->build_form < 0 || p->build_form > 2) {
         msg = "build_form must be 0 (automatic), 1 (warp per cell) or 2 (block per cell)";
         return MD_E_INVAL;
@@ -244,6 +299,10 @@ int make_geometry(const md_params *p, int R, const int64_t *nrep, const double *
     // 64 registers), 4 for FP64 (measured on GB300)
     g.tpp = tpp ? tpp : (p->precision == MD_PREC_FP64 ? 4 : 2);
     g.ppb_f = kForceBlock / g.tpp;
+    if (p->step_form == 2 && (p->precision == MD_PREC_FP64 || g.tpp > 2)) {
+        msg = "step_form 2 needs MIXED or FP32 and 1 or 2 threads per particle";
+        return MD_E_INVAL;
+    }
     g.n = 0;
     g.rep.assign(R, mdk::Rep{});
     g.blk_i.clear();
@@ -358,6 +417,7 @@ Layout make_layout(const md_params *p, const Geometry &g)
     L.off_rep = take(sizeof(mdk::Rep) * g.R);
     L.off_blk_i = take(sizeof(int4) * g.nblk_i);
     L.off_blk_f = take(sizeof(int4) * g.nblk_f);
+    L.off_blk_s = take(sizeof(int4) * 2 * (size_t)g.nblk_f);   // < nblk_f + resident blocks rows
     L.off_crank = take(sizeof(int) * g.ncell);
     L.off_cxyz = take(sizeof(int4) * g.ncell);
     L.off_pa = take(pb * n);
@@ -466,6 +526,13 @@ int cuda_fail(md_handle *h, cudaError_t e, const char *what)
         if (e_ != cudaSuccess)                        \
             return cuda_fail((h), e_, #expr);         \
     } while (0)
+
+// The step kernel in use: lanes per particle, smoothing, and the block form.
+const void *step_kernel(const md_handle *h)
+{
+    const int sm = h->p.smooth_h > 0.0, li = force_index(h->g.tpp);
+    return h->g.sweep ? h->ks->step_sweep[sm][li] : h->ks->step[sm][li];
+}
 
 int launch(md_handle *h, const void *f, int grid, int block, const KArgs &a)
 {
@@ -663,7 +730,7 @@ int build_graph(md_handle *h)
     if ((rc = add_conditional(h, g, &n_while, n_if0, c_loop, cudaGraphCondTypeWhile, &wbody)))
         return rc;
     // loop body: kUnroll step kernels, a conditional rebuild after every g.check
-    const void *stepk = h->ks->step[h->p.smooth_h > 0.0][force_index(h->g.tpp)];
+    const void *stepk = step_kernel(h);
     cudaGraphNode_t prev = nullptr;
     for (int slot = 0; slot < kUnroll; ++slot) {
         KArgs sa = step_args(h, slot);
@@ -675,7 +742,7 @@ int build_graph(md_handle *h)
             sa.h_rebuild = c_reb;
         }
         cudaGraphNode_t n_s;
-        if ((rc = add_kernel(h, wbody, &n_s, prev ? &prev : nullptr, prev ? 1 : 0, stepk, h->g.nblk_f,
+        if ((rc = add_kernel(h, wbody, &n_s, prev ? &prev : nullptr, prev ? 1 : 0, stepk, h->g.nblk_s,
                              kForceBlock, sa)))
             return rc;
         prev = n_s;
@@ -944,6 +1011,8 @@ static int create_impl(md_handle *h, const md_params *p, const int32_t *species,
     a.nnbr = (int *)(w + L.off_nnbr);
     a.blk_i = (const int4 *)(w + L.off_blk_i);
     a.blk_f = (const int4 *)(w + L.off_blk_f);
+    a.blk_s = (const int4 *)(w + L.off_blk_s);
+    a.cpb = g.cpb;
     a.part_f = (double *)(w + L.off_part_f);
     a.part_i = (double *)(w + L.off_part_i);
     a.part_e = w + L.off_part_e;
@@ -1010,11 +1079,20 @@ static int create_impl(md_handle *h, const md_params *p, const int32_t *species,
     if (a.hdtm_hi[0] == 0.0f)
         return fail(h, MD_E_INVAL, "dt / (2 m) underflows single precision");
 
-    int dev = 0, nsm = 0, per_sm = 0, per_sm_nb = 0;
+    int dev = 0, nsm = 0, per_sm = 0, per_sm_sw = 0, per_sm_nb = 0;
     CK(h, cudaGetDevice(&dev));
     CK(h, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-              &per_sm, h->ks->step[h->p.smooth_h > 0.0][force_index(g.tpp)], kForceBlock, 0));
+    {
+        // step kernel: the sweeping form when asked for, or (automatic) when one block per chunk
+        // would need more blocks than the GPU holds at once
+        const int sm = h->p.smooth_h > 0.0, li = force_index(g.tpp);
+        const void *sweepk = li < 2 ? h->ks->step_sweep[sm][li] : nullptr;
+        CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, h->ks->step[sm][li], kForceBlock, 0));
+        if (sweepk)
+            CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_sw, sweepk, kForceBlock, 0));
+        h->g.sweep = sweepk && per_sm_sw > 0 &&
+                     (p->step_form == 2 || (p->step_form == 0 && (int64_t)g.nblk_f > (int64_t)nsm * per_sm_sw));
+    }
     // the build takes a warp per cell when the cells fill the GPU's warp slots that way
     CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_nb, h->ks->nbuild, kNbBlock, 0));
     h->g.nb_block = p->build_form == 2 ||
@@ -1025,7 +1103,7 @@ static int create_impl(md_handle *h, const md_params *p, const int32_t *species,
     CK(h, cudaEventCreate(&h->ev_f1));
     CK(h, cudaEventCreate(&h->ev_i1));
     CK(h, cudaEventRecord(h->ev_stage, h->s));
-    size_t tbytes = sizeof(mdk::Rep) * g.R + sizeof(int4) * (g.nblk_i + g.nblk_f) +
+    size_t tbytes = sizeof(mdk::Rep) * g.R + sizeof(int4) * (g.nblk_i + 3 * (size_t)g.nblk_f) +
                     sizeof(int) * g.ncell + sizeof(int4) * g.ncell;
     size_t sbytes = 64 * (size_t)g.n;
     if ((rc = ensure_pinned(h, std::max(tbytes, sbytes) + 4096)))
@@ -1040,9 +1118,12 @@ static int create_impl(md_handle *h, const md_params *p, const int32_t *species,
             return e == cudaSuccess ? MD_OK : cuda_fail(h, e, "table upload");
         };
         const std::vector<int4> bf = sm_block_order(g.blk_f, nsm, nsm * per_sm);
+        const std::vector<int4> bs = step_table(bf, g.blk_f, h->g.sweep, nsm, per_sm_sw, h->g.nblk_s, h->g.cpb);
+        h->a.cpb = h->g.cpb;
         if ((rc = put(L.off_rep, g.rep.data(), sizeof(mdk::Rep) * g.R)) ||
             (rc = put(L.off_blk_i, g.blk_i.data(), sizeof(int4) * g.nblk_i)) ||
             (rc = put(L.off_blk_f, bf.data(), sizeof(int4) * g.nblk_f)) ||
+            (rc = put(L.off_blk_s, bs.data(), sizeof(int4) * bs.size())) ||
             (rc = put(L.off_crank, g.crank.data(), sizeof(int) * g.ncell)) ||
             (rc = put(L.off_cxyz, g.cxyz.data(), sizeof(int4) * g.ncell)))
             return rc;
@@ -1115,13 +1196,13 @@ int md_step(md_handle *h, int64_t nsteps)
     if ((rc = launch(h, h->ks->integrate, h->g.nblk_i, kIntBlock, first_args(h))) ||
         (rc = rebuild_if_flagged(h, nullptr)))
         return rc;
-    const void *stepk = h->ks->step[h->p.smooth_h > 0.0][force_index(h->g.tpp)];
+    const void *stepk = step_kernel(h);
     const int64_t iters = (nsteps + kUnroll - 1) / kUnroll;
     for (int64_t it = 0; it < iters; ++it) {
         for (int slot = 0; slot < kUnroll; ++slot) {
             const KArgs sa = step_args(h, slot);
             CK(h, cudaEventRecord(h->ev_f0, h->s));
-            if ((rc = launch(h, stepk, h->g.nblk_f, kForceBlock, sa)))
+            if ((rc = launch(h, stepk, h->g.nblk_s, kForceBlock, sa)))
                 return rc;
             CK(h, cudaEventRecord(h->ev_f1, h->s));
             CK(h, cudaEventSynchronize(h->ev_f1));
@@ -1615,6 +1696,7 @@ int md_info(md_handle *h, md_info_t *out)
     out->neigh_capacity_max = h->g.Kmax;
     out->regrows = c.regrows;
     out->build_form = h->g.nb_block ? 2 : 1;
+    out->step_form = h->g.sweep ? 2 : 1;
     out->threads_per_particle = h->g.tpp;
     out->check_interval = h->g.check;
     out->cells_per_edge = h->g.rep[0].nc;

@@ -113,6 +113,9 @@ struct KArgs {
     int *nbr, *nnbr;
     const int4 *blk_i, *blk_f;        // per block: first particle, end, replica (blk_f: + its
                                       // chunk index, the slot of its partial sums)
+    const int4 *blk_s;                // step kernel: rows of blk_f in the order the resident blocks
+                                      // take them, cpb per block (w = -1: padding)
+    int cpb;                          // step kernel: chunks per block
     double *part_f, *part_i;          // per-block partial sums [nblk_f][12], [nblk_i][4]
     void *part_e;                     // per-block potential energy [nblk_f]: double (FP64 mode) or
                                       // float2 double-single (MIXED, FP32)
@@ -195,6 +198,8 @@ __device__ __forceinline__ ds ds_from_double(double x)
 // table of kernel entry addresses for one precision (one translation unit each)
 struct KernelSet {
     const void *integrate, *force[2][6], *step[2][6];   // [smoothed][log2 lanes per particle]
+    const void *step_sweep[2][2];     // step kernel, resident blocks sweeping runs of chunks
+                                      // (single-precision pair loops, 1 or 2 lanes; else null)
     const void *bin, *scan, *scatter, *permute, *nbuild, *nbuild_blk;
     const void *load, *getstate, *expforce, *scale, *set_steps, *reset, *mark_rebuild;
     const void *andersen, *andersen_fix, *snapshot, *epot_flush;

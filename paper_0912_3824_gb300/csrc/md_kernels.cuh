@@ -385,16 +385,16 @@ __device__ __forceinline__ void half_kick(const KArgs &a, PState<P> &s, FT<P> fx
         s.vx = ds_add(s.vx, ds_mul_f(hk, fx));
         s.vy = ds_add(s.vy, ds_mul_f(hk, fy));
         s.vz = ds_add(s.vz, ds_mul_f(hk, fz));
-    } else if constexpr (P == FP64) {
+    } else if constexpr (P == FP64) {       // (roundings spelled out: the same in every kernel)
         const double hk = a.hdtm[s.sp];
-        s.vx += hk * fx;
-        s.vy += hk * fy;
-        s.vz += hk * fz;
+        s.vx = fma(hk, fx, s.vx);
+        s.vy = fma(hk, fy, s.vy);
+        s.vz = fma(hk, fz, s.vz);
     } else {
         const float hk = a.hdtm_hi[s.sp];
-        s.vx += hk * fx;
-        s.vy += hk * fy;
-        s.vz += hk * fz;
+        s.vx = fmaf(hk, fx, s.vx);
+        s.vy = fmaf(hk, fy, s.vy);
+        s.vz = fmaf(hk, fz, s.vz);
     }
 }
 
@@ -409,18 +409,27 @@ __device__ __forceinline__ void kinetic(const KArgs &a, const PState<P> &s, doub
         vx = s.vx; vy = s.vy; vz = s.vz;
     }
     const double m = a.mass[s.sp];
-    kin[0] = 0.5 * m * (vx * vx + vy * vy + vz * vz);
+    kin[0] = __dmul_rn(0.5 * m, fma(vz, vz, fma(vy, vy, __dmul_rn(vx, vx))));
     kin[1] = m * vx;
     kin[2] = m * vy;
     kin[3] = m * vz;
 }
 
-__device__ __forceinline__ float speed2(const PState<MIXED> &s)
+// |v|^2 and |d|^2 feed the rebuild decision, which sets the particle order and
+// so the summation order: their roundings are spelled out, so that every
+// kernel that computes them decides alike.
+__device__ __forceinline__ float norm2f(float x, float y, float z)
 {
-    return s.vx.hi * s.vx.hi + s.vy.hi * s.vy.hi + s.vz.hi * s.vz.hi;
+    return fmaf(z, z, fmaf(y, y, __fmul_rn(x, x)));
 }
-__device__ __forceinline__ float speed2(const PState<FP64> &s) { return (float)(s.vx * s.vx + s.vy * s.vy + s.vz * s.vz); }
-__device__ __forceinline__ float speed2(const PState<FP32> &s) { return s.vx * s.vx + s.vy * s.vy + s.vz * s.vz; }
+__device__ __forceinline__ float norm2(float x, float y, float z) { return norm2f(x, y, z); }
+__device__ __forceinline__ float norm2(double x, double y, double z)
+{
+    return (float)fma(z, z, fma(y, y, __dmul_rn(x, x)));
+}
+__device__ __forceinline__ float speed2(const PState<MIXED> &s) { return norm2f(s.vx.hi, s.vy.hi, s.vz.hi); }
+__device__ __forceinline__ float speed2(const PState<FP64> &s) { return norm2(s.vx, s.vy, s.vz); }
+__device__ __forceinline__ float speed2(const PState<FP32> &s) { return norm2f(s.vx, s.vy, s.vz); }
 
 // r += dt v, wrapped into [0, L) with image counting; writes the new position
 // into buffer `dst`, updates the image counter in the state buffers `spar`,
@@ -453,13 +462,13 @@ __device__ __forceinline__ float drift(const KArgs &a, const Rep &rp, PState<P> 
         const float ex = __fadd_rn(sep_f(s.H.x, rr.x, rp.Lhi, rp.invLf), s.l.x);
         const float ey = __fadd_rn(sep_f(s.H.y, rr.y, rp.Lhi, rp.invLf), s.l.y);
         const float ez = __fadd_rn(sep_f(s.H.z, rr.z, rp.Lhi, rp.invLf), s.l.z);
-        dd = ex * ex + ey * ey + ez * ez;
+        dd = norm2f(ex, ey, ez);
     } else if constexpr (P == FP64) {
-        const double sx = a.dt * s.vx, sy = a.dt * s.vy, sz = a.dt * s.vz;
+        const double sx = __dmul_rn(a.dt, s.vx), sy = __dmul_rn(a.dt, s.vy), sz = __dmul_rn(a.dt, s.vz);
         const double lim = 0.25 * rp.L;
         if (fabs(sx) > lim || fabs(sy) > lim || fabs(sz) > lim)
             bad |= ST_UNSTABLE;
-        double x = s.x.x + sx, y = s.x.y + sy, z = s.x.z + sz;
+        double x = __dadd_rn(s.x.x, sx), y = __dadd_rn(s.x.y, sy), z = __dadd_rn(s.x.z, sz);
         ix = iy = iz = 0;
         if (x >= rp.L) { x -= rp.L; ix = 1; } else if (x < 0.0) { x += rp.L; ix = -1; }
         if (y >= rp.L) { y -= rp.L; iy = 1; } else if (y < 0.0) { y += rp.L; iy = -1; }
@@ -472,14 +481,14 @@ __device__ __forceinline__ float drift(const KArgs &a, const Rep &rp, PState<P> 
         const float ex = sep_f(__double2float_rn(x), rr.x, rp.Lhi, rp.invLf);
         const float ey = sep_f(__double2float_rn(y), rr.y, rp.Lhi, rp.invLf);
         const float ez = sep_f(__double2float_rn(z), rr.z, rp.Lhi, rp.invLf);
-        dd = ex * ex + ey * ey + ez * ez;
+        dd = norm2f(ex, ey, ez);
     } else {
         const float dt = a.dt_hi;
-        const float sx = dt * s.vx, sy = dt * s.vy, sz = dt * s.vz;
+        const float sx = __fmul_rn(dt, s.vx), sy = __fmul_rn(dt, s.vy), sz = __fmul_rn(dt, s.vz);
         const float L = rp.Lhi;
         if (fabsf(sx) > 0.25f * L || fabsf(sy) > 0.25f * L || fabsf(sz) > 0.25f * L)
             bad |= ST_UNSTABLE;
-        float x = s.x.x + sx, y = s.x.y + sy, z = s.x.z + sz;
+        float x = __fadd_rn(s.x.x, sx), y = __fadd_rn(s.x.y, sy), z = __fadd_rn(s.x.z, sz);
         ix = iy = iz = 0;
         if (x >= L) { x -= L; ix = 1; } else if (x < 0.f) { x += L; ix = -1; }
         if (y >= L) { y -= L; iy = 1; } else if (y < 0.f) { y += L; iy = -1; }
@@ -497,7 +506,7 @@ __device__ __forceinline__ float drift(const KArgs &a, const Rep &rp, PState<P> 
         const float ex = sep_f(x, rr.x, L, rp.invLf);
         const float ey = sep_f(y, rr.y, L, rp.invLf);
         const float ez = sep_f(z, rr.z, L, rp.invLf);
-        dd = ex * ex + ey * ey + ez * ez;
+        dd = norm2f(ex, ey, ez);
     }
     if (ix | iy | iz) {
         int4 *im = img_of(a, spar);
@@ -1188,18 +1197,18 @@ __device__ __forceinline__ void component_update(const KArgs &a, const Rep &rp, 
         vh = v.hi;
         vl = v.lo;
     } else if constexpr (P == FP64) {
-        const double hk = a.hdtm[sp];
-        double v = vd + hk * f_cd;
+        const double hk = a.hdtm[sp];            // (roundings spelled out, as in half_kick / drift)
+        double v = fma(hk, f_cd, vd);
         if (sample) {
             ke = 0.5 * a.mass[sp] * v * v;
             pc = a.mass[sp] * v;
         }
         if (!last) {
-            v += hk * f_cd;
-            const double s = a.dt * v;
+            v = fma(hk, f_cd, v);
+            const double s = __dmul_rn(a.dt, v);
             if (fabs(s) > 0.25 * rp.L)
                 bad |= ST_UNSTABLE;
-            double x = ((const double *)pos_a(a, pp))[e] + s;
+            double x = __dadd_rn(((const double *)pos_a(a, pp))[e], s);
             int dimg = 0;
             if (x >= rp.L) { x -= rp.L; dimg = 1; } else if (x < 0.0) { x += rp.L; dimg = -1; }
             if (!isfinite(x))
@@ -1214,18 +1223,18 @@ __device__ __forceinline__ void component_update(const KArgs &a, const Rep &rp, 
         vd = v;
     } else {
         const float hk = a.hdtm_hi[sp];
-        float v = vh + hk * f_c;
+        float v = fmaf(hk, f_c, vh);
         if (sample) {
             ke = 0.5 * a.mass[sp] * (double)v * (double)v;
             pc = a.mass[sp] * (double)v;
         }
         if (!last) {
-            v += hk * f_c;
-            const float s = a.dt_hi * v;
+            v = fmaf(hk, f_c, v);
+            const float s = __fmul_rn(a.dt_hi, v);
             const float L = rp.Lhi;
             if (fabsf(s) > 0.25f * L)
                 bad |= ST_UNSTABLE;
-            float x = ((const float *)pos_a(a, pp))[e] + s;
+            float x = __fadd_rn(((const float *)pos_a(a, pp))[e], s);
             int dimg = 0;
             if (x >= L) { x -= L; dimg = 1; } else if (x < 0.f) { x += L; dimg = -1; }
             if (x >= L) { x = 0.f; dimg += 1; }
@@ -1249,12 +1258,12 @@ __device__ __forceinline__ void component_update(const KArgs &a, const Rep &rp, 
 // position buffer.  The operands of the update are loaded before the
 // neighbour loop so that their latency is hidden.
 template <int P, int TPP, bool SAMPLE, bool SM>
-__device__ __forceinline__ void step_body_split(const KArgs &a, bool active, bool last, int pp, int spar,
-                                                double *part, ET<P> &eo, float &d2, float &v2, float &a2,
+__device__ __forceinline__ void step_body_split(const KArgs &a, const int4 *tab, int row, bool active, bool last,
+                                                int pp, int spar, double *part, ET<P> &eo, float &d2, float &v2, float &a2,
                                                 unsigned int &bad)
 {
     constexpr int NC = TPP >= 4 ? 1 : 4 / TPP;
-    const int4 b = a.blk_f[blockIdx.x];
+    const int4 b = tab[row];
     const Rep rp = a.rep[b.z];
     const int lane = threadIdx.x & (TPP - 1);
     const int i = b.x + (int)(threadIdx.x / TPP);
@@ -1366,21 +1375,20 @@ __device__ __forceinline__ void step_body_split(const KArgs &a, bool active, boo
         d2 = dd;
         v2 = vv;
         const float im = a.inv_mass[sp];
-        const float f2 = (float)(fx * fx + fy * fy + fz * fz);
-        a2 = f2 * im * im;
+        a2 = __fmul_rn(__fmul_rn(norm2(fx, fy, fz), im), im);
     }
 }
 
 template <int P, int TPP, bool SAMPLE, bool SM>
-__device__ __forceinline__ void step_body(const KArgs &a, bool active, bool last, int pp, int spar,
-                                          double *part, ET<P> &eo, float &d2, float &v2, float &a2,
+__device__ __forceinline__ void step_body(const KArgs &a, const int4 *tab, int row, bool active, bool last,
+                                          int pp, int spar, double *part, ET<P> &eo, float &d2, float &v2, float &a2,
                                           unsigned int &bad)
 {
     if constexpr (kSplitUpdate || TPP >= 4) {
-        step_body_split<P, TPP, SAMPLE, SM>(a, active, last, pp, spar, part, eo, d2, v2, a2, bad);
+        step_body_split<P, TPP, SAMPLE, SM>(a, tab, row, active, last, pp, spar, part, eo, d2, v2, a2, bad);
         return;
     }
-    const int4 b = a.blk_f[blockIdx.x];
+    const int4 b = tab[row];
     const Rep rp = a.rep[b.z];
     const int lane = threadIdx.x & (TPP - 1);
     const int i = b.x + (int)(threadIdx.x / TPP);
@@ -1415,8 +1423,7 @@ __device__ __forceinline__ void step_body(const KArgs &a, bool active, bool last
         d2 = drift<P>(a, rp, s, pp ^ 1, spar, i, bad);
         v2 = speed2(s);
         const float im = a.inv_mass[s.sp];
-        const float f2 = (float)(fx * fx + fy * fy + fz * fz);
-        a2 = f2 * im * im;
+        a2 = __fmul_rn(__fmul_rn(norm2(fx, fy, fz), im), im);
     }
     store_vel<P>(a, spar, i, s);
 }
@@ -1427,7 +1434,7 @@ __device__ __forceinline__ void step_body(const KArgs &a, bool active, bool last
 // kernels keep the compiler's own register choice (they would spill).
 template <int P, bool SM> constexpr int step_min_blocks() { return (P != FP64 && !SM) ? 7 : 0; }
 
-template <int P, int TPP, bool SM>
+template <int P, int TPP, bool SM, bool SWEEP>
 __global__ void __launch_bounds__(kForceBlock, step_min_blocks<P, SM>()) k_step(KArgs a)
 {
     __shared__ double sh[32 * kPartF];
@@ -1450,39 +1457,90 @@ __global__ void __launch_bounds__(kForceBlock, step_min_blocks<P, SM>()) k_step(
     if (threadIdx.x == 0)                       // device timing of this launch: earliest start
         atomicMax(&ctl->t_first_inv, ~global_ns());
 
-    double part[kPartF];
-    ET<P> eo;
-    float d2 = 0.f, v2 = 0.f, a2 = 0.f;
-    unsigned int bad = 0u;
-    if (sample)
-        step_body<P, TPP, true, SM>(a, active, last, pp, spar, part, eo, d2, v2, a2, bad);
-    else
-        step_body<P, TPP, false, SM>(a, active, last, pp, spar, part, eo, d2, v2, a2, bad);
-    if (bad)
-        atomicOr(&ctl->status, bad);
-
-    // This step's potential energy, every step: one partial per warp (written
-    // only by active launches, so that an idle one never overwrites partials
-    // that still await their sum; the shuffles run in every lane regardless).
-    // Block sums of the maxima every step, of the other reductions on sample
-    // steps (their component 0 stays unused).
-    store_warp_energy<P>(a, step, a.blk_f[blockIdx.x].w, eo, active);
-    block_max3(d2, v2, a2, shf);
-    if (sample)
-        block_sum<kPartF>(part, sh);
-    if (threadIdx.x == 0) {
-        const size_t pb = (size_t)a.blk_f[blockIdx.x].w * kPartF;
-        if (sample) {
+    if constexpr (SWEEP) {
+        // The block sweeps its run of chunks: rows blockIdx.x * cpb ... of the
+        // step table.  Per chunk: this step's potential energy, one partial per
+        // warp (written only by active launches, so that an idle one never
+        // overwrites partials that still await their sum; the shuffles run in
+        // every lane regardless); block maxima into the launch's maxima every
+        // step; the chunk's other reductions on sample steps (component 0 stays
+        // unused).
+        for (int q = 0; q < a.cpb; ++q) {
+            const int row = blockIdx.x * a.cpb + q;
+            const int chunk = a.blk_s[row].w;
+            if (chunk < 0)                       // (padding rows: the same for the whole block)
+                break;
+            double part[kPartF];
+            ET<P> eo;
+            float d2 = 0.f, v2 = 0.f, a2 = 0.f;
+            unsigned int bad = 0u;
+            if (sample)
+                step_body<P, TPP, true, SM>(a, a.blk_s, row, active, last, pp, spar, part, eo, d2, v2, a2,
+                                            bad);
+            else
+                step_body<P, TPP, false, SM>(a, a.blk_s, row, active, last, pp, spar, part, eo, d2, v2, a2,
+                                             bad);
+            if (bad)
+                atomicOr(&ctl->status, bad);
+            store_warp_energy<P>(a, step, chunk, eo, active);
+            block_max3(d2, v2, a2, shf);
+            if (sample)
+                block_sum<kPartF>(part, sh);
+            if (threadIdx.x == 0) {
+                if (sample) {
+                    const size_t pb = (size_t)chunk * kPartF;
 #pragma unroll
-            for (int k = 1; k < kPartF; ++k)
-                a.part_f[pb + k] = part[k];
+                    for (int k = 1; k < kPartF; ++k)
+                        a.part_f[pb + k] = part[k];
+                }
+                if (d2 > 0.f)
+                    atomicMax(&ctl->maxdisp2, __float_as_uint(d2));
+                if (v2 > 0.f)
+                    atomicMax(&ctl->maxv2, __float_as_uint(v2));
+                if (a2 > 0.f)
+                    atomicMax(&ctl->maxa2, __float_as_uint(a2));
+            }
+            __syncthreads();                     // (shf and sh serve the next chunk)
         }
-        if (d2 > 0.f)
-            atomicMax(&ctl->maxdisp2, __float_as_uint(d2));
-        if (v2 > 0.f)
-            atomicMax(&ctl->maxv2, __float_as_uint(v2));
-        if (a2 > 0.f)
-            atomicMax(&ctl->maxa2, __float_as_uint(a2));
+    } else {
+        // One chunk per block: the block's row of the force kernel's table.
+        // This step's potential energy, every step: one partial per warp
+        // (written only by active launches, so that an idle one never
+        // overwrites partials that still await their sum; the shuffles run in
+        // every lane regardless).  Block sums of the maxima every step, of the
+        // other reductions on sample steps (their component 0 stays unused).
+        double part[kPartF];
+        ET<P> eo;
+        float d2 = 0.f, v2 = 0.f, a2 = 0.f;
+        unsigned int bad = 0u;
+        if (sample)
+            step_body<P, TPP, true, SM>(a, a.blk_f, blockIdx.x, active, last, pp, spar, part, eo, d2, v2, a2,
+                                        bad);
+        else
+            step_body<P, TPP, false, SM>(a, a.blk_f, blockIdx.x, active, last, pp, spar, part, eo, d2, v2, a2,
+                                         bad);
+        if (bad)
+            atomicOr(&ctl->status, bad);
+        store_warp_energy<P>(a, step, a.blk_f[blockIdx.x].w, eo, active);
+        block_max3(d2, v2, a2, shf);
+        if (sample)
+            block_sum<kPartF>(part, sh);
+        if (threadIdx.x == 0) {
+            const size_t pb = (size_t)a.blk_f[blockIdx.x].w * kPartF;
+            if (sample) {
+#pragma unroll
+                for (int k = 1; k < kPartF; ++k)
+                    a.part_f[pb + k] = part[k];
+            }
+            if (d2 > 0.f)
+                atomicMax(&ctl->maxdisp2, __float_as_uint(d2));
+            if (v2 > 0.f)
+                atomicMax(&ctl->maxv2, __float_as_uint(v2));
+            if (a2 > 0.f)
+                atomicMax(&ctl->maxa2, __float_as_uint(a2));
+        }
+    }
+    if (threadIdx.x == 0) {
         __threadfence();
         const unsigned int t = atomicAdd(&ctl->ticket, 1u);
         s_first = (t == 0);
@@ -1603,8 +1661,7 @@ __global__ void __launch_bounds__(kIntBlock) k_integrate(KArgs a)
             d2 = drift<P>(a, rp, s, pp ^ 1, spar, i, bad);
             v2 = speed2(s);
             const float im = a.inv_mass[s.sp];
-            const float f2 = (float)(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
-            a2 = f2 * im * im;
+            a2 = __fmul_rn(__fmul_rn(norm2(f[0], f[1], f[2]), im), im);
             store_vel<P>(a, spar, i, s);
         }
     }
@@ -2744,12 +2801,12 @@ KernelSet make_kernel_set()
     k.force[0][3] = (const void *)k_force<P, 8, false>;
     k.force[0][4] = (const void *)k_force<P, 16, false>;
     k.force[0][5] = (const void *)k_force<P, 32, false>;
-    k.step[0][0] = (const void *)k_step<P, 1, false>;
-    k.step[0][1] = (const void *)k_step<P, 2, false>;
-    k.step[0][2] = (const void *)k_step<P, 4, false>;
-    k.step[0][3] = (const void *)k_step<P, 8, false>;
-    k.step[0][4] = (const void *)k_step<P, 16, false>;
-    k.step[0][5] = (const void *)k_step<P, 32, false>;
+    k.step[0][0] = (const void *)k_step<P, 1, false, false>;
+    k.step[0][1] = (const void *)k_step<P, 2, false, false>;
+    k.step[0][2] = (const void *)k_step<P, 4, false, false>;
+    k.step[0][3] = (const void *)k_step<P, 8, false, false>;
+    k.step[0][4] = (const void *)k_step<P, 16, false, false>;
+    k.step[0][5] = (const void *)k_step<P, 32, false, false>;
     // smoothed potential (Sec. 4): the common lane counts only
     k.force[1][0] = (const void *)k_force<P, 1, true>;
     k.force[1][1] = (const void *)k_force<P, 2, true>;
@@ -2757,12 +2814,23 @@ KernelSet make_kernel_set()
     k.force[1][3] = (const void *)k_force<P, 8, true>;
     k.force[1][4] = nullptr;
     k.force[1][5] = nullptr;
-    k.step[1][0] = (const void *)k_step<P, 1, true>;
-    k.step[1][1] = (const void *)k_step<P, 2, true>;
-    k.step[1][2] = (const void *)k_step<P, 4, true>;
-    k.step[1][3] = (const void *)k_step<P, 8, true>;
+    k.step[1][0] = (const void *)k_step<P, 1, true, false>;
+    k.step[1][1] = (const void *)k_step<P, 2, true, false>;
+    k.step[1][2] = (const void *)k_step<P, 4, true, false>;
+    k.step[1][3] = (const void *)k_step<P, 8, true, false>;
     k.step[1][4] = nullptr;
     k.step[1][5] = nullptr;
+    // resident blocks sweeping runs of chunks: single-precision pair loops at 1 and 2 lanes
+    // (at 4 lanes the chunk loop costs registers and was measured slower)
+    for (int m = 0; m < 2; ++m)
+        for (int l = 0; l < 2; ++l)
+            k.step_sweep[m][l] = nullptr;
+    if constexpr (P != FP64) {
+        k.step_sweep[0][0] = (const void *)k_step<P, 1, false, true>;
+        k.step_sweep[0][1] = (const void *)k_step<P, 2, false, true>;
+        k.step_sweep[1][0] = (const void *)k_step<P, 1, true, true>;
+        k.step_sweep[1][1] = (const void *)k_step<P, 2, true, true>;
+    }
     k.bin = (const void *)k_bin<P>;
     k.scan = (const void *)k_scan<P>;
     k.scatter = (const void *)k_scatter<P>;

@@ -35,7 +35,7 @@ class md_params(C.Structure):
                 ("precision", C.c_int32), ("neigh_capacity", C.c_int32),
                 ("sample_interval", C.c_int32), ("obs_capacity", C.c_int32),
                 ("threads_per_particle", C.c_int32), ("use_graph", C.c_int32),
-                ("reorder", C.c_int32), ("reserved0", C.c_int32), ("smooth_h", C.c_double),
+                ("reorder", C.c_int32), ("step_form", C.c_int32), ("smooth_h", C.c_double),
                 ("check_interval", C.c_int32), ("neigh_capacity_max", C.c_int32),
                 ("step_budget", C.c_int32), ("build_form", C.c_int32)]
 
@@ -55,7 +55,7 @@ class md_info_t(C.Structure):
                 ("rebuild_ms", C.c_double), ("rebuild_checks", C.c_int64),
                 ("step_device_ms", C.c_double), ("step_device_launches", C.c_int64),
                 ("check_interval", C.c_int32), ("neigh_capacity_max", C.c_int32),
-                ("regrows", C.c_int64), ("build_form", C.c_int32), ("reserved", C.c_int32)]
+                ("regrows", C.c_int64), ("build_form", C.c_int32), ("step_form", C.c_int32)]
 
 
 OBS_DTYPE = np.dtype([("step", np.int64), ("e_pot", np.float64), ("e_kin", np.float64),
@@ -316,7 +316,7 @@ def make_params(pot: dict, dt: float, skin: float = 0.3, precision: int = MD_PRE
                 sample_interval: int = 100, neigh_capacity: int = 0, threads_per_particle: int = 0,
                 use_graph: bool = True, reorder: int = 1, obs_capacity: int = 0,
                 check_interval: int = 0, neigh_capacity_max: int = 0, step_budget: int = 0,
-                build_form: int = 0) -> md_params:
+                build_form: int = 0, step_form: int = 0) -> md_params:
     p = md_params_default()
     p.n_species = int(pot["n_species"])
     p.shift = 1 if pot.get("shift", True) else 0
@@ -340,6 +340,7 @@ def make_params(pot: dict, dt: float, skin: float = 0.3, precision: int = MD_PRE
     p.neigh_capacity_max = int(neigh_capacity_max)   # 0: twice the starting capacity
     p.step_budget = int(step_budget)         # 0: automatic bound of md_step's device loop
     p.build_form = int(build_form)           # 0 automatic, 1 warp per cell, 2 block per cell
+    p.step_form = int(step_form)             # 0 automatic, 1 block per chunk, 2 resident blocks sweep
     return p
 
 

@@ -95,7 +95,8 @@ def test_workspace_holds_the_capacity_cap(md):
 
 
 @pytest.mark.parametrize("bad", ["box", "dt", "species", "tpp", "sample", "asym", "smooth", "smooth_tpp",
-                                 "check3", "check32", "capmax", "capneg", "budget", "reserved", "form"])
+                                 "check3", "check32", "capmax", "capneg", "budget", "stepform", "sweep64", "sweep4",
+                                 "form"])
 def test_argument_checks(md, bad):
     from paper_0912_3824_gb300 import synth
     pot = synth.ka_params()
@@ -127,8 +128,14 @@ def test_argument_checks(md, bad):
         p.neigh_capacity = -8
     if bad == "budget":
         p.step_budget = -1
-    if bad == "reserved":
-        p.reserved0 = 1
+    if bad == "stepform":
+        p.step_form = 3
+    if bad == "sweep64":                 # the sweeping step kernel exists for the FP32 pair loops
+        p.precision = md.MD_PREC_FP64
+        p.step_form = 2
+    if bad == "sweep4":                  # ... at 1 or 2 lanes per particle
+        p.threads_per_particle = 4
+        p.step_form = 2
     if bad == "form":
         p.build_form = 3
     with pytest.raises(md.MDError) as ei:

@@ -292,6 +292,54 @@ def test_build_forms_give_the_same_lists_and_trajectory(md, prec, kind, n):
     assert np.array_equal(p1, p2) and np.array_equal(v1, v2) and np.array_equal(i1, i2)
 
 
+@pytest.mark.parametrize("prec", ["mixed", "fp32"])
+@pytest.mark.parametrize("kind,n,tpp,smooth", [("lj", 262144, 1, 0.0), ("ka", 4000, 2, 0.0), ("ka", 4000, 2, 0.005),
+                                               ("lj", 300, 1, 0.0)])
+def test_step_forms_give_the_same_trajectory(md, prec, kind, n, tpp, smooth):
+    """The step kernel with one block per chunk and with the resident blocks
+    sweeping runs of chunks compute every particle and every chunk's partial
+    sums the same way: equal positions, velocities, images, samples and
+    per-step energies after 150 steps with rebuilds, bit for bit.  LJ at
+    N = 262,144 and 1 lane needs more blocks than are resident (the automatic
+    choice is the sweep); the small systems force it on fewer chunks than
+    resident blocks (N = 300: fewer chunks than SMs)."""
+    s = _system(kind, n, amp=0.02)
+    if smooth:
+        s.params["smooth"] = smooth
+    runs = []
+    for form in (1, 2):
+        sim = _sim(md, s, prec, dt=0.005 if kind == "lj" else 0.002, step_form=form, threads_per_particle=tpp,
+                   sample_interval=10)
+        assert sim.info()["step_form"] == form
+        sim.step(150)
+        assert sim.sync() == md.MD_OK
+        info = sim.info()
+        pos, vel, img = sim.get_state()
+        st, e = sim.epot_series()
+        runs.append((pos, vel, img, sim.observables(), st, e, info["rebuilds"]))
+        sim.close()
+    (p1, v1, i1, o1, s1, e1, r1), (p2, v2, i2, o2, s2, e2, r2) = runs
+    assert r1 == r2 and r1 >= 2
+    assert np.array_equal(p1, p2) and np.array_equal(v1, v2) and np.array_equal(i1, i2)
+    assert np.array_equal(o1, o2)
+    assert np.array_equal(s1, s2) and np.array_equal(e1, e2) and len(s1) == 151
+    if n == 262144:
+        auto = _sim(md, s, prec, dt=0.005, threads_per_particle=tpp)
+        assert auto.info()["step_form"] == 2
+        auto.close()
+
+
+def test_step_form_two_needs_a_single_precision_pair_loop(md):
+    s = _system("ka", 1000)
+    for prec, tpp in (("fp64", 4), ("mixed", 4)):
+        with pytest.raises(md.MDError) as ei:
+            _sim(md, s, prec, step_form=2, threads_per_particle=tpp)
+        assert ei.value.code == md.MD_E_INVAL
+    sim = _sim(md, s, "fp64")
+    assert sim.info()["step_form"] == 1
+    sim.close()
+
+
 def test_epot_series_with_many_replicas(md):
     """More than 8 replicas (each replica summed by one thread): every
     replica's per-step potential energy equals that of the same system run

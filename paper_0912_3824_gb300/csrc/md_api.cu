@@ -337,6 +337,7 @@ int make_geometry(const md_params *p, int R, const int64_t *nrep, const double *
         q.invLf = (float)(1.0 / L);
         q.cscalef = (float)(nc / L);
         q.qunit = (float)(L / 4294967296.0);
+        q.qscale = (float)(4294967296.0 / L);
         // anchoring grid: smallest power of two with 2L < 2^24 * grid
         int e = (int)std::ceil(std::log2(2.0 * L)) - 24;
         double grid = std::ldexp(1.0, e);
@@ -344,6 +345,9 @@ int make_geometry(const md_params *p, int R, const int64_t *nrep, const double *
             grid *= 2.0;
         q.grid = (float)grid;
         q.inv_grid = (float)(1.0 / grid);
+        // grid * 2^32 / L lies in (2^9, 2^10]: times 2^28 it fits 38 bits, and times the
+        // anchored high word's grid index (< 2^24) 62 bits
+        q.qgrid = (unsigned long long)std::llround(grid * 4294967296.0 / L * 268435456.0);
         if (p->precision == MD_PREC_MIXED) {
             const double lh = std::rint(L / grid) * grid;
             q.Lhi = (float)lh;

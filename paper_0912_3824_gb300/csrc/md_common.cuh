@@ -68,7 +68,8 @@ struct Rep {                  // one independent system
     float Lhi, Llo, invLf, cscalef;
     float grid, inv_grid;     // anchoring grid of MIXED positions (powers of two)
     float qunit;              // L / 2^32: length of one unit of the fixed-point positions
-    float pad;
+    float qscale;             // 2^32 / L (single precision): units per length
+    unsigned long long qgrid; // grid * 2^32 / L in units of 2^-28: units per grid step, fixed point
     double mtot;              // total mass of the replica
 };
 

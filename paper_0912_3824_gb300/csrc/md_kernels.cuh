@@ -251,10 +251,19 @@ __device__ __forceinline__ double sep_d(double xi, double xj, double L, double i
 // the full 32-bit circle, so the 32-bit wrapped difference of two coordinates
 // is the minimum-image separation, exact in integers; only its conversion to
 // single precision rounds.  One unit is L / 2^32 (8.8e-9 sigma at L = 38).
-__device__ __forceinline__ unsigned int fixq(float H, float l, double invL)
+//
+// Without FP64 (whose pipe is narrow on this GPU): the high word is an
+// integer number m of grid steps (0 <= m < 2^24, exact), so x 2^32 / L =
+// m C + l 2^32 / L with C = grid 2^32 / L in (2^9, 2^10].  m C is formed in
+// 64-bit integers from C in units of 2^-28 (error < 2^-5 units) and rounded;
+// |l| <= grid, so l 2^32 / L (at most C, single precision, error < 2^-13
+// units) is rounded on its own.  The result is within 1 + 2^-5 units of the
+// exact value (two roundings), the same in every kernel.
+__device__ __forceinline__ unsigned int fixq(float H, float l, const Rep &rp)
 {
-    const double x = (double)H + (double)l;
-    return (unsigned int)(unsigned long long)__double2ll_rn(x * invL * 4294967296.0);
+    const unsigned int m = (unsigned int)__float2int_rn(__fmul_rn(H, rp.inv_grid));   // exact
+    const unsigned long long hi = ((unsigned long long)m * rp.qgrid + (1ull << 27)) >> 28;
+    return (unsigned int)hi + (unsigned int)__float2int_rn(__fmul_rn(l, rp.qscale));
 }
 
 __device__ __forceinline__ float sep_q(unsigned int qi, unsigned int qj, float unit)
@@ -456,8 +465,8 @@ __device__ __forceinline__ float drift(const KArgs &a, const Rep &rp, PState<P> 
             bad |= ST_NONFINITE;
         ((float4 *)pos_a(a, dst))[i] = s.H;
         ((float4 *)pos_b(a, dst))[i] = s.l;
-        q_of(a, dst)[i] = make_int4((int)fixq(s.H.x, s.l.x, rp.invL), (int)fixq(s.H.y, s.l.y, rp.invL),
-                                    (int)fixq(s.H.z, s.l.z, rp.invL), s.sp);
+        q_of(a, dst)[i] = make_int4((int)fixq(s.H.x, s.l.x, rp), (int)fixq(s.H.y, s.l.y, rp),
+                                    (int)fixq(s.H.z, s.l.z, rp), s.sp);
         const float4 rr = a.rref[i];
         const float ex = __fadd_rn(sep_f(s.H.x, rr.x, rp.Lhi, rp.invLf), s.l.x);
         const float ey = __fadd_rn(sep_f(s.H.y, rr.y, rp.Lhi, rp.invLf), s.l.y);
@@ -1187,7 +1196,7 @@ __device__ __forceinline__ void component_update(const KArgs &a, const Rep &rp, 
                 bad |= ST_NONFINITE;
             ((float *)pos_a(a, pp ^ 1))[e] = Hn;
             ((float *)pos_b(a, pp ^ 1))[e] = ln;
-            ((unsigned int *)q_of(a, pp ^ 1))[e] = fixq(Hn, ln, rp.invL);
+            ((unsigned int *)q_of(a, pp ^ 1))[e] = fixq(Hn, ln, rp);
             const float dx = __fadd_rn(sep_f(Hn, rr, rp.Lhi, rp.invLf), ln);
             dd = dx * dx;
             vv = v.hi * v.hi;
@@ -2482,8 +2491,8 @@ __global__ void __launch_bounds__(kIntBlock) k_load(KArgs a)
         }
         ((float4 *)pos_a(a, pp))[i] = make_float4(H[0], H[1], H[2], __int_as_float(sp));
         ((float4 *)pos_b(a, pp))[i] = make_float4(l[0], l[1], l[2], 0.f);
-        q_of(a, pp)[i] = make_int4((int)fixq(H[0], l[0], rp.invL), (int)fixq(H[1], l[1], rp.invL),
-                                   (int)fixq(H[2], l[2], rp.invL), sp);
+        q_of(a, pp)[i] = make_int4((int)fixq(H[0], l[0], rp), (int)fixq(H[1], l[1], rp),
+                                   (int)fixq(H[2], l[2], rp), sp);
         ds vx = ds_from_double(vv[0]), vy = ds_from_double(vv[1]), vz = ds_from_double(vv[2]);
         ((float4 *)vel_a(a, spar))[i] = make_float4(vx.hi, vy.hi, vz.hi, 0.f);
         ((float4 *)vel_b(a, spar))[i] = make_float4(vx.lo, vy.lo, vz.lo, 0.f);

@@ -168,6 +168,10 @@ def measured_peaks():
 # (38 per pair).  This is the convention the roofline's `achieved` uses.
 FLOP_PER_ENTRY_METHOD = 26
 FLOP_PER_PAIR_METHOD = 38
+# The plain (FP64 or FP32) count of the same method: separation 20 per entry,
+# force, energy and virial 20 per pair, no compensation.
+FLOP_PER_ENTRY_PLAIN = 20
+FLOP_PER_PAIR_PLAIN = 20
 # The same work counted as this kernel does it (reported beside): separation
 # from the 32-bit fixed-point positions 3 x (integer difference, conversion,
 # scale) = 9, r^2 = 5, cutoff test = 1; inside the cutoff: reciprocal 1,
@@ -606,7 +610,12 @@ def lj_cases(args, local, cases, workload, temperature, dt, skin):
         k_ms = (info1["step_device_ms"] - info0["step_device_ms"]) / max(1, n_dev)
         n_list, n_cut = list_statistics(sim, s.params)
         t_step = ms * 1e-3 / (args.inner * args.steps)
-        flops = (FLOP_PER_ENTRY_METHOD * n_list + FLOP_PER_PAIR_METHOD * n_cut) * n
+        # the method's count and the peak of the precision the pair loop runs in
+        if args.precision == "mixed":
+            flops = (FLOP_PER_ENTRY_METHOD * n_list + FLOP_PER_PAIR_METHOD * n_cut) * n
+        else:
+            flops = (FLOP_PER_ENTRY_PLAIN * n_list + FLOP_PER_PAIR_PLAIN * n_cut) * n
+        alu_peak = peaks["fp64_tflops"] if args.precision == "fp64" else peaks["fp32_tflops"]
         hbm = n * (4 * n_list + 52 + 192)
         line = {"workload": workload,
                 "config": f"LJ rho={rho} T={temperature} dt={dt} r_c=2.5 shifted skin {skin}, N={n}",
@@ -622,12 +631,15 @@ def lj_cases(args, local, cases, workload, temperature, dt, skin):
                 "step_kernel_alu_tflops": flops / (k_ms * 1e-3) / 1e12 if k_ms > 0 else None,
                 "step_kernel_list_gbs": n * (4 * n_list + 52) / (k_ms * 1e-3) / 1e9 if k_ms > 0 else None,
                 # roofline fractions of the step kernel: its algorithmic flops against the
-                # measured FP32 peak, its algorithmic bytes (list + own state + the fused
-                # integrator's state traffic) against the measured HBM copy rate
-                "step_kernel_alu_frac": flops / (k_ms * 1e-3) / 1e12 / peaks["fp32_tflops"] if k_ms > 0 else None,
+                # measured FMA peak of its precision (FP64 for the FP64 mode, FP32 otherwise),
+                # its algorithmic bytes (list + own state + the fused integrator's state
+                # traffic) against the measured HBM copy rate
+                "step_kernel_alu_frac": flops / (k_ms * 1e-3) / 1e12 / alu_peak if k_ms > 0 else None,
+                "step_kernel_alu_peak": "fp64" if args.precision == "fp64" else "fp32",
                 "step_kernel_hbm_frac": n * (4 * n_list + 52 + 192) / (k_ms * 1e-3) / 1e9 / hbm_peak
                 if k_ms > 0 else None,
-                "peaks": {"fp32_tflops": peaks["fp32_tflops"], "hbm_gbs": hbm_peak},
+                "peaks": {"fp32_tflops": peaks["fp32_tflops"], "fp64_tflops": peaks["fp64_tflops"],
+                          "hbm_gbs": hbm_peak},
                 "clocks": clk,
                 "autotune": [{k: (round(v, 5) if isinstance(v, float) else v) for k, v in t.items()}
                              for t in trials] if trials else None}

@@ -1966,9 +1966,9 @@ __global__ void __launch_bounds__(kIntBlock) k_permute(KArgs a)
 // inside a cell), dropping those farther than the largest list radius from
 // the cell's own box; then every lane tests the staged candidates one after
 // the other (each read is a broadcast) against its own particle and appends
-// those closer than r_c,ab + skin (plus a rounding margin) to its row, in that
-// order: a small per-lane buffer in shared memory is written out to the
-// particle-major list nbr[i*Kstride + k] 16 entries at a time.  No block
+// those closer than r_c,ab + skin (plus a rounding margin) to its row of the
+// particle-major list nbr[i*Kstride + k], in that order, one store per entry
+// kept (the L2 merges the row's words).  No block
 // barrier: the cells of a block never wait for one another.  Distances are
 // single precision: from the fixed-point copy in MIXED mode, from the
 // (rounded) positions otherwise; the list only has to contain every pair
@@ -1978,12 +1978,10 @@ __global__ void __launch_bounds__(kIntBlock) k_permute(KArgs a)
 // size is too large.
 // ---------------------------------------------------------------------------
 constexpr int kNbStage = 256;    // staged candidates per round and warp
-constexpr int kNbBuf = 16;       // list entries a lane collects before writing them out
 
 struct NbWarp {
     float4 pos[kNbStage];
     int idx[kNbStage];
-    int buf[32][kNbBuf + 1];     // (+1: lanes in different banks)
     int cell[27];
 };
 
@@ -2090,7 +2088,6 @@ __device__ __forceinline__ void nbuild_cell_warp(const KArgs &a, int pn, int c, 
     const unsigned lt_mask = (1u << lane) - 1u;
     // nb_r2 of the fixed-point words is in units of qunit^2: the list radii follow
     const float r2unit = (P == MIXED && kNbFixed) ? 1.0f / (rp.qunit * rp.qunit) : 1.0f;
-    int *buf = S.buf[lane];
 
     for (int ob = c0; ob < c1; ob += 32) {
         const int i = ob + lane;
@@ -2101,11 +2098,10 @@ __device__ __forceinline__ void nbuild_cell_warp(const KArgs &a, int pn, int c, 
         const float rl1 = own ? a.tab.rl2[ti * 2 + 1] * r2unit : -1.0f;
         int *row = a.nbr + (size_t)(own ? i : ob) * (size_t)a.Kstride;
         int cnt = 0;          // neighbours found
-        int nb = 0;           // of them in the lane's buffer
         int staged = 0;
 
-        // test the staged candidates against the lane's particle, in order; every
-        // 16 entries kept go out as four 16-byte stores (rows start 32-byte aligned)
+        // test the staged candidates against the lane's particle, in order; each
+        // entry kept goes straight to the lane's row (the L2 merges a row's writes)
         auto scan = [&]() {
             __syncwarp();
 #pragma unroll 4
@@ -2114,19 +2110,9 @@ __device__ __forceinline__ void nbuild_cell_warp(const KArgs &a, int pn, int c, 
                 const int jj = S.idx[s];
                 const float r2 = nb_r2<P>(H, y, rp);
                 const bool in = r2 < (nb_species<P>(y) != 0 ? rl1 : rl0) && jj != i;
-                if (in) {
-                    if (cnt < K) {
-                        buf[nb] = jj;
-                        if (++nb == kNbBuf) {
-                            int4 *dst = (int4 *)(row + (cnt + 1 - kNbBuf));
-#pragma unroll
-                            for (int w = 0; w < kNbBuf / 4; ++w)
-                                dst[w] = make_int4(buf[4 * w], buf[4 * w + 1], buf[4 * w + 2], buf[4 * w + 3]);
-                            nb = 0;
-                        }
-                    }
-                    ++cnt;
-                }
+                if (in && cnt < K)
+                    row[cnt] = jj;
+                cnt += in ? 1 : 0;
             }
             __syncwarp();
             staged = 0;
@@ -2163,12 +2149,9 @@ __device__ __forceinline__ void nbuild_cell_warp(const KArgs &a, int pn, int c, 
         scan();
 
         if (own) {
-            // the entries still in the buffer, then padding with the particle itself to a
-            // multiple of kUnr entries, so the pair loop reads whole groups without masking
+            // padding with the particle itself to a multiple of kUnr entries, so the pair
+            // loop reads whole groups without masking
             const int kept = cnt < K ? cnt : K;
-            const int from = kept - nb;
-            for (int w = 0; w < nb; ++w)
-                row[from + w] = buf[w];
             for (int k = kept; k < (kept + kUnr - 1) / kUnr * kUnr && k < K; ++k)
                 row[k] = i;
             a.nnbr[i] = kept;

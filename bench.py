@@ -59,6 +59,8 @@ def parse_args(argv=None):
     ap.add_argument("--tpp", type=int, default=0, help="force-kernel threads per particle (0 = auto)")
     ap.add_argument("--step-form", type=int, default=0, choices=[0, 1, 2],
                     help="step-kernel blocks: 0 auto, 1 one per chunk, 2 resident blocks sweep (not FP64)")
+    ap.add_argument("--build-form", type=int, default=0, choices=[0, 1, 2],
+                    help="neighbour build: 0 auto, 1 one warp per cell, 2 one block per cell")
     ap.add_argument("--check", type=int, default=0,
                     help="MD steps between rebuild checks of the graph (0 = the library's choice)")
     ap.add_argument("--skin", type=float, default=0.3, help="neighbour-list skin (with --no-tune)")
@@ -288,7 +290,7 @@ def run_ours(args, rank, world, local):
     pos0, vel0, img0 = sim.get_state()
     base = md.make_params(s.params, 0.001, skin=args.skin, precision=md.PRECISIONS[args.precision],
                           sample_interval=100, use_graph=not args.no_graph, threads_per_particle=args.tpp,
-                          check_interval=args.check, step_form=args.step_form)
+                          check_interval=args.check, step_form=args.step_form, build_form=args.build_form)
     trials = None
     if not args.no_tune:
         from paper_0912_3824_gb300 import tune
@@ -580,7 +582,8 @@ def lj_cases(args, local, cases, workload, temperature, dt, skin):
         s = synth.lj_fluid(n=n, density=rho, temperature=temperature, seed=3)
         sim = md.System.from_synth(s, dt=dt, skin=skin, precision=md.PRECISIONS[args.precision],
                                    sample_interval=100, device=device, threads_per_particle=args.tpp,
-                                   use_graph=not args.no_graph, step_form=args.step_form)
+                                   use_graph=not args.no_graph, step_form=args.step_form,
+                                   build_form=args.build_form)
         equilibrate(sim, max(1.5, temperature), temperature, melt_blocks=5, final_blocks=5)
         trials = None
         if not args.no_tune:
@@ -589,7 +592,7 @@ def lj_cases(args, local, cases, workload, temperature, dt, skin):
             pos0, vel0, img0 = sim.get_state()
             base = md.make_params(s.params, dt, skin=skin, precision=md.PRECISIONS[args.precision],
                                   sample_interval=100, threads_per_particle=args.tpp, use_graph=not args.no_graph,
-                                  step_form=args.step_form)
+                                  step_form=args.step_form, build_form=args.build_form)
             base, trials = tune.autotune(base, [s.n], [s.box], s.species, pos0, vel0, img0, device=device,
                                          skins=(skin,))
             sim.close()

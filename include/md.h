@@ -129,10 +129,10 @@ typedef struct {
                                  MD_E_TIMEOUT after this many step-kernel executions (its
                                  iteration bound; automatic = nsteps + 64), so the bounded-
                                  loop path can be exercised                                     */
-    int32_t build_form;       /* neighbour build: 0 = automatic (one warp per cell when the cells
-                                 are at least as many as the GPU's warp slots for it, else one
-                                 block per cell), 1 = one warp per cell, 2 = one block per cell;
-                                 the lists are the same either way                             */
+    int32_t build_form;       /* neighbour build: 0 = automatic (one warp per cell when there
+                                 are at least 8 cells per SM and at most 32 particles per cell
+                                 on average, else one block per cell), 1 = one warp per cell,
+                                 2 = one block per cell; the lists are the same either way     */
 } md_params;
 
 /* one sample of the reductions of Sec. 2.2, per replica */

@@ -55,6 +55,7 @@ namespace {
 
 constexpr size_t kAlign = 256;
 constexpr int kIntBlock = 256, kForceBlock = 128, kScanBlock = 1024;
+constexpr int kNbWarpCellsPerSm = 8;                     // warp-per-cell build from this many cells per SM
 constexpr int kNbCells = 4, kNbBlock = 32 * kNbCells;   // neighbour build: one warp per cell ...
 constexpr int kNbBlockB = 256;                          // ... or one block per cell
 constexpr double kCellMargin = 1e-3;   // cell edge exceeds the largest list radius by this
@@ -1083,7 +1084,7 @@ static int create_impl(md_handle *h, const md_params *p, const int32_t *species,
     if (a.hdtm_hi[0] == 0.0f)
         return fail(h, MD_E_INVAL, "dt / (2 m) underflows single precision");
 
-    int dev = 0, nsm = 0, per_sm = 0, per_sm_sw = 0, per_sm_nb = 0;
+    int dev = 0, nsm = 0, per_sm = 0, per_sm_sw = 0;
     CK(h, cudaGetDevice(&dev));
     CK(h, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     {
@@ -1097,10 +1098,13 @@ static int create_impl(md_handle *h, const md_params *p, const int32_t *species,
         h->g.sweep = sweepk && per_sm_sw > 0 &&
                      (p->step_form == 2 || (p->step_form == 0 && (int64_t)g.nblk_f > (int64_t)nsm * per_sm_sw));
     }
-    // the build takes a warp per cell when the cells fill the GPU's warp slots that way
-    CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_nb, h->ks->nbuild, kNbBlock, 0));
+    // the build takes a warp per cell when there are at least kNbWarpCellsPerSm cells per SM
+    // and a cell's particles fit one batch of lanes on average; a block per cell otherwise
+    // (measured on GB300: LJ at 729 cells or fewer and dense cells of ~40 are faster with a
+    // block per cell, LJ from 1331 cells and KA N=65,536 with a warp per cell)
     h->g.nb_block = p->build_form == 2 ||
-                    (p->build_form == 0 && (int64_t)g.ncell < (int64_t)nsm * per_sm_nb * kNbCells);
+                    (p->build_form == 0 && ((int64_t)g.ncell < (int64_t)kNbWarpCellsPerSm * nsm ||
+                                            (double)g.n > 32.0 * (double)g.ncell));
     // pinned staging, events
     CK(h, cudaEventCreateWithFlags(&h->ev_stage, cudaEventDisableTiming));
     CK(h, cudaEventCreate(&h->ev_f0));

@@ -386,8 +386,8 @@ def run_ours(args, rank, world, local):
         "kernel_count": {"flop_per_launch": flops_kernel, "tflops": flops_kernel / (f_ms * 1e-3) / 1e12,
                          "note": f"{FLOP_PER_ENTRY} per entry + {FLOP_PER_PAIR} per pair + {FLOP_PER_UPDATE} "
                                  "per particle (update), counted as this kernel computes"},
-        "traffic": profiled_traffic(f"k_step<{md.PRECISIONS[args.precision]}, {info1['threads_per_particle']}, 0>",
-                                    base.skin),
+        "traffic": profiled_traffic(f"k_step<{md.PRECISIONS[args.precision]}, {info1['threads_per_particle']}, 0, "
+                                    f"{1 if info1['step_form'] == 2 else 0}>", base.skin),
         "per_launch_ms": f_ms, "launches_timed": int(n_dev),
         "per_launch_ms_events": ev_ms,
         "timing": "per_launch_ms: device timer over the timed region (every k_step launch of the graph); "

@@ -53,7 +53,7 @@ def test_profiled_traffic_only_for_the_captured_kernel_and_skin():
         assert 20e6 < got < 40e6                  # one cold launch at KA N=65536: list + state
     else:
         assert got is None                        # sources changed since the capture
-    assert bench.profiled_traffic("k_step<0, 4, 0>", skin) is None
+    assert bench.profiled_traffic("k_step<0, 4, 0, 0>", skin) is None
     assert bench.profiled_traffic(kernel, skin + 0.1) is None
 
 

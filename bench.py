@@ -248,7 +248,9 @@ def prepare(md, synth, n, seed, precision, device, use_graph=True, tpp=0):
     return s, sim
 
 
-def time_chunks(torch, sim, nsteps_inner, k, flush, stream):
+def time_iterations(torch, sim, nsteps_inner, k, flush, stream):
+    """k timed md_step(nsteps_inner) calls, the L2 flushed before each; the
+    device time of each call (CUDA events on the launching stream), in ms."""
     ms = []
     for _ in range(k):
         flush.fill_(1)
@@ -259,7 +261,20 @@ def time_chunks(torch, sim, nsteps_inner, k, flush, stream):
         e1.record(stream)
         ms.append((e0, e1))
     torch.cuda.synchronize()
-    return sum(a.elapsed_time(b) for a, b in ms)
+    return [a.elapsed_time(b) for a, b in ms]
+
+
+def time_chunks(torch, sim, nsteps_inner, k, flush, stream):
+    return sum(time_iterations(torch, sim, nsteps_inner, k, flush, stream))
+
+
+def median_of_groups(iter_ms, groups=5):
+    """The timed iterations split into `groups` consecutive groups: the median
+    of the groups' mean times per iteration (ms), or None with fewer iterations."""
+    if len(iter_ms) < groups:
+        return None
+    parts = np.array_split(np.asarray(iter_ms, dtype=np.float64), groups)
+    return float(np.median([p.mean() for p in parts]))
 
 
 def energy_drift(obs, n):
@@ -312,7 +327,8 @@ def run_ours(args, rank, world, local):
     # cudaProfilerStart/Stop bracket the timed region, so a profiler started
     # with profiling off (ncu --profile-from-start off) sees exactly its launches
     torch.cuda.profiler.start()
-    total_ms = time_chunks(torch, sim, args.inner, args.steps, flush, stream)
+    iter_ms = time_iterations(torch, sim, args.inner, args.steps, flush, stream)
+    total_ms = sum(iter_ms)
     torch.cuda.synchronize()
     torch.cuda.profiler.stop()
     clk = clocks.stop()
@@ -332,6 +348,12 @@ def run_ours(args, rank, world, local):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": tmax * 1e3 / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
+        # the timed iterations in 5 consecutive groups: the median group, as particle-steps/s
+        # of this rank, beside the spread of single iterations
+        "repeats": {"groups": 5, "median_ms_per_step": median_of_groups(iter_ms),
+                    "median_value": (float(args.n) * args.inner / (median_of_groups(iter_ms) * 1e-3)
+                                     if median_of_groups(iter_ms) else None),
+                    "min_ms_per_step": float(min(iter_ms)), "max_ms_per_step": float(max(iter_ms))},
         "dtype": {"mixed": "f32 pair math, f32x2 (double-single) state", "fp64": "f64", "fp32": "f32"}[args.precision],
         "data": "synthetic (seeded fcc lattice, melted and quenched on the GPU)",
         "config": {"workload": ka_workload(args.n),

@@ -113,3 +113,10 @@ def test_paper_workload_constants_match_the_generators_and_bench():
     assert (st["n"], st["density"], st["temperature"]) == (const["stab_n"], const["stab_density"],
                                                            const["stab_temperature"])
     assert bench.KA_DT == const["ka_dt"]
+
+
+def test_median_of_groups():
+    """Five consecutive groups of the timed iterations; the median of their means."""
+    it = [1.0, 1.0, 2.0, 2.0, 3.0, 3.0, 4.0, 4.0, 9.0, 9.0]
+    assert bench.median_of_groups(it) == 3.0
+    assert bench.median_of_groups([1.0, 2.0]) is None

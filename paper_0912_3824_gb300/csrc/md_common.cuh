@@ -117,10 +117,9 @@ struct KArgs {
     const int4 *blk_s;                // step kernel: rows of blk_f in the order the resident blocks
                                       // take them, cpb per block (w = -1: padding)
     int cpb;                          // step kernel: chunks per block
-    double *part_f, *part_i;          // partial sums per chunk [nblk_f][12], per block [nblk_i][4]
-    void *part_e;                     // potential energy per warp of each chunk, two step parities
-                                      // [2][nblk_f][4]: double (FP64 mode) or float2 double-single
-                                      // (MIXED, FP32)
+    double *part_f, *part_i;          // per-block partial sums [nblk_f][12], [nblk_i][4]
+    void *part_e;                     // per-block potential energy [nblk_f]: double (FP64 mode) or
+                                      // float2 double-single (MIXED, FP32)
     Obs *ring, *totals;
     double *epot;                     // per-step potential energy [epot_cap][nrep], slot = step % cap
     long long *epot_step;             // [epot_cap]: the step held by each slot (-1 = none)

@@ -72,8 +72,11 @@ def parse_args(argv=None):
     ap.add_argument("--sizes", type=int, nargs="*", default=None, help="lj-sweep / e1 particle counts")
     ap.add_argument("--densities", type=float, nargs="*", default=None, help="e1 number densities")
     ap.add_argument("--md-steps", type=int, default=100000, help="drift: NVE MD steps per run")
+    ap.add_argument("--fp64-steps", type=int, default=None,
+                    help="longrun: FP64 NVE steps (default a fifth of --md-steps)")
     ap.add_argument("--cases", nargs="*", default=None, help="drift: subset of cases")
-    ap.add_argument("--seeds", type=int, nargs="*", default=None, help="stats: seeds of the independent runs")
+    ap.add_argument("--seeds", type=int, nargs="*", default=None,
+                    help="stats / longrun: seeds of the independent runs")
     ap.add_argument("--precisions", nargs="*", default=None, help="stats / drift-floor / longrun: precisions")
     ap.add_argument("--dt", type=float, default=None, help="longrun: time step (default 0.001)")
     ap.add_argument("--smooth", type=float, nargs="*", default=None, help="longrun: smoothing widths h")
@@ -783,20 +786,24 @@ def run_drift(args, local):
 
 def run_longrun(args, local):
     """KA N=65536 quenched to T=0.5 (rescaled after every step for 10^4 steps),
-    then NVE for --md-steps steps (FP64: 1/5 of that) in each of --precisions
-    (mixed and FP64 by default), for each smoothing width of --smooth (the
-    plain cut and h = 0.005 of Sec. 4 by default) at time step --dt (0.001 by
-    default): the energy drift per particle over a long run."""
+    then NVE for --md-steps steps (FP64: --fp64-steps, by default 1/5 of that)
+    in each of --precisions (mixed and FP64 by default), for each smoothing
+    width of --smooth (the plain cut and h = 0.005 of Sec. 4 by default) at
+    time step --dt (0.001 by default) and each of --seeds (5 by default): the
+    energy drift per particle over a long run."""
     from paper_0912_3824_gb300 import synth
     cases = []
     dt = args.dt or KA_DT
-    for h in (args.smooth if args.smooth is not None else (0.0, 0.005)):
-        params = synth.ka_params(smooth=h)
-        cases.append((f"ka65536-h{h}-dt{dt}", lambda params=params: synth.make_system(65536, 1.2, 2.0, 5, params),
-                      dt, (2.0, 0.5), args.md_steps))
+    for sd in (args.seeds or [5]):
+        for h in (args.smooth if args.smooth is not None else (0.0, 0.005)):
+            params = synth.ka_params(smooth=h)
+            cases.append((f"ka65536-h{h}-dt{dt}" + (f"-s{sd}" if sd != 5 else ""),
+                          lambda params=params, sd=sd: synth.make_system(65536, 1.2, 2.0, sd, params),
+                          dt, (2.0, 0.5), args.md_steps))
     emit = lambda ln: print(json.dumps(ln), flush=True)
+    fp64_steps = args.fp64_steps if args.fp64_steps else max(1000, args.md_steps // 5)
     nve_cases(args, local, cases, "longrun", precisions=tuple(args.precisions or ("mixed", "fp64")),
-              steps_of={"fp64": max(1000, args.md_steps // 5)}, emit=emit)
+              steps_of={"fp64": fp64_steps}, emit=emit)
     return []
 
 

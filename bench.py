@@ -462,7 +462,9 @@ def run_ours(args, rank, world, local):
     t_e2e = time.perf_counter() - t0
     result["e2e"] = {"value": s.n * args.inner * ke / t_e2e, "unit": UNIT,
                      "h2d_bytes_per_step": int(pos_h.nbytes + vel_h.nbytes + img_h.nbytes),
-                     "d2h_bytes_per_step": int(nrec * 120 // ke + 104), "iterations": ke}
+                     "d2h_bytes_per_step": int(nrec * 120 // ke + 104), "iterations": ke,
+                     "step": f"one timed iteration: state up from host memory, md_step({args.inner}), "
+                             "observables back"}
     sim.close()
 
     # ---- CPU baseline: the FP64 oracle as it stands, on the host cores ----

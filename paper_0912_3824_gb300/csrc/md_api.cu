@@ -153,8 +153,10 @@ int auto_capacity(const md_params *p, const Geometry &g, const std::vector<doubl
 }
 
 // Launch order of the force-kernel chunks.  A launch that fits in one wave
-// (at most `resident` blocks) hands its blocks to the SMs in turns, so blocks
-// p, p + nsm, p + 2 nsm, ... share an SM; giving them consecutive chunks
+// (at most `resident` blocks) hands its blocks to the SMs in turns: the first
+// nsm blocks go one to each SM (in an order of the GPU's own, not p -> SM p),
+// and the next nsm in the same order, so blocks p, p + nsm, p + 2 nsm, ...
+// share an SM (per-block SM ids read on GB300); giving them consecutive chunks
 // (neighbouring cells along the cell curve) lets one SM's blocks share the
 // neighbour positions they gather in its L1.  A longer launch keeps the chunk
 // order, so that the blocks resident at any time cover one compact region.
@@ -179,11 +181,12 @@ static std::vector<int4> sm_block_order(const std::vector<int4> &chunks, int nsm
 
 // Rows of the step kernel's table (see KArgs::blk_s).  With one block per
 // chunk they are the force kernel's rows.  The sweeping form launches only the
-// resident blocks (nsm * per_sm, block p on SM p mod nsm) and gives each SM one
-// run of consecutive chunks along the cell curve: the per_sm blocks of an SM
-// take neighbouring chunks of its run side by side (block k of SM s: chunks
-// base_s + k, base_s + k + per_sm, ...), so that at any time they work on one
-// compact region and share the neighbour positions they gather in the SM's L1
+// resident blocks (nsm * per_sm) and gives each group of blocks that share an
+// SM (blocks s, s + nsm, s + 2 nsm, ...) one run of consecutive chunks along
+// the cell curve: the per_sm blocks of group s take neighbouring chunks of its
+// run side by side (block s + k nsm: chunks base_s + k, base_s + k + per_sm,
+// ...), so that at any time they work on one compact region and share the
+// neighbour positions they gather in the SM's L1
 // (with one block per chunk, a launch longer than one wave hands each freed
 // slot the next chunk, so an SM's blocks lie anywhere in the resident region).
 // Each row carries its chunk index in w; a block's rows end in padding

@@ -27,7 +27,7 @@ OUT_DIR_CHECKED = os.path.join(HERE, "_build_checked")
 LIB_CHECKED = os.path.join(HERE, "libmdgb300_checked.so")
 SOURCES = ["md_api.cu", "md_kernels_mixed.cu", "md_kernels_fp64.cu", "md_kernels_fp32.cu", "md_noalloc.cu",
            "md_peak.cu"]
-HEADERS = ["md_common.cuh", "md_kernels.cuh"]
+HEADERS = ["md_common.cuh", "md_kernels.cuh", "md_tables.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -29,6 +29,7 @@
 #include <vector>
 
 #include "md.h"
+#include "md_tables.h"
 #include "md_common.cuh"
 #include "md_corr.cuh"
 
@@ -150,84 +151,6 @@ int auto_capacity(const md_params *p, const Geometry &g, const std::vector<doubl
     k = (k + 31) / 32 * 32;
     (void)p;
     return std::max(k, 32);
-}
-
-// Launch order of the force-kernel chunks.  A launch that fits in one wave
-// (at most `resident` blocks) hands its blocks to the SMs in turns: the first
-// nsm blocks go one to each SM (in an order of the GPU's own, not p -> SM p),
-// and the next nsm in the same order, so blocks p, p + nsm, p + 2 nsm, ...
-// share an SM (per-block SM ids read on GB300); giving them consecutive chunks
-// (neighbouring cells along the cell curve) lets one SM's blocks share the
-// neighbour positions they gather in its L1.  A longer launch keeps the chunk
-// order, so that the blocks resident at any time cover one compact region.
-// Block p carries its chunk index in w, where its partial sums go, so the
-// per-replica sums keep their order.
-static std::vector<int4> sm_block_order(const std::vector<int4> &chunks, int nsm, int resident)
-{
-    const int nb = (int)chunks.size();
-    std::vector<int4> out(chunks);
-    for (int c = 0; c < nb; ++c)
-        out[c].w = c;
-    if (nsm <= 1 || nb <= nsm || nb > resident)
-        return out;
-    int c = 0;
-    for (int s = 0; s < nsm; ++s)
-        for (int p = s; p < nb; p += nsm, ++c) {
-            out[p] = chunks[c];
-            out[p].w = c;
-        }
-    return out;
-}
-
-// Rows of the step kernel's table (see KArgs::blk_s).  With one block per
-// chunk they are the force kernel's rows.  The sweeping form launches only the
-// resident blocks (nsm * per_sm) and gives each group of blocks that share an
-// SM (blocks s, s + nsm, s + 2 nsm, ...) one run of consecutive chunks along
-// the cell curve: the per_sm blocks of group s take neighbouring chunks of its
-// run side by side (block s + k nsm: chunks base_s + k, base_s + k + per_sm,
-// ...), so that at any time they work on one compact region and share the
-// neighbour positions they gather in the SM's L1
-// (with one block per chunk, a launch longer than one wave hands each freed
-// slot the next chunk, so an SM's blocks lie anywhere in the resident region).
-// Each row carries its chunk index in w; a block's rows end in padding
-// (w = -1).  Returns the rows, cpb per block.
-static std::vector<int4> step_table(const std::vector<int4> &order, const std::vector<int4> &chunks, bool sweep,
-                                    int nsm, int per_sm, int &nblk_s, int &cpb)
-{
-    const int nb = (int)chunks.size();
-    if (!sweep || nsm < 1 || per_sm < 1) {
-        nblk_s = nb;
-        cpb = 1;
-        return order;
-    }
-    if ((int64_t)nsm * per_sm > nb) {           // fewer chunks than resident blocks: at most nb blocks
-        if (nb < nsm) {
-            nsm = nb;
-            per_sm = 1;
-        } else {
-            per_sm = nb / nsm;
-        }
-    }
-    const int resident = nsm * per_sm;           // <= nb, so the rows (< nb + resident) fit 2 nb
-    nblk_s = resident;
-    cpb = (nb + resident - 1) / resident;
-    std::vector<int4> rows((size_t)resident * cpb, make_int4(0, 0, 0, -1));
-    int base = 0;
-    for (int s = 0; s < nsm; ++s) {
-        const int ns = nb / nsm + (s < nb % nsm ? 1 : 0);   // chunks of SM s
-        for (int k = 0; k < per_sm; ++k) {
-            const int b = s + k * nsm;
-            for (int q = 0; q < cpb; ++q) {
-                const int c = q * per_sm + k;
-                if (c >= ns)
-                    break;
-                rows[(size_t)b * cpb + q] = chunks[base + c];
-                rows[(size_t)b * cpb + q].w = base + c;
-            }
-        }
-        base += ns;
-    }
-    return rows;
 }
 
 // Returns MD_OK or MD_E_INVAL with *msg set.
@@ -1128,8 +1051,9 @@ static int create_impl(md_handle *h, const md_params *p, const int32_t *species,
             q += align_up(bytes);
             return e == cudaSuccess ? MD_OK : cuda_fail(h, e, "table upload");
         };
-        const std::vector<int4> bf = sm_block_order(g.blk_f, nsm, nsm * per_sm);
-        const std::vector<int4> bs = step_table(bf, g.blk_f, h->g.sweep, nsm, per_sm_sw, h->g.nblk_s, h->g.cpb);
+        const std::vector<int4> bf = mdt::sm_block_order(g.blk_f, nsm, nsm * per_sm);
+        const std::vector<int4> bs =
+            mdt::step_table(bf, g.blk_f, h->g.sweep, nsm, per_sm_sw, h->g.nblk_s, h->g.cpb);
         h->a.cpb = h->g.cpb;
         if ((rc = put(L.off_rep, g.rep.data(), sizeof(mdk::Rep) * g.R)) ||
             (rc = put(L.off_blk_i, g.blk_i.data(), sizeof(int4) * g.nblk_i)) ||
